@@ -1,0 +1,209 @@
+/*
+ * dwfmg — adaptive multigrid for the 5D Shamir domain-wall fermion operator
+ * on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The method is that of Cohen, Brower, Clark, Osborn, "Multigrid Algorithms
+ * for Domain-Wall Fermions" (Lattice 2011): solve D x = b (Sec. 1: the
+ * problem A x = b with residual r = A x - b) with flexible GCR (Sec. 3)
+ * preconditioned by a V-cycle (Sec. 2: pre-smooth, restrict, coarse solve,
+ * prolong, post-smooth) whose coarse spaces are spanned by adaptively found
+ * near-null vectors cut into blocks that cover the whole fifth dimension
+ * (Sec. 2).
+ *
+ * Conventions used throughout
+ * ---------------------------
+ * Lattice: dims[4] = {X, Y, Z, T}; 4D site index site = ((t*Z + z)*Y + y)*X + x.
+ * Operator (Sec. 2 names the Shamir domain-wall operator; Sec. 4 its 11-site
+ * one-hop stencil; the explicit form below is the standard unnormalised
+ * Shamir operator):
+ *   (D psi)(x,s) = (5 - M5) psi(x,s)
+ *       - 1/2 sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu,s) + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu,s) ]
+ *       - P_- psi(x,s+1) - P_+ psi(x,s-1),
+ *   where at s = Ls-1 the term -P_- psi(x,Ls) becomes +mf P_- psi(x,0) and at
+ *   s = 0 the term -P_+ psi(x,-1) becomes +mf P_+ psi(x,Ls-1).  Gamma matrices
+ *   in the chiral (DeGrand-Rossi) basis, g_5 = diag(1,1,-1,-1), P_+- = (1 +- g_5)/2.
+ *   Links are periodic; the fermion is periodic in x, y, z and, if
+ *   antiperiodic_t != 0, antiperiodic in t.
+ * Links (input): complex128, U[site][mu][a][b] (row a, column b), mu = 0..3
+ *   for x, y, z, t.  They must be SU(3) (unitary, det 1): the FP32 copy keeps
+ *   two rows and rebuilds the third.
+ * Canonical fermion layout (dwf_pack / dwf_unpack): complex, index
+ *   ((s*V + site)*4 + spin)*3 + colour, s slowest.
+ * Internal fermion layout (every other call): complex, index
+ *   (site*12 + spin*3 + colour)*Ls + s, s fastest.  FP64 = interleaved
+ *   double pairs, FP32 = interleaved float pairs.  With nrhs > 1 the nrhs
+ *   fields follow one another in memory.
+ *
+ * Memory and ownership: every pointer argument named *_dev must be device
+ * memory of the current CUDA device; arguments documented as "host or
+ * device" are inspected with cudaPointerGetAttributes and staged through
+ * library-owned device buffers when they are host memory.  The caller owns
+ * all buffers it passes in; the library never frees them.  The context owns
+ * everything it allocates (link copies, near-null vectors, coarse operators,
+ * workspaces) and frees it in dwf_destroy.
+ *
+ * Streams: all work of a context runs on the stream given to dwf_create.
+ * dwf_apply, dwf_pack and dwf_unpack are asynchronous; mg_setup and mg_solve
+ * synchronise the stream before they return their status.
+ *
+ * Errors: calls return a dwf_status and never throw.  After DWF_ECUDA the
+ * context is left in an error state and every later call returns DWF_ESTATE.
+ * There is no CPU fallback: without a CUDA device dwf_create fails.
+ */
+#ifndef DWFMG_H
+#define DWFMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dwf_ctx dwf_ctx;
+
+typedef enum {
+    DWF_OK = 0,
+    DWF_EINVAL = -1,      /* bad argument (sizes, null pointers, unsupported combination) */
+    DWF_ECUDA = -2,       /* a CUDA call failed; the context is unusable */
+    DWF_ENOMEM = -3,      /* device allocation failed */
+    DWF_ENOCONV = -4,     /* solver hit its iteration limit; x holds the best iterate */
+    DWF_EBREAKDOWN = -5,  /* Krylov or Gram-Schmidt breakdown (zero or dependent vectors) */
+    DWF_ENAN = -6,        /* NaN or Inf met in a norm */
+    DWF_ETIMEOUT = -7,    /* a bounded device-side wait gave up */
+    DWF_ESTATE = -8       /* wrong call order, or context in error state */
+} dwf_status;
+
+typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_BF16 = 2, DWF_F16 = 3 } dwf_prec;
+
+/* Multigrid parameters.  The paper leaves the smoothers S1, S3, the coarse
+ * solver S2 and the iteration counts open (Sec. 2); mg_default_params fills
+ * in this library's choices.  Level 0 is the fine lattice. */
+typedef struct {
+    int nu_pre;             /* nu_1: CGNR smoothing steps before restriction (default 0) */
+    int nu_post;            /* nu_3: CGNR smoothing steps after prolongation (default 4) */
+    double coarse_tol;      /* S2 relative tolerance on intermediate levels (0.1) */
+    int coarse_maxiter;     /* (24) */
+    double coarsest_tol;    /* S2 relative tolerance on the coarsest level (0.1) */
+    int coarsest_maxiter;   /* (64) */
+    int coarse_restart;     /* GCR restart length of S2 (16) */
+    int outer_restart;      /* outer flexible GCR restart length (10) */
+    int outer_maxiter;      /* (500) */
+    int setup_iters0;       /* CGNR iterations on D x = 0 for the initial vectors (20) */
+    int setup_sweeps;       /* adaptive sweeps re-applying the multigrid to D x = 0 (3) */
+    int setup_sweep_iters;  /* MG-GCR iterations per vector and sweep (4) */
+    int split;              /* 1: each vector split into Gamma = +-1 halves, Nvec/2 vectors (1) */
+    dwf_prec smoother_prec; /* F64 (plain method) or F32 (mixed) for the fine V-cycle (F64) */
+    dwf_prec coarse_prec[4];/* link precision of each coarse level's stencil: F64, F32, BF16, F16 */
+    uint32_t seed;          /* Philox seed of the random start vectors when none are given */
+} mg_params;
+
+typedef struct {
+    int iters;                  /* outer GCR iterations */
+    int restarts;               /* outer cycles (each ends with an FP64 true residual) */
+    long long fine_applies_f64; /* fine D applications in FP64 (incl. D^+ in CGNR) */
+    long long fine_applies_f32; /* fine D applications in FP32 */
+    long long coarse_applies[4];/* coarse operator applications per level 1..3 */
+    double true_res;            /* |b - D x| / |b| in FP64 at return */
+    double seconds;             /* wall time of the call */
+} mg_stats;
+
+/* Fill p with the defaults listed above. */
+void mg_default_params(mg_params *p);
+
+/* Create a context for one lattice.
+ *   dims        X, Y, Z, T (each >= 1)
+ *   Ls          fifth-dimension extent (1 <= Ls <= 128)
+ *   M5, mf      domain-wall height and quark mass
+ *   links       complex128 U[V][4][3][3], host or device; copied
+ *   antiperiodic_t  nonzero: antiperiodic fermion boundary in t
+ *   stream      cudaStream_t to run on (NULL = legacy default stream)
+ * Returns DWF_EINVAL for bad sizes, DWF_ENOMEM / DWF_ECUDA on CUDA failure. */
+dwf_status dwf_create(dwf_ctx **out, const int dims[4], int Ls, double M5, double mf,
+                      const void *links, int antiperiodic_t, void *stream);
+
+/* out = D in (dagger = 0) or D^+ in (dagger != 0) for nrhs fields in the
+ * internal layout, in FP64 or FP32 (prec = DWF_F64 or DWF_F32).  Fine
+ * operator of Sec. 2 / Sec. 4 (the 11-site stencil).  out and in are
+ * device pointers and must not overlap.  Asynchronous. */
+dwf_status dwf_apply(dwf_ctx *ctx, void *out_dev, const void *in_dev, dwf_prec prec, int dagger,
+                     int nrhs);
+
+/* Convert nrhs fields between the canonical layout (complex128, s slowest)
+ * and the internal layout in precision prec.  Both pointers device memory. */
+dwf_status dwf_pack(dwf_ctx *ctx, void *internal_dev, const void *canonical_dev, dwf_prec prec,
+                    int nrhs);
+dwf_status dwf_unpack(dwf_ctx *ctx, void *canonical_dev, const void *internal_dev, dwf_prec prec,
+                      int nrhs);
+
+/* Adaptive multigrid setup (Sec. 2).
+ *   levels      total number of levels including the fine one (2 or 3)
+ *   nvec        coarse components per site for each coarse level (levels-1
+ *               entries); with split = 1 each must be even and Nvec/2 adaptive
+ *               vectors are used
+ *   block       4D block (bx, by, bz, bt) of each transfer (levels-1 entries);
+ *               each must divide the lattice of its level.  Blocks always
+ *               cover the whole fifth dimension (Sec. 2).
+ *   opt         parameters, NULL = mg_default_params
+ *   start       optional random start vectors of the fine level: Nvec/2 (split)
+ *               or Nvec fields in the canonical layout, complex128, host or
+ *               device.  NULL: drawn on the device from Philox-4x32-10 with
+ *               opt->seed.
+ * Synchronous.  DWF_EBREAKDOWN if block Gram-Schmidt meets dependent
+ * vectors. */
+dwf_status mg_setup(dwf_ctx *ctx, int levels, const int *nvec, const int (*block)[4],
+                    const mg_params *opt, const void *start);
+
+/* Solve D x = b to |b - D x| / |b| <= tol (true residual, FP64) with
+ * flexible GCR preconditioned by one V-cycle per iteration (Sec. 2, Sec. 3).
+ *   b, x        nrhs fields in the internal layout, complex128, host or
+ *               device; x holds the initial guess on entry and the solution
+ *               on return (also on DWF_ENOCONV: the best iterate).
+ *   stats       optional, filled on return (totals over the nrhs solves).
+ * Synchronous. */
+dwf_status mg_solve(dwf_ctx *ctx, const void *b, void *x, double tol, int nrhs, mg_stats *stats);
+
+/* ---- Component calls --------------------------------------------------
+ * Each runs one step of the V-cycle on its own, for parity checks against a
+ * reference and for diagnostics.  They need a completed mg_setup.  Levels
+ * count from 0 (the fine lattice).  A coarse field of level l >= 1 is
+ * [site][Nvec] complex over that level's lattice (site index x fastest).
+ * All fields are device memory; FP64 unless stated.  Asynchronous unless
+ * stated. */
+
+/* Lattice extents and components per site of level l (fine: 12 per s). */
+dwf_status mg_level_info(dwf_ctx *ctx, int level, int dims_out[4], int *ncomp_out);
+
+/* Copy the Nvec block-orthonormal basis fields q_k of level l (Sec. 1:
+ * columns of the prolongator P, R = P^+, R P = 1_c), FP64. */
+dwf_status mg_get_vectors(dwf_ctx *ctx, int level, void *out_dev);
+
+/* Copy the coarse stencil of level l >= 1: Y[site][d][k][m], d = 0 self,
+ * 1+2mu (+mu), 2+2mu (-mu), FP64 (Sec. 2: the coarse operator R A P). */
+dwf_status mg_get_coarse_links(dwf_ctx *ctx, int level, void *out_dev);
+
+/* coarse_out (level l+1) = R fine_in (level l);  fine_out = P coarse_in. */
+dwf_status mg_restrict(dwf_ctx *ctx, int level, void *coarse_out_dev, const void *fine_in_dev);
+dwf_status mg_prolong(dwf_ctx *ctx, int level, void *fine_out_dev, const void *coarse_in_dev);
+
+/* out = A_l in (or A_l^+ in) with the coarse stencil of level l >= 1 in the
+ * level's link precision; prec = DWF_F64 or DWF_F32 for the fields. */
+dwf_status mg_coarse_apply(dwf_ctx *ctx, int level, void *out_dev, const void *in_dev, int dagger, dwf_prec prec);
+
+/* x = one fine-level V-cycle applied to b (Sec. 2), run in the smoother
+ * precision; x and b are FP64.  Synchronous. */
+dwf_status mg_vcycle(dwf_ctx *ctx, void *x_dev, const void *b_dev);
+
+/* Description of the last error raised on this thread (diagnostics). */
+const char *dwf_last_error(void);
+
+/* Description of a status code (static string). */
+const char *dwf_strerror(dwf_status s);
+
+/* Release everything the context owns.  Safe on NULL. */
+void dwf_destroy(dwf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWFMG_H */

@@ -1,0 +1,221 @@
+// C-ABI entry points of dwfmg (see include/dwfmg.h for the contract).
+#include <cstring>
+#include <exception>
+
+#include "dwf_internal.cuh"
+#include "mg.cuh"
+
+using dwf::Error;
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+dwf_status fail(dwf_ctx *c, const Error &e) {
+    if (c && (e.st == DWF_ECUDA)) c->sticky = DWF_ESTATE;
+    if (c) dwf::set_last_error(e.msg);
+    return e.st;
+}
+
+template <typename F> dwf_status guarded(dwf_ctx *c, F &&f) {
+    if (c && c->sticky != DWF_OK) return DWF_ESTATE;
+    try {
+        return f();
+    } catch (const Error &e) {
+        return fail(c, e);
+    } catch (const std::bad_alloc &) {
+        return DWF_ENOMEM;
+    } catch (...) {
+        return DWF_ECUDA;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_default_params(mg_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nu_pre = 0;
+    p->nu_post = 4;
+    p->coarse_tol = 0.1;
+    p->coarse_maxiter = 24;
+    p->coarsest_tol = 0.1;
+    p->coarsest_maxiter = 64;
+    p->coarse_restart = 16;
+    p->outer_restart = 10;
+    p->outer_maxiter = 500;
+    p->setup_iters0 = 20;
+    p->setup_sweeps = 3;
+    p->setup_sweep_iters = 4;
+    p->split = 1;
+    p->smoother_prec = DWF_F64;
+    for (int i = 0; i < 4; ++i) p->coarse_prec[i] = DWF_F64;
+    p->seed = 1u;
+}
+
+const char *dwf_strerror(dwf_status s) {
+    switch (s) {
+        case DWF_OK: return "success";
+        case DWF_EINVAL: return "invalid argument";
+        case DWF_ECUDA: return "CUDA error";
+        case DWF_ENOMEM: return "out of device memory";
+        case DWF_ENOCONV: return "solver did not converge within its iteration limit";
+        case DWF_EBREAKDOWN: return "Krylov or Gram-Schmidt breakdown";
+        case DWF_ENAN: return "NaN or Inf encountered";
+        case DWF_ETIMEOUT: return "device-side wait timed out";
+        case DWF_ESTATE: return "invalid call order or context in error state";
+    }
+    return "unknown status";
+}
+
+dwf_status dwf_create(dwf_ctx **out, const int dims[4], int Ls, double M5, double mf, const void *links,
+                      int antiperiodic_t, void *stream) {
+    if (!out || !dims || !links) return DWF_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < 4; ++i)
+        if (dims[i] < 1) return DWF_EINVAL;
+    if (Ls < 1 || Ls > 128) return DWF_EINVAL;
+    dwf_ctx *c = new dwf_ctx();
+    dwf_status st = guarded(nullptr, [&]() -> dwf_status {
+        int ndev = 0;
+        DWF_CUDA(cudaGetDeviceCount(&ndev));
+        DWF_REQUIRE(ndev > 0, DWF_ECUDA, "no CUDA device");
+        DWF_CUDA(cudaGetDevice(&c->device));
+        DWF_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+        for (int i = 0; i < 4; ++i) c->g.L[i] = dims[i];
+        c->g.Ls = Ls;
+        c->g.V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+        c->g.ap = antiperiodic_t ? 1 : 0;
+        c->M5 = M5;
+        c->mf = mf;
+        c->stream = (cudaStream_t)stream;
+        size_t lb = (size_t)c->g.V * 4 * 9 * sizeof(double2);
+        c->U64.alloc(lb);
+        c->U32.alloc((size_t)c->g.V * 4 * 6 * sizeof(float2));
+        DWF_CUDA(cudaMemcpyAsync(c->U64.p, links, lb, is_device_ptr(links) ? cudaMemcpyDeviceToDevice
+                                                                             : cudaMemcpyHostToDevice,
+                                 c->stream));
+        dwf::pack_links(c, c->U64.as<double2>());
+        c->scal.alloc(sizeof(double) * dwf::NSCALAR);
+        DWF_CUDA(cudaMemsetAsync(c->scal.p, 0, c->scal.bytes, c->stream));
+        DWF_CUDA(cudaMallocHost((void **)&c->hscal, sizeof(double) * dwf::NSCALAR));
+        c->red_part.alloc(sizeof(double2) * 1024);
+        c->red_count.alloc(sizeof(unsigned));
+        DWF_CUDA(cudaMemsetAsync(c->red_count.p, 0, sizeof(unsigned), c->stream));
+        DWF_CUDA(cudaStreamSynchronize(c->stream));
+        return DWF_OK;
+    });
+    if (st != DWF_OK) {
+        dwf_destroy(c);
+        return st;
+    }
+    *out = c;
+    return DWF_OK;
+}
+
+void dwf_destroy(dwf_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    dwf::mg_free(c);
+    if (c->hscal) cudaFreeHost(c->hscal);
+    delete c;
+}
+
+dwf_status dwf_apply(dwf_ctx *c, void *out, const void *in, dwf_prec prec, int dagger, int nrhs) {
+    if (!c || !out || !in || nrhs < 1 || nrhs > 65535) return DWF_EINVAL;
+    if (prec != DWF_F64 && prec != DWF_F32) return DWF_EINVAL;
+    if (out == in) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        if (prec == DWF_F64)
+            dwf::dslash(c, (double2 *)out, (const double2 *)in, dagger != 0, nrhs);
+        else
+            dwf::dslash(c, (float2 *)out, (const float2 *)in, dagger != 0, nrhs);
+        return DWF_OK;
+    });
+}
+
+dwf_status dwf_pack(dwf_ctx *c, void *internal, const void *canonical, dwf_prec prec, int nrhs) {
+    if (!c || !internal || !canonical || nrhs < 1) return DWF_EINVAL;
+    if (prec != DWF_F64 && prec != DWF_F32) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        dwf::pack(c, internal, (const double2 *)canonical, prec, nrhs);
+        return DWF_OK;
+    });
+}
+
+dwf_status dwf_unpack(dwf_ctx *c, void *canonical, const void *internal, dwf_prec prec, int nrhs) {
+    if (!c || !internal || !canonical || nrhs < 1) return DWF_EINVAL;
+    if (prec != DWF_F64 && prec != DWF_F32) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        dwf::unpack(c, (double2 *)canonical, internal, prec, nrhs);
+        return DWF_OK;
+    });
+}
+
+dwf_status mg_setup(dwf_ctx *c, int levels, const int *nvec, const int (*block)[4], const mg_params *opt,
+                    const void *start) {
+    if (!c || levels < 2 || levels > 4 || !nvec || !block) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        mg_params p;
+        if (opt) p = *opt;
+        else mg_default_params(&p);
+        return dwf::mg_setup_impl(c, levels, nvec, block, p, start, start && !is_device_ptr(start));
+    });
+}
+
+dwf_status mg_solve(dwf_ctx *c, const void *b, void *x, double tol, int nrhs, mg_stats *stats) {
+    if (!c || !b || !x || nrhs < 1 || !(tol > 0.0)) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        bool host = !is_device_ptr(b) || !is_device_ptr(x);
+        return dwf::mg_solve_impl(c, b, x, tol, nrhs, stats, host);
+    });
+}
+
+dwf_status mg_level_info(dwf_ctx *c, int level, int dims_out[4], int *ncomp_out) {
+    if (!c || !dims_out || !ncomp_out) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_level_info_impl(c, level, dims_out, ncomp_out); return DWF_OK; });
+}
+
+dwf_status mg_get_vectors(dwf_ctx *c, int level, void *out) {
+    if (!c || !out) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_get_vectors_impl(c, level, (double2 *)out); return DWF_OK; });
+}
+
+dwf_status mg_get_coarse_links(dwf_ctx *c, int level, void *out) {
+    if (!c || !out) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_get_coarse_links_impl(c, level, (double2 *)out); return DWF_OK; });
+}
+
+dwf_status mg_restrict(dwf_ctx *c, int level, void *cout, const void *fin) {
+    if (!c || !cout || !fin) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_restrict_impl(c, level, (double2 *)cout, (const double2 *)fin); return DWF_OK; });
+}
+
+dwf_status mg_prolong(dwf_ctx *c, int level, void *fout, const void *cin) {
+    if (!c || !fout || !cin) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_prolong_impl(c, level, (double2 *)fout, (const double2 *)cin); return DWF_OK; });
+}
+
+dwf_status mg_coarse_apply(dwf_ctx *c, int level, void *out, const void *in, int dagger, dwf_prec prec) {
+    if (!c || !out || !in || out == in) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_coarse_apply_impl(c, level, out, in, dagger != 0, prec); return DWF_OK; });
+}
+
+dwf_status mg_vcycle(dwf_ctx *c, void *x, const void *b) {
+    if (!c || !x || !b || x == b) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_vcycle_impl(c, (double2 *)x, (const double2 *)b); return DWF_OK; });
+}
+
+const char *dwf_last_error(void) { return dwf::last_error(); }
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Level-1 vector kernels.  Reductions accumulate in FP64 whatever the
+// storage precision and are deterministic: every CTA writes a partial sum,
+// and the last CTA to finish (atomic ticket) adds the partials in a fixed
+// order and stores the result in a device scalar slot, so that solver
+// coefficients can stay on the GPU.
+#include "dwf_internal.cuh"
+
+namespace dwf {
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1024;
+
+__device__ __forceinline__ double2 to_d(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+
+__device__ __forceinline__ double2 block_sum(double2 v, double2 *sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : make_double2(0, 0);
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        }
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+// finish: last CTA reduces the partials; writes out[0] (and out[1] for complex)
+__device__ void finish(double2 mine, double2 *part, unsigned *count, double *out, bool complex_result) {
+    __shared__ double2 sh[32];
+    __shared__ bool last;
+    double2 t = block_sum(mine, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t;
+        __threadfence();
+        unsigned ticket = atomicAdd(count, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double2 v = make_double2(0, 0);
+    for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        const volatile double *pp = reinterpret_cast<const volatile double *>(&part[i]);
+        v.x += pp[0];
+        v.y += pp[1];
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        out[0] = v.x;
+        if (complex_result) out[1] = v.y;
+        *count = 0u;
+    }
+}
+
+template <typename TX, typename TY>
+__global__ void __launch_bounds__(RED_THREADS) dot_kernel(const TX *__restrict__ x, const TY *__restrict__ y, int64_t n,
+                                                          double2 *part, unsigned *count, double *out) {
+    double2 a = make_double2(0, 0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 u = to_d(x[i]), v = to_d(y[i]);
+        a.x += u.x * v.x + u.y * v.y;
+        a.y += u.x * v.y - u.y * v.x;
+    }
+    finish(a, part, count, out, true);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) norm2_kernel(const T *__restrict__ x, int64_t n, double2 *part,
+                                                            unsigned *count, double *out) {
+    double2 a = make_double2(0, 0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 u = to_d(x[i]);
+        a.x += u.x * u.x + u.y * u.y;
+    }
+    finish(a, part, count, out, false);
+}
+
+template <typename T>
+__global__ void zero_kernel(T *x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = cvt<T, double2>(make_double2(0, 0));
+}
+
+template <typename TO, typename TI>
+__global__ void copy_kernel(TO *__restrict__ out, const TI *__restrict__ in, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = cvt<TO, TI>(in[i]);
+}
+
+unsigned red_blocks(dwf_ctx *c, int64_t n) {
+    int64_t b = (n + RED_THREADS - 1) / RED_THREADS;
+    int64_t cap = std::min<int64_t>(RED_MAX_BLOCKS, (int64_t)c->sm_count * 4);
+    return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+unsigned ew_blocks(dwf_ctx *c, int64_t n) {
+    int64_t b = (n + 255) / 256;
+    int64_t cap = (int64_t)c->sm_count * 16;
+    return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+}  // namespace
+
+template <typename T> void bzero(dwf_ctx *c, T *x, int64_t n) {
+    zero_kernel<T><<<ew_blocks(c, n), 256, 0, c->stream>>>(x, n);
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename TO, typename TI> void bcopy(dwf_ctx *c, TO *out, const TI *in, int64_t n) {
+    copy_kernel<TO, TI><<<ew_blocks(c, n), 256, 0, c->stream>>>(out, in, n);
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename TX, typename TY> void bdot(dwf_ctx *c, int slot, const TX *x, const TY *y, int64_t n) {
+    dot_kernel<TX, TY><<<red_blocks(c, n), RED_THREADS, 0, c->stream>>>(
+        x, y, n, c->red_part.as<double2>(), c->red_count.as<unsigned>(), c->scal.as<double>() + slot);
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename T> void bnorm2(dwf_ctx *c, int slot, const T *x, int64_t n) {
+    norm2_kernel<T><<<red_blocks(c, n), RED_THREADS, 0, c->stream>>>(
+        x, n, c->red_part.as<double2>(), c->red_count.as<unsigned>(), c->scal.as<double>() + slot);
+    DWF_CHECK_LAUNCH();
+}
+
+double read_scalar(dwf_ctx *c, int slot) {
+    double v;
+    read_scalars(c, slot, 1, &v);
+    return v;
+}
+
+void read_scalars(dwf_ctx *c, int slot, int count, double *out) {
+    DWF_CUDA(cudaMemcpyAsync(c->hscal, c->scal.as<double>() + slot, sizeof(double) * count,
+                             cudaMemcpyDeviceToHost, c->stream));
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < count; ++i) out[i] = c->hscal[i];
+}
+
+void write_scalar(dwf_ctx *c, int slot, double v) {
+    DWF_CUDA(cudaMemcpyAsync(c->scal.as<double>() + slot, &v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+#define INST2(TX, TY) template void bdot<TX, TY>(dwf_ctx *, int, const TX *, const TY *, int64_t); \
+                      template void bcopy<TX, TY>(dwf_ctx *, TX *, const TY *, int64_t);
+INST2(double2, double2)
+INST2(double2, float2)
+INST2(float2, double2)
+INST2(float2, float2)
+template void bzero<double2>(dwf_ctx *, double2 *, int64_t);
+template void bzero<float2>(dwf_ctx *, float2 *, int64_t);
+template void bnorm2<double2>(dwf_ctx *, int, const double2 *, int64_t);
+template void bnorm2<float2>(dwf_ctx *, int, const float2 *, int64_t);
+
+}  // namespace dwf

@@ -1,0 +1,156 @@
+// Vector updates with host-side coefficients, and the device Philox
+// generator of random start vectors.
+#include "mg.cuh"
+
+namespace dwf {
+
+namespace {
+
+template <typename T>
+__global__ void caxpy_kernel(T *__restrict__ y, double2 a, const T *__restrict__ x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 xv = cvt<double2, T>(x[i]), yv = cvt<double2, T>(y[i]);
+        yv.x += a.x * xv.x - a.y * xv.y;
+        yv.y += a.x * xv.y + a.y * xv.x;
+        y[i] = cvt<T, double2>(yv);
+    }
+}
+
+template <typename T>
+__global__ void cxpay_kernel(T *__restrict__ y, double2 a, const T *__restrict__ x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 xv = cvt<double2, T>(x[i]), yv = cvt<double2, T>(y[i]);
+        y[i] = cvt<T, double2>(make_double2(xv.x + a.x * yv.x - a.y * yv.y, xv.y + a.x * yv.y + a.y * yv.x));
+    }
+}
+
+template <typename T>
+__global__ void rscale_kernel(T *__restrict__ x, double a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = cvt<double2, T>(x[i]);
+        x[i] = cvt<T, double2>(make_double2(a * v.x, a * v.y));
+    }
+}
+
+template <typename T, typename U>
+__global__ void caxpy_mixed_kernel(T *__restrict__ y, double2 a, const U *__restrict__ x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 xv = cvt<double2, U>(x[i]), yv = cvt<double2, T>(y[i]);
+        yv.x += a.x * xv.x - a.y * xv.y;
+        yv.y += a.x * xv.y + a.y * xv.x;
+        y[i] = cvt<T, double2>(yv);
+    }
+}
+
+template <typename T> struct MultiArgs {
+    const T *p[32];
+    double2 b[32];
+    int k;
+};
+
+template <typename T>
+__global__ void multiaxpy_kernel(T *__restrict__ w, MultiArgs<T> a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = cvt<double2, T>(w[i]);
+        for (int j = 0; j < a.k; ++j) {
+            double2 u = cvt<double2, T>(a.p[j][i]);
+            v.x += a.b[j].x * u.x - a.b[j].y * u.y;
+            v.y += a.b[j].x * u.y + a.b[j].y * u.x;
+        }
+        w[i] = cvt<T, double2>(v);
+    }
+}
+
+// Philox-4x32-10 (Salmon et al., SC'11) and Box-Muller, matching the host
+// input generator's addressing: key (seed, stream), counter (i, 0, 0, i>>32).
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__global__ void gauss_kernel(double2 *__restrict__ out, int nfields, int64_t nelem, int Ls, int64_t V, int canon,
+                             uint32_t seed, uint32_t stream) {
+    const int64_t total = nelem * nfields;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = i / nelem, e = i - j * nelem;
+        int64_t idx = i;
+        if (canon) {  // internal (site*12 + comp)*Ls + s  ->  canonical (s*V + site)*12 + comp
+            int s = (int)(e % Ls);
+            int64_t sc = e / Ls;
+            int64_t site = sc / 12;
+            int comp = (int)(sc - site * 12);
+            idx = j * nelem + ((int64_t)s * V + site) * 12 + comp;
+        }
+        uint32_t c[4] = {(uint32_t)idx, 0u, 0u, (uint32_t)(idx >> 32)};
+        philox(c, seed, stream);
+        const double inv53 = 1.0 / 9007199254740992.0;
+        double u0 = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6) + 0.5) * inv53;
+        double u1 = ((double)(c[2] >> 5) * 67108864.0 + (double)(c[3] >> 6) + 0.5) * inv53;
+        double r = sqrt(-2.0 * log(u0));
+        double th = 6.283185307179586476925286766559 * u1;
+        out[i] = make_double2(r * cos(th), r * sin(th));
+    }
+}
+
+unsigned blocks_for(dwf_ctx *c, int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)c->sm_count * 16));
+}
+
+}  // namespace
+
+template <typename T> void caxpy(dwf_ctx *c, T *y, double2 a, const T *x, int64_t n) {
+    caxpy_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(y, a, x, n);
+    DWF_CHECK_LAUNCH();
+}
+template <typename T> void cxpay(dwf_ctx *c, T *y, double2 a, const T *x, int64_t n) {
+    cxpay_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(y, a, x, n);
+    DWF_CHECK_LAUNCH();
+}
+template <typename T> void rscale(dwf_ctx *c, T *x, double a, int64_t n) {
+    rscale_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(x, a, n);
+    DWF_CHECK_LAUNCH();
+}
+template <typename T, typename U> void caxpy_mixed(dwf_ctx *c, T *y, double2 a, const U *x, int64_t n) {
+    caxpy_mixed_kernel<T, U><<<blocks_for(c, n), 256, 0, c->stream>>>(y, a, x, n);
+    DWF_CHECK_LAUNCH();
+}
+template <typename T> void multiaxpy(dwf_ctx *c, T *w, const double2 *beta, T *const *V, int k, int64_t n) {
+    DWF_REQUIRE(k <= 32, DWF_EINVAL, "multiaxpy: at most 32 vectors");
+    if (k == 0) return;
+    MultiArgs<T> a;
+    for (int j = 0; j < k; ++j) {
+        a.p[j] = V[j];
+        a.b[j] = beta[j];
+    }
+    a.k = k;
+    multiaxpy_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(w, a, n);
+    DWF_CHECK_LAUNCH();
+}
+template <typename T> void gauss_fill(dwf_ctx *c, double2 *out, int nfields, int64_t nelem, int Ls, int64_t V,
+                                      bool canonical_fine, uint32_t seed, uint32_t stream) {
+    gauss_kernel<<<blocks_for(c, nelem * nfields), 256, 0, c->stream>>>(out, nfields, nelem, Ls, V,
+                                                                        canonical_fine ? 1 : 0, seed, stream);
+    DWF_CHECK_LAUNCH();
+}
+
+template void caxpy<double2>(dwf_ctx *, double2 *, double2, const double2 *, int64_t);
+template void caxpy<float2>(dwf_ctx *, float2 *, double2, const float2 *, int64_t);
+template void cxpay<double2>(dwf_ctx *, double2 *, double2, const double2 *, int64_t);
+template void cxpay<float2>(dwf_ctx *, float2 *, double2, const float2 *, int64_t);
+template void rscale<double2>(dwf_ctx *, double2 *, double, int64_t);
+template void rscale<float2>(dwf_ctx *, float2 *, double, int64_t);
+template void caxpy_mixed<double2, float2>(dwf_ctx *, double2 *, double2, const float2 *, int64_t);
+template void caxpy_mixed<double2, double2>(dwf_ctx *, double2 *, double2, const double2 *, int64_t);
+template void multiaxpy<double2>(dwf_ctx *, double2 *, const double2 *, double2 *const *, int, int64_t);
+template void multiaxpy<float2>(dwf_ctx *, float2 *, const double2 *, float2 *const *, int, int64_t);
+template void gauss_fill<double2>(dwf_ctx *, double2 *, int, int64_t, int, int64_t, bool, uint32_t, uint32_t);
+
+}  // namespace dwf

@@ -1,0 +1,520 @@
+// Multigrid solver orchestration: the V-cycle (Sec. 2), its CGNR smoother,
+// GCR on coarse levels (S2, recursing through the V-cycle of the next level),
+// the adaptive setup (Sec. 2: Krylov iterations on A x = 0 from random
+// vectors, then re-applying the multigrid to A x = 0) and the outer flexible
+// GCR (Sec. 3) with FP64 true residuals at every restart.
+//
+// Precision: the V-cycle, its smoother and all inner Krylov vectors run in R
+// (double for the plain method, float for the mixed one); coarse stencils use
+// the link precision chosen per level; the outer solution and residual, the
+// block Gram-Schmidt and the coarse-operator construction are FP64.
+#include <chrono>
+#include <cstring>
+#include <type_traits>
+#include <cmath>
+
+#include "mg.cuh"
+
+namespace dwf {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string &m) { g_last_error = m; }
+const char *last_error() { return g_last_error.c_str(); }
+
+namespace {
+
+constexpr int SLOT_A = 0;  // scalar slots used by the solvers (double index)
+
+template <typename R> DevBuf &Qbuf(Level &L);
+template <> DevBuf &Qbuf<double>(Level &L) { return L.Q64; }
+template <> DevBuf &Qbuf<float>(Level &L) { return L.Q32; }
+
+template <typename R> std::vector<DevBuf> &wsv(MGState &mg, int l);
+template <> std::vector<DevBuf> &wsv<double>(MGState &mg, int l) { return mg.ws64[l]; }
+template <> std::vector<DevBuf> &wsv<float>(MGState &mg, int l) { return mg.ws32[l]; }
+
+struct GcrInfo {
+    int iters = 0;
+    double rel = 0.0;
+};
+
+template <typename R> class Runner {
+  public:
+    using T = C<R>;
+    dwf_ctx *c;
+    MGState &mg;
+    long long coarse_applies[MAX_LEVELS] = {0, 0, 0, 0};
+
+    Runner(dwf_ctx *ctx, MGState &m) : c(ctx), mg(m) {}
+
+    int64_t n(int l) const { return mg.lev[l].lg.nelem; }
+
+    // workspace vector i of level l
+    T *ws(int l, int i) {
+        auto &v = wsv<R>(mg, l);
+        if ((int)v.size() <= i) v.resize(i + 1);
+        if (!v[i].p) v[i].alloc(sizeof(T) * n(l));
+        return v[i].template as<T>();
+    }
+
+    T *Q(int l) { return Qbuf<R>(mg.lev[l]).template as<T>(); }
+
+    void apply(int l, T *out, const T *in, bool dag) {
+        if (l == 0) {
+            dslash(c, out, in, dag, 1);
+        } else {
+            coarse_apply<R>(c, mg.lev[l], out, in, dag);
+            coarse_applies[l]++;
+        }
+    }
+
+    double norm2(int l, const T *x) {
+        bnorm2<T>(c, SLOT_A, x, n(l));
+        double v = read_scalar(c, SLOT_A);
+        if (!std::isfinite(v)) throw Error{DWF_ENAN, "NaN or Inf in a norm"};
+        return v;
+    }
+    double2 dot(int l, const T *x, const T *y) {
+        bdot<T, T>(c, SLOT_A, x, y, n(l));
+        double v[2];
+        read_scalars(c, SLOT_A, 2, v);
+        return make_double2(v[0], v[1]);
+    }
+
+    // nu CGNR iterations on A_l x = b.  x_zero: start from x = 0 (else from x).
+    // b_zero: b = 0 (the adaptive setup's A x = 0).
+    void cgnr(int l, T *x, const T *b, int iters, bool x_zero, bool b_zero) {
+        const int64_t N = n(l);
+        T *r = ws(l, 0), *z = ws(l, 1), *p = ws(l, 2), *w = ws(l, 3);
+        if (x_zero) {
+            bzero<T>(c, x, N);
+            if (b_zero) return;
+            bcopy<T, T>(c, r, b, N);
+        } else {
+            apply(l, r, x, false);
+            if (b_zero) rscale<T>(c, r, -1.0, N);
+            else cxpay<T>(c, r, make_double2(-1.0, 0.0), b, N);  // r = b - A x
+        }
+        apply(l, z, r, true);
+        bcopy<T, T>(c, p, z, N);
+        double zz = norm2(l, z);
+        for (int it = 0; it < iters && zz > 0.0; ++it) {
+            apply(l, w, p, false);
+            double ww = norm2(l, w);
+            if (!(ww > 0.0)) break;
+            double a = zz / ww;
+            caxpy<T>(c, x, make_double2(a, 0), p, N);
+            caxpy<T>(c, r, make_double2(-a, 0), w, N);
+            if (it + 1 == iters) break;
+            apply(l, z, r, true);
+            double zz2 = norm2(l, z);
+            cxpay<T>(c, p, make_double2(zz2 / zz, 0), z, N);  // p = z + beta p
+            zz = zz2;
+        }
+    }
+
+    // Flexible GCR on level l, right-preconditioned by the V-cycle of level l
+    // when pc is set.  Modified Gram-Schmidt on the stored directions as in
+    // the oracle, done as classical Gram-Schmidt twice (same span, FP64 dots).
+    GcrInfo gcr(int l, T *x, const T *b, double tol, int maxit, int restart, bool pc, bool x_zero, bool b_zero) {
+        const int64_t N = n(l);
+        DWF_REQUIRE(restart >= 1 && restart <= 32, DWF_EINVAL, "GCR restart must be in 1..32");
+        T *r = ws(l, 10);
+        std::vector<T *> Z(restart), W(restart);
+        for (int i = 0; i < restart; ++i) {
+            Z[i] = ws(l, 16 + i);
+            W[i] = ws(l, 16 + restart + i);
+        }
+        double bnorm = b_zero ? 0.0 : std::sqrt(norm2(l, b));
+        if (bnorm == 0.0) {
+            if (x_zero) {
+                bzero<T>(c, x, N);
+                return GcrInfo{0, 0.0};
+            }
+            bnorm = 1.0;  // A x = 0 from a nonzero start: absolute residual
+        }
+        auto residual = [&]() {
+            if (x_zero) {
+                bcopy<T, T>(c, r, b, N);
+                x_zero = false;
+                return;
+            }
+            apply(l, r, x, false);
+            if (b_zero) rscale<T>(c, r, -1.0, N);
+            else cxpay<T>(c, r, make_double2(-1.0, 0.0), b, N);
+        };
+        if (x_zero) bzero<T>(c, x, N);
+        residual();
+        double rn = std::sqrt(norm2(l, r));
+        GcrInfo info;
+        int k = 0;
+        std::vector<double2> beta(restart);
+        while (info.iters < maxit && rn > tol * bnorm) {
+            if (pc) vcycle(l, Z[k], r);
+            else bcopy<T, T>(c, Z[k], r, N);
+            apply(l, W[k], Z[k], false);
+            for (int pass = 0; pass < 2 && k > 0; ++pass) {
+                for (int i = 0; i < k; ++i) bdot<T, T>(c, SLOT_A + 2 * i, W[i], W[k], N);
+                std::vector<double> v(2 * k);
+                read_scalars(c, SLOT_A, 2 * k, v.data());
+                for (int i = 0; i < k; ++i) beta[i] = make_double2(-v[2 * i], -v[2 * i + 1]);
+                multiaxpy<T>(c, W[k], beta.data(), W.data(), k, N);
+                multiaxpy<T>(c, Z[k], beta.data(), Z.data(), k, N);
+            }
+            bnorm2<T>(c, SLOT_A, W[k], N);
+            bdot<T, T>(c, SLOT_A + 2, W[k], r, N);
+            double s[4];
+            read_scalars(c, SLOT_A, 4, s);
+            double ww = s[0];
+            if (!std::isfinite(ww) || !std::isfinite(s[2])) throw Error{DWF_ENAN, "NaN or Inf in GCR"};
+            if (!(ww > 0.0)) break;
+            double inv = 1.0 / std::sqrt(ww);
+            rscale<T>(c, W[k], inv, N);
+            rscale<T>(c, Z[k], inv, N);
+            double2 alpha = make_double2(s[2] * inv, s[3] * inv);  // <w_unit, r>
+            caxpy<T>(c, x, alpha, Z[k], N);
+            caxpy<T>(c, r, make_double2(-alpha.x, -alpha.y), W[k], N);
+            double r2 = rn * rn - (alpha.x * alpha.x + alpha.y * alpha.y);
+            rn = r2 > 0 ? std::sqrt(r2) : 0.0;
+            ++info.iters;
+            ++k;
+            if (k == restart || rn <= tol * bnorm) {
+                residual();
+                rn = std::sqrt(norm2(l, r));
+                k = 0;
+            }
+        }
+        info.rel = rn / bnorm;
+        return info;
+    }
+
+    // One V-cycle for A_l x = b (Sec. 2):
+    //   x1 = S1^nu1(A, b); b2 = R(b - A x1); x2 = S2(R A P, b2);
+    //   b3 = b - A(P x2 + x1); x = x1 + P x2 + S3^nu3(A, b3)
+    void vcycle(int l, T *x, const T *b) {
+        const int64_t N = n(l);
+        Level &L = mg.lev[l];
+        const mg_params &p = mg.p;
+        T *res = ws(l, 4), *sm = ws(l, 5), *b3 = ws(l, 6);
+        T *b2 = ws(l + 1, 8), *x2 = ws(l + 1, 9);
+        if (p.nu_pre > 0) {
+            cgnr(l, x, b, p.nu_pre, true, false);
+            apply(l, res, x, false);
+            cxpay<T>(c, res, make_double2(-1.0, 0.0), b, N);  // b - A x1
+            restrict_<R>(c, L, b2, res, Q(l));
+        } else {
+            restrict_<R>(c, L, b2, b, Q(l));
+        }
+        coarse_solve(l + 1, x2, b2);
+        prolong_<R>(c, L, x, x2, Q(l), p.nu_pre > 0);
+        if (p.nu_post > 0) {
+            apply(l, res, x, false);
+            bcopy<T, T>(c, b3, b, N);
+            caxpy<T>(c, b3, make_double2(-1.0, 0.0), res, N);
+            cgnr(l, sm, b3, p.nu_post, true, false);
+            caxpy<T>(c, x, make_double2(1.0, 0.0), sm, N);
+        }
+    }
+
+    void coarse_solve(int l, T *x, const T *b) {
+        const mg_params &p = mg.p;
+        bool coarsest = (l == mg.nlevels - 1);
+        gcr(l, x, b, coarsest ? p.coarsest_tol : p.coarse_tol, coarsest ? p.coarsest_maxiter : p.coarse_maxiter,
+            p.coarse_restart, !coarsest, true, false);
+    }
+
+    // normalise x (level l) and store it as FP64 into dst
+    void store_normalised(int l, double2 *dst, const T *x) {
+        double nn = std::sqrt(norm2(l, x));
+        DWF_REQUIRE(nn > 0.0, DWF_EBREAKDOWN, "adaptive setup produced a zero vector");
+        bcopy<double2, T>(c, dst, x, n(l));
+        rscale<double2>(c, dst, 1.0 / nn, n(l));
+    }
+
+    // block Gram-Schmidt, basis copies and the coarse operator of level l+1
+    void build(int l) {
+        Level &L = mg.lev[l];
+        const int64_t N = n(l);
+        gamma_split<double>(c, L, L.Q64.as<double2>(), L.vec64.as<double2>(), L.nadapt, mg.p.split != 0);
+        if (!block_orthonormalise<double>(c, L, L.Q64.as<double2>()))
+            throw Error{DWF_EBREAKDOWN, "block Gram-Schmidt met linearly dependent near-null vectors"};
+        if (std::is_same<R, float>::value) bcopy<float2, double2>(c, L.Q32.as<float2>(), L.Q64.as<double2>(), N * L.nv);
+        DevBuf W(sizeof(double2) * N * L.nv);
+        build_coarse_from(c, L, mg.lev[l + 1], W.as<double2>());
+        mg.nlevels = l + 2;
+        DWF_CUDA(cudaStreamSynchronize(c->stream));
+    }
+
+    void setup_level(int l, const void *start, bool start_on_host) {
+        Level &L = mg.lev[l];
+        const mg_params &p = mg.p;
+        const int64_t N = n(l);
+        L.vec64.alloc(sizeof(double2) * N * L.nadapt);
+        L.Q64.alloc(sizeof(double2) * N * L.nv);
+        if (std::is_same<R, float>::value) L.Q32.alloc(sizeof(float2) * N * L.nv);
+        double2 *v = L.vec64.as<double2>();
+        if (l == 0 && start) {
+            DevBuf canon(sizeof(double2) * N * L.nadapt);
+            DWF_CUDA(cudaMemcpyAsync(canon.p, start, canon.bytes,
+                                     start_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+            pack(c, v, canon.as<double2>(), DWF_F64, L.nadapt);
+            DWF_CUDA(cudaStreamSynchronize(c->stream));
+        } else {
+            gauss_fill<double2>(c, v, L.nadapt, N, L.lg.g.Ls, L.lg.g.V, l == 0, p.seed + (uint32_t)l, 4u);
+        }
+        // start vectors: CGNR on A x = 0 from each random vector
+        T *xv = ws(l, 9);
+        for (int j = 0; j < L.nadapt; ++j) {
+            bcopy<T, double2>(c, xv, v + (int64_t)j * N, N);
+            cgnr(l, xv, nullptr, p.setup_iters0, false, true);
+            store_normalised(l, v + (int64_t)j * N, xv);
+        }
+        build(l);
+        // sweeps: the current multigrid applied to A x = 0 from each vector
+        for (int sw = 0; sw < p.setup_sweeps; ++sw) {
+            for (int j = 0; j < L.nadapt; ++j) {
+                bcopy<T, double2>(c, xv, v + (int64_t)j * N, N);
+                gcr(l, xv, nullptr, 0.0, p.setup_sweep_iters, p.setup_sweep_iters + 1, true, false, true);
+                store_normalised(l, v + (int64_t)j * N, xv);
+            }
+            build(l);
+        }
+    }
+
+    // Outer flexible GCR in FP64: each cycle solves A e = r approximately with
+    // up to `restart` V-cycle-preconditioned GCR iterations in precision R,
+    // then x += e and r = b - D x is recomputed in FP64 (reliable update).
+    dwf_status solve_one(double2 *b, double2 *x, double tol, mg_stats &st) {
+        const mg_params &p = mg.p;
+        const int64_t N = n(0);
+        double2 *r64 = mg_ws64(0, 12), *t64 = mg_ws64(0, 13);
+        bnorm2<double2>(c, SLOT_A, b, N);
+        double bn = std::sqrt(read_scalar(c, SLOT_A));
+        if (bn == 0.0) {
+            bzero<double2>(c, x, N);
+            st.true_res = 0.0;
+            return DWF_OK;
+        }
+        auto true_residual = [&]() {
+            dslash(c, t64, x, false, 1);
+            bcopy<double2, double2>(c, r64, b, N);
+            caxpy<double2>(c, r64, make_double2(-1.0, 0.0), t64, N);
+            bnorm2<double2>(c, SLOT_A, r64, N);
+            double v = read_scalar(c, SLOT_A);
+            if (!std::isfinite(v)) throw Error{DWF_ENAN, "NaN or Inf in the residual"};
+            return std::sqrt(v);
+        };
+        double rn = true_residual();
+        int iters = 0;
+        dwf_status status = DWF_OK;
+        T *bR = ws(0, 8), *eR = ws(0, 9);
+        const double floor_rel = std::is_same<R, float>::value ? 2e-6 : 0.0;
+        while (rn > tol * bn) {
+            if (iters >= p.outer_maxiter) {
+                status = DWF_ENOCONV;
+                break;
+            }
+            bcopy<T, double2>(c, bR, r64, N);
+            double tin = std::max(tol * bn / rn, floor_rel);
+            GcrInfo gi = gcr(0, eR, bR, tin, std::min(p.outer_restart, p.outer_maxiter - iters), p.outer_restart + 1,
+                             true, true, false);
+            if (gi.iters == 0) {
+                status = DWF_EBREAKDOWN;
+                break;
+            }
+            iters += gi.iters;
+            st.restarts++;
+            caxpy_mixed<double2, T>(c, x, make_double2(1.0, 0.0), eR, N);
+            rn = true_residual();
+        }
+        st.iters += iters;
+        st.true_res = std::max(st.true_res, rn / bn);
+        return status;
+    }
+
+    double2 *mg_ws64(int l, int i) {
+        auto &v = mg.ws64[l];
+        if ((int)v.size() <= i) v.resize(i + 1);
+        if (!v[i].p) v[i].alloc(sizeof(double2) * n(l));
+        return v[i].as<double2>();
+    }
+};
+
+template <typename R>
+dwf_status setup_t(dwf_ctx *c, MGState &mg, int levels, const void *start, bool start_on_host) {
+    Runner<R> run(c, mg);
+    mg.nlevels = 1;
+    for (int l = 0; l + 1 < levels; ++l) run.setup_level(l, start, start_on_host);
+    return DWF_OK;
+}
+
+template <typename R>
+dwf_status solve_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, int nrhs, mg_stats &st) {
+    Runner<R> run(c, mg);
+    dwf_status worst = DWF_OK;
+    const int64_t N = mg.lev[0].lg.nelem;
+    for (int r = 0; r < nrhs; ++r) {
+        dwf_status s = run.solve_one(b + r * N, x + r * N, tol, st);
+        if (s != DWF_OK && worst == DWF_OK) worst = s;
+    }
+    for (int l = 0; l < MAX_LEVELS; ++l) st.coarse_applies[l] += run.coarse_applies[l];
+    return worst;
+}
+
+bool nv_supported(int nv) {
+    switch (nv) {
+        case 2: case 4: case 6: case 8: case 12: case 16: case 24: case 32: return true;
+        default: return false;
+    }
+}
+
+}  // namespace
+
+int mg_nlevels_minus1(dwf_ctx *c) { return c->mg ? c->mg->nlevels - 1 : 0; }
+
+void mg_free(dwf_ctx *c) {
+    delete c->mg;
+    c->mg = nullptr;
+}
+
+dwf_status mg_setup_impl(dwf_ctx *c, int levels, const int *nvec, const int (*block)[4], const mg_params &p,
+                         const void *start, bool start_on_host) {
+    mg_free(c);
+    DWF_REQUIRE(p.smoother_prec == DWF_F64 || p.smoother_prec == DWF_F32, DWF_EINVAL, "smoother_prec must be F64 or F32");
+    DWF_REQUIRE(p.nu_post >= 0 && p.nu_pre >= 0 && p.coarse_restart >= 1 && p.coarse_restart <= 32 &&
+                    p.outer_restart >= 1 && p.outer_restart <= 31 && p.setup_sweep_iters >= 1 &&
+                    p.setup_sweep_iters <= 31,
+                DWF_EINVAL, "iteration parameters out of range");
+    MGState *mg = new MGState();
+    mg->p = p;
+    std::memset(&mg->stats, 0, sizeof(mg->stats));
+    Level &L0 = mg->lev[0];
+    L0.index = 0;
+    L0.lg.g = c->g;
+    L0.lg.ncomp = 12;
+    L0.lg.nelem = c->g.V * 12 * c->g.Ls;
+    for (int l = 0; l + 1 < levels; ++l) {
+        Level &L = mg->lev[l];
+        Level &Lc = mg->lev[l + 1];
+        bool ok = nv_supported(nvec[l]) && (!p.split || nvec[l] % 2 == 0);
+        for (int i = 0; i < 4; ++i) ok = ok && block[l][i] >= 1 && L.lg.g.L[i] % block[l][i] == 0;
+        if (!ok) {
+            delete mg;
+            return DWF_EINVAL;
+        }
+        for (int i = 0; i < 4; ++i) L.block[i] = block[l][i];
+        L.nv = nvec[l];
+        L.nadapt = p.split ? nvec[l] / 2 : nvec[l];
+        Lc.index = l + 1;
+        Lc.lg.g.ap = 0;
+        Lc.lg.g.Ls = 1;
+        for (int i = 0; i < 4; ++i) Lc.lg.g.L[i] = L.lg.g.L[i] / block[l][i];
+        Lc.lg.g.V = (int64_t)Lc.lg.g.L[0] * Lc.lg.g.L[1] * Lc.lg.g.L[2] * Lc.lg.g.L[3];
+        Lc.lg.ncomp = nvec[l];
+        Lc.lg.nelem = Lc.lg.g.V * nvec[l];
+        dwf_prec yp = p.coarse_prec[l];
+        Lc.yprec = (yp == DWF_F32 || yp == DWF_BF16 || yp == DWF_F16) ? yp : DWF_F64;
+    }
+    c->mg = mg;
+    try {
+        if (p.smoother_prec == DWF_F32) setup_t<float>(c, *mg, levels, start, start_on_host);
+        else setup_t<double>(c, *mg, levels, start, start_on_host);
+    } catch (...) {
+        mg_free(c);
+        throw;
+    }
+    return DWF_OK;
+}
+
+dwf_status mg_solve_impl(dwf_ctx *c, const void *b, void *x, double tol, int nrhs, mg_stats *stats, bool host) {
+    if (!c->mg || c->mg->nlevels < 2) return DWF_ESTATE;
+    MGState &mg = *c->mg;
+    auto t0 = std::chrono::steady_clock::now();
+    mg_stats st;
+    std::memset(&st, 0, sizeof(st));
+    long long a64 = c->applies64, a32 = c->applies32;
+    const int64_t N = mg.lev[0].lg.nelem;
+    DevBuf bd, xd;
+    double2 *bp = (double2 *)b, *xp = (double2 *)x;
+    if (host) {
+        bd.alloc(sizeof(double2) * N * nrhs);
+        xd.alloc(sizeof(double2) * N * nrhs);
+        DWF_CUDA(cudaMemcpyAsync(bd.p, b, bd.bytes, cudaMemcpyDefault, c->stream));
+        DWF_CUDA(cudaMemcpyAsync(xd.p, x, xd.bytes, cudaMemcpyDefault, c->stream));
+        bp = bd.as<double2>();
+        xp = xd.as<double2>();
+    }
+    dwf_status s = (mg.p.smoother_prec == DWF_F32) ? solve_t<float>(c, mg, bp, xp, tol, nrhs, st)
+                                                   : solve_t<double>(c, mg, bp, xp, tol, nrhs, st);
+    if (host) DWF_CUDA(cudaMemcpyAsync(x, xd.p, xd.bytes, cudaMemcpyDefault, c->stream));
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+    st.fine_applies_f64 = c->applies64 - a64;
+    st.fine_applies_f32 = c->applies32 - a32;
+    st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = st;
+    return s;
+}
+
+namespace {
+MGState &need_mg(dwf_ctx *c, int level, int lo, int hi_excl) {
+    DWF_REQUIRE(c->mg && c->mg->nlevels >= 2, DWF_ESTATE, "mg_setup has not completed");
+    DWF_REQUIRE(level >= lo && level < hi_excl && level < c->mg->nlevels, DWF_EINVAL, "level out of range");
+    return *c->mg;
+}
+}  // namespace
+
+void mg_level_info_impl(dwf_ctx *c, int level, int dims[4], int *ncomp) {
+    MGState &mg = need_mg(c, level, 0, MAX_LEVELS);
+    for (int i = 0; i < 4; ++i) dims[i] = mg.lev[level].lg.g.L[i];
+    *ncomp = mg.lev[level].lg.ncomp;
+}
+
+void mg_get_vectors_impl(dwf_ctx *c, int level, double2 *out) {
+    MGState &mg = need_mg(c, level, 0, mg_nlevels_minus1(c));
+    const Level &L = mg.lev[level];
+    DWF_CUDA(cudaMemcpyAsync(out, L.Q64.p, sizeof(double2) * L.lg.nelem * L.nv, cudaMemcpyDeviceToDevice, c->stream));
+}
+
+void mg_get_coarse_links_impl(dwf_ctx *c, int level, double2 *out) {
+    MGState &mg = need_mg(c, level, 1, MAX_LEVELS);
+    const Level &L = mg.lev[level];
+    DWF_CUDA(cudaMemcpyAsync(out, L.Y64.p, sizeof(double2) * L.lg.g.V * 9 * L.lg.ncomp * L.lg.ncomp,
+                             cudaMemcpyDeviceToDevice, c->stream));
+}
+
+void mg_restrict_impl(dwf_ctx *c, int level, double2 *cout, const double2 *fin) {
+    MGState &mg = need_mg(c, level, 0, mg_nlevels_minus1(c));
+    restrict_<double>(c, mg.lev[level], cout, fin, mg.lev[level].Q64.as<double2>());
+}
+
+void mg_prolong_impl(dwf_ctx *c, int level, double2 *fout, const double2 *cin) {
+    MGState &mg = need_mg(c, level, 0, mg_nlevels_minus1(c));
+    prolong_<double>(c, mg.lev[level], fout, cin, mg.lev[level].Q64.as<double2>(), false);
+}
+
+void mg_coarse_apply_impl(dwf_ctx *c, int level, void *out, const void *in, bool dag, dwf_prec prec) {
+    MGState &mg = need_mg(c, level, 1, MAX_LEVELS);
+    DWF_REQUIRE(prec == DWF_F64 || prec == DWF_F32, DWF_EINVAL, "field precision must be F64 or F32");
+    if (prec == DWF_F64) coarse_apply<double>(c, mg.lev[level], (double2 *)out, (const double2 *)in, dag);
+    else coarse_apply<float>(c, mg.lev[level], (float2 *)out, (const float2 *)in, dag);
+}
+
+namespace {
+template <typename R> void vcycle_t(dwf_ctx *c, MGState &mg, double2 *x, const double2 *b) {
+    Runner<R> run(c, mg);
+    const int64_t N = mg.lev[0].lg.nelem;
+    C<R> *bR = run.ws(0, 8), *xR = run.ws(0, 9);
+    bcopy<C<R>, double2>(c, bR, b, N);
+    run.vcycle(0, xR, bR);
+    bcopy<double2, C<R>>(c, x, xR, N);
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+}
+}  // namespace
+
+void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b) {
+    MGState &mg = need_mg(c, 0, 0, 1);
+    if (mg.p.smoother_prec == DWF_F32) vcycle_t<float>(c, mg, x, b);
+    else vcycle_t<double>(c, mg, x, b);
+}
+
+}  // namespace dwf

@@ -1,0 +1,95 @@
+// Multigrid internals: per-level data, transfer and coarse-operator kernels,
+// solver entry points.
+#pragma once
+
+#include "dwf_internal.cuh"
+
+namespace dwf {
+
+void set_last_error(const std::string &m);
+const char *last_error();
+
+constexpr int MAX_LEVELS = 4;
+
+// A field on one level: V sites x ncomp components x Ls (fine: ncomp = 12,
+// Ls = Ls; coarse: ncomp = Nvec, Ls = 1), element (site*ncomp + comp)*Ls + s.
+struct LevelGeom {
+    Geom g;        // g.Ls = 1 on coarse levels
+    int ncomp;     // components per site and s
+    int64_t nelem; // complex elements per field
+};
+
+struct Level {
+    int index = 0;         // 0 = fine lattice
+    LevelGeom lg;
+    // transfer to level + 1 (absent on the coarsest level)
+    int block[4] = {1, 1, 1, 1};
+    int nv = 0;            // coarse components per site of level + 1
+    int nadapt = 0;        // adaptive vectors (nv / 2 when split)
+    DevBuf Q64, Q32;       // nv block-orthonormalised fields of this level
+    DevBuf vec64;          // nadapt adaptive vectors (unsplit, normalised), FP64
+    // coarse operator of this level (levels >= 1): [V][9][n][n] complex
+    DevBuf Y64, Y32, Y16;  // Y16 holds bf16 or fp16 pairs per coarse_prec
+    dwf_prec yprec = DWF_F64;
+    // block reductions scratch: [Vc][nv][nv] complex FP64
+    DevBuf G, F, Rinv;
+    DevBuf info;           // int per coarse site: Cholesky status
+};
+
+struct MGState {
+    int nlevels = 0;
+    mg_params p;
+    Level lev[MAX_LEVELS];
+    // workspaces (allocated lazily by precision)
+    std::vector<DevBuf> ws64[MAX_LEVELS], ws32[MAX_LEVELS];
+    mg_stats stats;
+};
+
+void mg_free(dwf_ctx *c);
+int mg_nlevels_minus1(dwf_ctx *c);
+dwf_status mg_setup_impl(dwf_ctx *c, int levels, const int *nvec, const int (*block)[4], const mg_params &p,
+                         const void *start, bool start_on_host);
+dwf_status mg_solve_impl(dwf_ctx *c, const void *b, void *x, double tol, int nrhs, mg_stats *stats, bool host);
+// component calls of the C ABI (see dwfmg.h); throw Error on bad arguments
+void mg_level_info_impl(dwf_ctx *c, int level, int dims[4], int *ncomp);
+void mg_get_vectors_impl(dwf_ctx *c, int level, double2 *out);
+void mg_get_coarse_links_impl(dwf_ctx *c, int level, double2 *out);
+void mg_restrict_impl(dwf_ctx *c, int level, double2 *cout, const double2 *fin);
+void mg_prolong_impl(dwf_ctx *c, int level, double2 *fout, const double2 *cin);
+void mg_coarse_apply_impl(dwf_ctx *c, int level, void *out, const void *in, bool dag, dwf_prec prec);
+void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b);
+
+// ---- transfer.cu ----
+// c[Vc][nv] = R f  (R = P^+) ; f = P c (accumulate: f += P c)
+template <typename R> void restrict_(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const C<R> *Q);
+template <typename R> void prolong_(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const C<R> *Q, bool accumulate);
+// G[Vc][nv][nv] = block inner products <A_k, B_l> over each block (FP64 accumulate)
+template <typename R> void block_gram(dwf_ctx *c, const Level &L, double2 *G, const C<R> *A, const C<R> *B);
+// In-place block orthonormalisation of the nv fields Q (CholQR2, FP64); returns false on breakdown
+template <typename R> bool block_orthonormalise(dwf_ctx *c, Level &L, C<R> *Q);
+// Q[2j] = (1 + Gamma)/2 v_j, Q[2j+1] = (1 - Gamma)/2 v_j  (Gamma = g5 R5 on the fine level,
+// +-1 on even/odd components of a coarse level); split = false copies v_j to Q[j]
+template <typename R> void gamma_split(dwf_ctx *c, const Level &L, C<R> *Q, const double2 *v, int nadapt, bool split);
+
+// ---- coarse.cu ----
+// y = A_l c on coarse level l (l >= 1), or A_l^+ c
+template <typename R> void coarse_apply(dwf_ctx *c, const Level &L, C<R> *y, const C<R> *x, bool dag);
+// Build the Galerkin coarse operator Y of level Lc = l+1 from level L's FP64
+// basis Q64 (W: scratch of L.nv fields of level L, FP64)
+void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, double2 *W);
+// refresh the reduced-precision copies of Y on level l
+void convert_coarse_links(dwf_ctx *c, Level &L);
+
+// ---- blas2.cu ----  (host scalars; FP64 accumulate inside reductions)
+template <typename T> void caxpy(dwf_ctx *c, T *y, double2 a, const T *x, int64_t n);       // y += a x
+template <typename T> void cxpay(dwf_ctx *c, T *y, double2 a, const T *x, int64_t n);       // y = x + a y
+template <typename T> void rscale(dwf_ctx *c, T *x, double a, int64_t n);                   // x *= a
+// y_out(T) += a * x(U) with precision conversion (x may be another precision)
+template <typename T, typename U> void caxpy_mixed(dwf_ctx *c, T *y, double2 a, const U *x, int64_t n);
+// w += sum_i beta_i V_i, k <= 32 (pointers and coefficients from the host)
+template <typename T> void multiaxpy(dwf_ctx *c, T *w, const double2 *beta, T *const *V, int k, int64_t n);
+// x = a * x + b * y (real a, complex b) fused for two pairs: used by GCR updates
+template <typename T> void gauss_fill(dwf_ctx *c, double2 *out, int nfields, int64_t nelem, int Ls, int64_t V,
+                                      bool canonical_fine, uint32_t seed, uint32_t stream);
+
+}  // namespace dwf

@@ -1,0 +1,237 @@
+"""Python binding of the dwfmg C ABI (include/dwfmg.h).
+
+Argument marshalling only: every computation runs in the CUDA library
+libdwfmg.so.  The functions keep the C names; arrays are torch tensors
+(device or host) or numpy arrays (host), passed by pointer.  If the library
+is missing the import of this module fails loudly: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+
+_PKG = pathlib.Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libdwfmg.so"
+
+DWF_OK, DWF_EINVAL, DWF_ECUDA, DWF_ENOMEM, DWF_ENOCONV, DWF_EBREAKDOWN, DWF_ENAN, DWF_ETIMEOUT, DWF_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+DWF_F64, DWF_F32, DWF_BF16, DWF_F16 = 0, 1, 2, 3
+
+
+class mg_params(ctypes.Structure):
+    _fields_ = [
+        ("nu_pre", ctypes.c_int),
+        ("nu_post", ctypes.c_int),
+        ("coarse_tol", ctypes.c_double),
+        ("coarse_maxiter", ctypes.c_int),
+        ("coarsest_tol", ctypes.c_double),
+        ("coarsest_maxiter", ctypes.c_int),
+        ("coarse_restart", ctypes.c_int),
+        ("outer_restart", ctypes.c_int),
+        ("outer_maxiter", ctypes.c_int),
+        ("setup_iters0", ctypes.c_int),
+        ("setup_sweeps", ctypes.c_int),
+        ("setup_sweep_iters", ctypes.c_int),
+        ("split", ctypes.c_int),
+        ("smoother_prec", ctypes.c_int),
+        ("coarse_prec", ctypes.c_int * 4),
+        ("seed", ctypes.c_uint32),
+    ]
+
+
+class mg_stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("fine_applies_f64", ctypes.c_longlong),
+        ("fine_applies_f32", ctypes.c_longlong),
+        ("coarse_applies", ctypes.c_longlong * 4),
+        ("true_res", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {"iters": self.iters, "restarts": self.restarts, "fine_applies_f64": self.fine_applies_f64,
+                "fine_applies_f32": self.fine_applies_f32, "coarse_applies": list(self.coarse_applies),
+                "true_res": self.true_res, "seconds": self.seconds}
+
+
+class DWFError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.dwf_strerror(status).decode()
+        detail = _lib.dwf_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status})" + (f": {detail}" if detail else ""))
+
+
+def _load():
+    if not LIB_PATH.exists():
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1205_2933_gb300.build.build() "
+                          "(the library has no CPU fallback)")
+    L = ctypes.CDLL(str(LIB_PATH))
+    vp, ip, st, i = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int
+    L.mg_default_params.argtypes = [ctypes.POINTER(mg_params)]
+    L.mg_default_params.restype = None
+    L.dwf_strerror.argtypes = [st]
+    L.dwf_strerror.restype = ctypes.c_char_p
+    L.dwf_last_error.argtypes = []
+    L.dwf_last_error.restype = ctypes.c_char_p
+    L.dwf_create.argtypes = [ctypes.POINTER(vp), ip, i, ctypes.c_double, ctypes.c_double, vp, i, vp]
+    L.dwf_destroy.argtypes = [vp]
+    L.dwf_destroy.restype = None
+    L.dwf_apply.argtypes = [vp, vp, vp, st, i, i]
+    L.dwf_pack.argtypes = [vp, vp, vp, st, i]
+    L.dwf_unpack.argtypes = [vp, vp, vp, st, i]
+    L.mg_setup.argtypes = [vp, i, ip, ip, ctypes.POINTER(mg_params), vp]
+    L.mg_solve.argtypes = [vp, vp, vp, ctypes.c_double, i, ctypes.POINTER(mg_stats)]
+    L.mg_level_info.argtypes = [vp, i, ip, ip]
+    L.mg_get_vectors.argtypes = [vp, i, vp]
+    L.mg_get_coarse_links.argtypes = [vp, i, vp]
+    L.mg_restrict.argtypes = [vp, i, vp, vp]
+    L.mg_prolong.argtypes = [vp, i, vp, vp]
+    L.mg_coarse_apply.argtypes = [vp, i, vp, vp, i, st]
+    L.mg_vcycle.argtypes = [vp, vp, vp]
+    for name in ("dwf_create", "dwf_apply", "dwf_pack", "dwf_unpack", "mg_setup", "mg_solve", "mg_level_info",
+                 "mg_get_vectors", "mg_get_coarse_links", "mg_restrict", "mg_prolong", "mg_coarse_apply",
+                 "mg_vcycle"):
+        getattr(L, name).restype = st
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if hasattr(a, "ctypes"):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _check(status, where):
+    if status != DWF_OK:
+        raise DWFError(status, where)
+    return status
+
+
+def mg_default_params() -> mg_params:
+    p = mg_params()
+    _lib.mg_default_params(ctypes.byref(p))
+    return p
+
+
+def dwf_create(dims, Ls, M5, mf, links, antiperiodic_t=True, stream=None):
+    """Context handle (ctypes.c_void_p) for one lattice; links complex128 [V][4][3][3]."""
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    s = ctypes.c_void_p(int(stream)) if stream is not None else None
+    _check(_lib.dwf_create(ctypes.byref(h), d, int(Ls), float(M5), float(mf), _ptr(links),
+                           1 if antiperiodic_t else 0, s), "dwf_create")
+    return h
+
+
+def dwf_destroy(ctx):
+    _lib.dwf_destroy(ctx)
+
+
+def dwf_apply(ctx, out, inp, prec=DWF_F64, dagger=False, nrhs=1):
+    return _check(_lib.dwf_apply(ctx, _ptr(out), _ptr(inp), prec, 1 if dagger else 0, int(nrhs)), "dwf_apply")
+
+
+def dwf_pack(ctx, internal, canonical, prec=DWF_F64, nrhs=1):
+    return _check(_lib.dwf_pack(ctx, _ptr(internal), _ptr(canonical), prec, int(nrhs)), "dwf_pack")
+
+
+def dwf_unpack(ctx, canonical, internal, prec=DWF_F64, nrhs=1):
+    return _check(_lib.dwf_unpack(ctx, _ptr(canonical), _ptr(internal), prec, int(nrhs)), "dwf_unpack")
+
+
+def mg_setup(ctx, levels, nvec, block, params=None, start=None):
+    nv = (ctypes.c_int * (levels - 1))(*[int(v) for v in nvec])
+    bl = (ctypes.c_int * (4 * (levels - 1)))(*[int(b) for blk in block for b in blk])
+    p = ctypes.byref(params) if params is not None else None
+    return _check(_lib.mg_setup(ctx, int(levels), nv, bl, p, _ptr(start)), "mg_setup")
+
+
+def mg_solve(ctx, b, x, tol, nrhs=1, check=True) -> mg_stats:
+    st = mg_stats()
+    status = _lib.mg_solve(ctx, _ptr(b), _ptr(x), float(tol), int(nrhs), ctypes.byref(st))
+    if check:
+        _check(status, "mg_solve")
+    st.status = status
+    return st
+
+
+def mg_level_info(ctx, level):
+    d = (ctypes.c_int * 4)()
+    n = ctypes.c_int()
+    _check(_lib.mg_level_info(ctx, int(level), d, ctypes.byref(n)), "mg_level_info")
+    return tuple(d), n.value
+
+
+def mg_get_vectors(ctx, level, out):
+    return _check(_lib.mg_get_vectors(ctx, int(level), _ptr(out)), "mg_get_vectors")
+
+
+def mg_get_coarse_links(ctx, level, out):
+    return _check(_lib.mg_get_coarse_links(ctx, int(level), _ptr(out)), "mg_get_coarse_links")
+
+
+def mg_restrict(ctx, level, coarse_out, fine_in):
+    return _check(_lib.mg_restrict(ctx, int(level), _ptr(coarse_out), _ptr(fine_in)), "mg_restrict")
+
+
+def mg_prolong(ctx, level, fine_out, coarse_in):
+    return _check(_lib.mg_prolong(ctx, int(level), _ptr(fine_out), _ptr(coarse_in)), "mg_prolong")
+
+
+def mg_coarse_apply(ctx, level, out, inp, dagger=False, prec=DWF_F64):
+    return _check(_lib.mg_coarse_apply(ctx, int(level), _ptr(out), _ptr(inp), 1 if dagger else 0, prec),
+                  "mg_coarse_apply")
+
+
+def mg_vcycle(ctx, x, b):
+    return _check(_lib.mg_vcycle(ctx, _ptr(x), _ptr(b)), "mg_vcycle")
+
+
+class Context:
+    """Owns one dwf_ctx; fields are torch tensors in the library's internal layout."""
+
+    def __init__(self, dims, Ls, M5, mf, links, antiperiodic_t=True, stream=None):
+        import torch
+        self.dims = tuple(int(d) for d in dims)
+        self.Ls = int(Ls)
+        self.V = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self.h = dwf_create(dims, Ls, M5, mf, links, antiperiodic_t, stream)
+
+    @property
+    def field_elems(self):
+        return self.V * 12 * self.Ls
+
+    def close(self):
+        if self.h is not None:
+            dwf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,63 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads, and exports
+every function include/dwfmg.h declares (no compute calls without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "dwfmg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:dwf_status|void|const char\s*\*|char\s*\*)\s*\*?\s*(\w+)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1205_2933_gb300 import build as B
+    return str(B.build())
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dwf_create", "dwf_apply", "mg_setup", "mg_solve", "dwf_pack", "dwf_unpack",
+                     "dwf_strerror", "dwf_destroy", "mg_default_params"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_host_only_calls(libpath):
+    L = ctypes.CDLL(libpath)
+    L.dwf_strerror.restype = ctypes.c_char_p
+    assert L.dwf_strerror(0) == b"success"
+    assert b"converge" in L.dwf_strerror(-4)
+    from paper_1205_2933_gb300 import dwfmg as G
+    p = G.mg_default_params()
+    assert p.nu_post == 4 and p.split == 1 and p.outer_restart == 10
+    # invalid arguments are rejected before any device work
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(4, 4, 4, 4)
+    assert G.lib().dwf_create(ctypes.byref(h), d, 0, 1.8, 0.1, None, 1, None) == G.DWF_EINVAL
+    assert G.lib().dwf_apply(None, None, None, 0, 0, 1) == G.DWF_EINVAL
+
+
+def test_no_cpu_fallback_in_product_path():
+    """The package never imports the oracle (test infrastructure only)."""
+    pkg = os.path.join(ROOT, "paper_1205_2933_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".c", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f

@@ -1,0 +1,275 @@
+"""GPU parity of the multigrid steps (block Gram-Schmidt, R/P, the 9-point
+coarse operator, coarse stencil, V-cycle) and of whole solves, against the
+FP64 oracle on identical seeded inputs, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mg as OM
+import paper_1205_2933_gb300.inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1205_2933_gb300 import dwfmg
+    return dwfmg
+
+
+def _params(G, **kw):
+    p = G.mg_default_params()
+    for k, v in kw.items():
+        if k == "coarse_prec":
+            for i, x in enumerate(v):
+                p.coarse_prec[i] = x
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _oracle_params(nvec, block, **kw):
+    keys = {"nu_pre", "nu_post", "coarse_tol", "coarse_maxiter", "coarsest_tol", "coarsest_maxiter",
+            "coarse_restart", "setup_iters0", "setup_sweeps", "setup_sweep_iters", "split"}
+    return OM.MGParams(nvec=tuple(nvec), block=tuple(tuple(b) for b in block),
+                       **{k: v for k, v in kw.items() if k in keys})
+
+
+class Case:
+    """One lattice, its oracle, a GPU context and matching MG setups."""
+
+    def __init__(self, G, dims, Ls, mf, nvec, block, seed=1, eps=0.3, hb=False, **kw):
+        from gpu_util import ctx_for, to_internal
+        self.G, self.dims, self.Ls, self.nvec, self.block = G, dims, Ls, nvec, block
+        self.U = I.heatbath_links(dims, 6.0, 20, seed) if hb else I.epsilon_links(dims, eps, seed)
+        self.dwf = oracle.DWF(self.U, dims, Ls, 1.8, mf)
+        self.op = OM.FineOp(self.dwf)
+        self.ctx = ctx_for(self.U, dims, Ls, 1.8, mf)
+        na = nvec[0] // 2
+        self.start = I.random_vectors(na, dims, Ls, 3)
+        self.p = _params(G, **kw)
+        G.mg_setup(self.ctx.h, len(nvec) + 1, nvec, block, self.p, torch.from_numpy(self.start).cuda())
+        rv = [self.start.reshape((na,) + self.op.shape)]
+        for l in range(1, len(nvec)):
+            d, n = G.mg_level_info(self.ctx.h, l)
+            Vc = int(np.prod(d))
+            rv.append(I.gauss_complex((nvec[l] // 2, Vc * n), self.p.seed + l, I.STREAM_NULLVEC)
+                      .reshape(nvec[l] // 2, 1, d[3], d[2], d[1], d[0], n))
+        self.mg = OM.adaptive_setup(self.op, _oracle_params(nvec, block, **kw), rv)
+
+    def close(self):
+        self.ctx.close()
+
+
+SMALL = dict(dims=(4, 4, 4, 4), Ls=8, mf=0.1, nvec=[8], block=[(2, 2, 2, 2)])          # plain-method workload
+RAGGED = dict(dims=(4, 2, 6, 4), Ls=3, mf=0.05, nvec=[6], block=[(2, 2, 3, 2)])        # coarse 2x1x2x2
+
+
+@pytest.mark.parametrize("cfg", [SMALL, RAGGED], ids=["4^4xLs8", "ragged"])
+def test_basis_and_coarse_operator(G, cfg):
+    """No setup iterations: the GPU's block Gram-Schmidt of the same start
+    vectors and its 9-point R D P must equal the oracle's."""
+    c = Case(G, **cfg, setup_iters0=0, setup_sweeps=0)
+    from gpu_util import to_canonical, rel_max
+    nv = cfg["nvec"][0]
+    q = torch.empty(c.ctx.field_elems * nv, dtype=torch.complex128, device="cuda")
+    G.mg_get_vectors(c.ctx.h, 0, q)
+    got = to_canonical(c.ctx, q, (nv,) + c.op.shape, nrhs=nv)
+    T = c.mg.levels[0].transfer
+    ref = np.stack([T.vector(k) for k in range(nv)])
+    assert rel_max(got, ref) < 1e-12
+    d, n = G.mg_level_info(c.ctx.h, 1)
+    Vc = int(np.prod(d))
+    Y = torch.empty(Vc * 9 * n * n, dtype=torch.complex128, device="cuda")
+    G.mg_get_coarse_links(c.ctx.h, 1, Y)
+    Yref = c.mg.levels[1].op.Y.reshape(Vc, 9, n, n)
+    assert rel_max(Y.cpu().numpy().reshape(Vc, 9, n, n), Yref) < 1e-12
+    c.close()
+
+
+def test_device_philox_start_vectors(G):
+    """Without given start vectors the GPU draws them from its own Philox:
+    they must equal the host generator's (same counters) to rounding."""
+    from gpu_util import ctx_for, to_canonical, rel_max
+    dims, Ls = (4, 4, 4, 4), 4
+    U = I.epsilon_links(dims, 0.3, 1)
+    ctx = ctx_for(U, dims, Ls, 1.8, 0.1)
+    p = _params(G, setup_iters0=0, setup_sweeps=0, seed=9)
+    G.mg_setup(ctx.h, 2, [8], [(2, 2, 2, 2)], p)
+    op = OM.FineOp(oracle.DWF(U, dims, Ls, 1.8, 0.1))
+    rv = I.random_vectors(4, dims, Ls, 9).reshape((4,) + op.shape)
+    mg = OM.adaptive_setup(op, _oracle_params([8], [(2, 2, 2, 2)], setup_iters0=0, setup_sweeps=0), [rv])
+    q = torch.empty(ctx.field_elems * 8, dtype=torch.complex128, device="cuda")
+    G.mg_get_vectors(ctx.h, 0, q)
+    got = to_canonical(ctx, q, (8,) + op.shape, nrhs=8)
+    ref = np.stack([mg.levels[0].transfer.vector(k) for k in range(8)])
+    assert rel_max(got, ref) < 1e-12
+    ctx.close()
+
+
+def test_restrict_prolong_and_coarse_stencil(G):
+    c = Case(G, **SMALL, setup_iters0=5, setup_sweeps=0)
+    from gpu_util import to_internal, rel_max
+    T = c.mg.levels[0].transfer
+    A = c.mg.levels[1].op
+    d, n = G.mg_level_info(c.ctx.h, 1)
+    Vc = int(np.prod(d))
+    f = I.gaussian_source(c.dims, c.Ls, 21)
+    ft = to_internal(c.ctx, f)
+    co = torch.empty(Vc * n, dtype=torch.complex128, device="cuda")
+    G.mg_restrict(c.ctx.h, 0, co, ft)
+    ref = T.restrict(f.reshape(c.op.shape)).reshape(Vc, n)
+    assert rel_max(co.cpu().numpy().reshape(Vc, n), ref) < 1e-12
+    cin = I.gauss_complex((Vc * n,), 22, 50)
+    ct = torch.from_numpy(cin).cuda()
+    fo = torch.empty(c.ctx.field_elems, dtype=torch.complex128, device="cuda")
+    G.mg_prolong(c.ctx.h, 0, fo, ct)
+    from gpu_util import to_canonical
+    got = to_canonical(c.ctx, fo, f.shape)
+    assert rel_max(got, T.prolong(cin.reshape(T.cshape)).reshape(f.shape)) < 1e-13
+    for dag in (False, True):
+        yo = torch.empty_like(ct)
+        G.mg_coarse_apply(c.ctx.h, 1, yo, ct, dag, G.DWF_F64)
+        ref = (A.apply_dag if dag else A.apply)(cin.reshape(A.shape)).ravel()
+        assert rel_max(yo.cpu().numpy(), ref) < 1e-12
+    c.close()
+
+
+@pytest.mark.parametrize("lp,tol", [(1, 1e-6), (2, 1e-2), (3, 2e-3)], ids=["f32", "bf16", "f16"])
+def test_reduced_precision_coarse_stencil(G, lp, tol):
+    c = Case(G, **SMALL, setup_iters0=5, setup_sweeps=0, coarse_prec=[lp])
+    A = c.mg.levels[1].op
+    d, n = G.mg_level_info(c.ctx.h, 1)
+    cin = I.gauss_complex((int(np.prod(d)) * n,), 23, 50)
+    ct = torch.from_numpy(cin.astype(np.complex64)).cuda()
+    yo = torch.empty_like(ct)
+    G.mg_coarse_apply(c.ctx.h, 1, yo, ct, False, G.DWF_F32)
+    ref = A.apply(cin.reshape(A.shape)).ravel()
+    got = yo.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
+    c.close()
+
+
+def test_vcycle_parity(G):
+    c = Case(G, **SMALL, setup_iters0=10, setup_sweeps=0)
+    from gpu_util import to_internal, to_canonical, rel_norm
+    b = I.gaussian_source(c.dims, c.Ls, 31)
+    bt = to_internal(c.ctx, b)
+    xt = torch.empty_like(bt)
+    G.mg_vcycle(c.ctx.h, xt, bt)
+    got = to_canonical(c.ctx, xt, b.shape)
+    ref = c.mg.vcycle(0, b.reshape(c.op.shape)).reshape(b.shape)
+    assert rel_norm(got, ref) < 1e-9
+    c.close()
+
+
+def test_vcycle_galerkin_orthogonality(G):
+    """nu1 = nu3 = 0 and a tight coarse solve: R (b - D x) = 0 on the GPU."""
+    c = Case(G, **SMALL, setup_iters0=10, setup_sweeps=0, nu_post=0, coarsest_tol=1e-12,
+             coarsest_maxiter=500, coarse_restart=32)
+    from gpu_util import to_internal
+    b = I.gaussian_source(c.dims, c.Ls, 32)
+    bt = to_internal(c.ctx, b)
+    xt = torch.empty_like(bt)
+    G.mg_vcycle(c.ctx.h, xt, bt)
+    Dx = torch.empty_like(bt)
+    G.dwf_apply(c.ctx.h, Dx, xt)
+    d, n = G.mg_level_info(c.ctx.h, 1)
+    r1 = torch.empty(int(np.prod(d)) * n, dtype=torch.complex128, device="cuda")
+    r0 = torch.empty_like(r1)
+    G.mg_restrict(c.ctx.h, 0, r1, (bt - Dx).contiguous())
+    G.mg_restrict(c.ctx.h, 0, r0, bt)
+    assert (r1.abs().max() / r0.abs().max()).item() < 1e-10
+    c.close()
+
+
+def _oracle_solution(c, b):
+    x, info = OM.cgnr(c.op.apply, c.op.apply_dag, b.reshape(c.op.shape), tol=1e-13, maxiter=50000)
+    assert info.converged
+    return x.reshape(b.shape)
+
+
+def test_solve_fp64_matches_oracle(G):
+    """Plain FP64 method: same setup and solve as the oracle; solution within
+    1e-8, FP64 true residual <= 1e-10, outer iterations within 2."""
+    c = Case(G, **SMALL, setup_sweeps=1)
+    from gpu_util import to_internal, to_canonical, rel_norm
+    b = I.gaussian_source(c.dims, c.Ls, 2)
+    bt = to_internal(c.ctx, b)
+    xt = torch.zeros_like(bt)
+    st = G.mg_solve(c.ctx.h, bt, xt, 1e-10)
+    x = to_canonical(c.ctx, xt, b.shape)
+    xo, info = OM.mg_solve(c.mg, b.reshape(c.op.shape), tol=1e-10)
+    assert st.true_res <= 1e-10
+    assert rel_norm(x, _oracle_solution(c, b)) < 1e-8
+    assert abs(st.iters - info.iters) <= 2, (st.iters, info.iters)
+    tr = OM.norm(b.reshape(c.op.shape) - c.op.apply(x.reshape(c.op.shape))) / OM.norm(b)
+    assert tr <= 1e-10
+    c.close()
+
+
+@pytest.mark.parametrize("cp", [1, 2, 3], ids=["f32", "bf16", "f16"])
+def test_solve_mixed_precision(G, cp):
+    """FP32 V-cycle with reduced-precision coarse stencil, FP64 outer GCR with
+    reliable updates: still |r|/|b| <= 1e-10 and the oracle's solution."""
+    c = Case(G, **SMALL, setup_sweeps=1, smoother_prec=G.DWF_F32, coarse_prec=[cp])
+    from gpu_util import to_internal, to_canonical, rel_norm
+    b = I.gaussian_source(c.dims, c.Ls, 2)
+    bt = to_internal(c.ctx, b)
+    xt = torch.zeros_like(bt)
+    st = G.mg_solve(c.ctx.h, bt, xt, 1e-10)
+    x = to_canonical(c.ctx, xt, b.shape)
+    assert st.true_res <= 1e-10 and st.fine_applies_f32 > st.fine_applies_f64
+    assert rel_norm(x, _oracle_solution(c, b)) < 1e-8
+    c.close()
+
+
+def test_solve_host_buffers_and_multi_rhs(G):
+    """mg_solve with host (numpy) buffers, two right-hand sides."""
+    c = Case(G, **SMALL, setup_sweeps=0)
+    from gpu_util import to_internal
+    bs = np.stack([I.gaussian_source(c.dims, c.Ls, 40 + i) for i in range(2)])
+    bt = to_internal(c.ctx, bs, nrhs=2)
+    bh = bt.cpu().numpy()
+    xh = np.zeros_like(bh)
+    st = G.mg_solve(c.ctx.h, bh, xh, 1e-10, nrhs=2)
+    assert st.true_res <= 1e-10 and np.abs(xh).max() > 0
+    xd = torch.zeros_like(bt)
+    G.mg_solve(c.ctx.h, bt, xd, 1e-10, nrhs=2)
+    assert np.linalg.norm(xd.cpu().numpy() - xh) / np.linalg.norm(xh) < 1e-9
+    c.close()
+
+
+def test_three_level_solve(G):
+    """Recursion (Sec. 2): S2 is a V-cycle of the second coarse level."""
+    c = Case(G, dims=(4, 4, 4, 8), Ls=4, mf=0.1, nvec=[8, 8], block=[(2, 2, 2, 2), (2, 2, 2, 2)],
+             setup_sweeps=1)
+    from gpu_util import to_internal, to_canonical, rel_norm
+    b = I.gaussian_source(c.dims, c.Ls, 2)
+    bt = to_internal(c.ctx, b)
+    xt = torch.zeros_like(bt)
+    st = G.mg_solve(c.ctx.h, bt, xt, 1e-10)
+    assert st.true_res <= 1e-10 and st.coarse_applies[2] > 0
+    x = to_canonical(c.ctx, xt, b.shape)
+    assert rel_norm(x, _oracle_solution(c, b)) < 1e-8
+    d, n = G.mg_level_info(c.ctx.h, 2)
+    Y = torch.empty(int(np.prod(d)) * 9 * n * n, dtype=torch.complex128, device="cuda")
+    G.mg_get_coarse_links(c.ctx.h, 2, Y)
+    Yref = c.mg.levels[2].op.Y.reshape(-1)
+    assert np.linalg.norm(Y.cpu().numpy() - Yref) / np.linalg.norm(Yref) < 1e-6
+    c.close()
+
+
+def test_zero_source_and_bad_setup(G):
+    c = Case(G, **SMALL, setup_sweeps=0)
+    bt = torch.zeros(c.ctx.field_elems, dtype=torch.complex128, device="cuda")
+    xt = torch.ones_like(bt)
+    st = G.mg_solve(c.ctx.h, bt, xt, 1e-10)
+    assert st.true_res == 0.0 and xt.abs().max().item() == 0.0
+    # a block that does not divide the lattice, an odd split Nvec
+    with pytest.raises(G.DWFError):
+        G.mg_setup(c.ctx.h, 2, [8], [(3, 2, 2, 2)])
+    with pytest.raises(G.DWFError):
+        G.mg_setup(c.ctx.h, 2, [6 + 1], [(2, 2, 2, 2)])
+    c.close()
