@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the domain-wall multigrid solve on GB300.
+
+Metric: wall time per solve of D x = b to |b - D x| / |b| <= 1e-10 (FP64 true
+residual), with the multigrid setup amortised over the right-hand sides of
+one step; plus the fine Dslash's achieved HBM bandwidth (roofline).
+
+Workload (one GPU): 16^3 x 32 lattice, Ls = 16, M5 = 1.8, m_f = 0.001, links
+from 200 sweeps of a seeded quenched Wilson-gauge heatbath at beta = 6.0,
+2-level multigrid with 4^4 blocks and Nvec = 24, mixed precision (FP32 fine
+V-cycle, BF16 coarse stencil with FP32 accumulation, FP64 outer GCR with
+reliable updates), 12 Gaussian right-hand sides.  A step = mg_setup + the 12
+solves (every part of the solve path runs in each step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own independent problem
+(replicas; the path has no exchange step) and rank 0 prints the job line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import paper_1205_2933_gb300.inputs as I  # noqa: E402
+
+DIMS = (16, 16, 16, 32)
+LS = 16
+M5 = 1.8
+MF = 0.001
+BETA = 6.0
+HB_SWEEPS = 200
+HB_SEED = 100
+NVEC = 24
+BLOCK = (4, 4, 4, 4)
+NRHS = 12
+TOL = 1e-10
+FINE_BYTES_F32 = 204   # algorithmic bytes per 5D site of the FP32 Dslash
+FINE_BYTES_F64 = 408
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nrhs", type=int, default=NRHS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain", action="store_true", help="also time the plain FP64 method (1 solve)")
+    return ap.parse_args()
+
+
+def workload_config(nrhs):
+    return {"workload": f"DWF MG solve, 16^3x32 Ls=16 M5=1.8 mf=0.001, heatbath beta=6.0 ({HB_SWEEPS} sweeps, "
+                        f"seed {HB_SEED}), 2-level Nvec=24 blocks 4^4, FP32 V-cycle + BF16 coarse stencil + "
+                        f"FP64 outer GCR, setup amortised over {nrhs} Gaussian RHS",
+            "lattice": "16x16x16x32", "Ls": LS, "mf": MF, "nvec": NVEC, "block": list(BLOCK), "nrhs": nrhs,
+            "tol": TOL, "l2": "inputs larger than L2 (FP32 fine field 201 MB, FP64 403 MB; working set ~10 GB)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def gen_inputs(nrhs, rank=0):
+    U = I.heatbath_links(DIMS, BETA, HB_SWEEPS, HB_SEED)
+    bs = np.stack([I.gaussian_source(DIMS, LS, 101 + 1000 * rank + i) for i in range(nrhs)])
+    return U, bs
+
+
+def mixed_params(G):
+    p = G.mg_default_params()
+    p.smoother_prec = G.DWF_F32
+    p.coarse_prec[0] = G.DWF_BF16
+    return p
+
+
+def cpu_baseline_sample(U, b, seconds_target=15.0):
+    """The FP64 oracle as it stands, on the host cores: time applications of
+    its fine operator at the full lattice (the paper's cost unit, Sec. 3)."""
+    import oracle
+    dwf = oracle.DWF(U, DIMS, LS, M5, MF)
+    t0 = time.perf_counter()
+    dwf.D(b)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    n = max(1, min(20, int(seconds_target / max(per, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        dwf.D(b)
+    per = (time.perf_counter() - t0) / n
+    import ctypes
+    threads = os.environ.get("OMP_NUM_THREADS")
+    cores = int(threads) if threads else os.cpu_count()
+    return per, n, cores
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle timed on the host cores on bounded
+    samples of this workload, scaled to seconds per solve."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    U, bs = gen_inputs(1)
+    b = bs[0]
+    # cost of one solve in fine-operator applications, as measured on the GPU
+    # path for this workload (FP64 + FP32 applications per solve incl. amortised setup)
+    applies = float(os.environ.get("DWF_APPLIES_PER_SOLVE", "3000"))
+    times = []
+    for _ in range(args.warmup):
+        cpu_baseline_sample(U, b, 3.0)
+    for _ in range(args.steps):
+        per, n, cores = cpu_baseline_sample(U, b, 10.0)
+        times.append(per * applies)
+    v = statistics.median(times)
+    line = {"impl": "reference", "metric": "DWF MG solve time to |r|/|b|<=1e-10 (oracle, host cores)",
+            "value": v, "unit": "s/solve", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(1),
+            "cpu_baseline": {"value": v, "unit": "s/solve", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} applications of the oracle's FP64 fine operator at 16^3x32x16 per "
+                                       f"step, scaled by {applies:.0f} fine applications per solve"},
+            "e2e": {"value": v, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_1205_2933_gb300 import dwfmg as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nrhs = args.nrhs
+
+    U, bs = gen_inputs(nrhs, rank)
+    stream = torch.cuda.current_stream()
+    ctx = G.Context(DIMS, LS, M5, MF, torch.from_numpy(U).to(dev))
+    N = ctx.field_elems
+    canon = torch.from_numpy(bs).to(dev)
+    b = torch.empty(N * nrhs, dtype=torch.complex128, device=dev)
+    G.dwf_pack(ctx.h, b, canon, G.DWF_F64, nrhs)
+    x = torch.zeros_like(b)
+    del canon
+    p = mixed_params(G)
+
+    def step(stats_out=None):
+        G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p)
+        x.zero_()
+        st = G.mg_solve(ctx.h, b, x, TOL, nrhs)
+        if stats_out is not None:
+            stats_out.append(st.as_dict())
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    G.dwf_profile(ctx.h, True)
+    launches0 = G.dwf_launch_count()
+    stats = []
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(stats)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = G.dwf_launch_count() - launches0
+    ms_total = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    prof = {name: G.dwf_profile_read(ctx.h, k) for name, k in
+            (("dslash_f32", G.K_DSLASH_F32), ("dslash_f64", G.K_DSLASH_F64), ("restrict", G.K_RESTRICT),
+             ("prolong", G.K_PROLONG), ("coarse", G.K_COARSE))}
+    G.dwf_profile(ctx.h, False)
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = ms_step / 1000.0 / (nrhs * world)
+
+    # roofline of the dominant kernel: the FP32 fine Dslash
+    n32, ms32 = prof["dslash_f32"]
+    V5 = ctx.V * LS
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if n32:
+        avg = ms32 / n32
+        achieved = FINE_BYTES_F32 * V5 / (avg * 1e-3) / 1e9
+        roof = {"kernel": "dslash_f32", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "avg_launch_us": avg * 1e3, "launches": n32,
+                "bytes_per_launch": FINE_BYTES_F32 * V5}
+
+    applies_per_solve = None
+    if stats:
+        s = stats[-1]
+        applies_per_solve = (s["fine_applies_f64"] + s["fine_applies_f32"]) / nrhs
+
+    line = {"metric": "DWF MG solve time to |r|/|b|<=1e-10 (setup amortised over 12 RHS); Dslash HBM GB/s",
+            "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+bf16 (fp64 outer)", "data": "synthetic (seeded heatbath links, Gaussian sources)",
+            "config": workload_config(nrhs), "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
+            "solve_stats": stats[-1] if stats else None,
+            "kernel_time_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = run_e2e(G, torch, U, bs, p, nrhs)
+    if args.plain and rank == 0:
+        line["plain_fp64"] = run_plain(G, torch, ctx, b, nrhs)
+    if rank == 0 and not args.no_cpu_baseline:
+        per, n, cores = cpu_baseline_sample(U, bs[0])
+        if applies_per_solve:
+            line["cpu_baseline"] = {"value": per * applies_per_solve, "unit": "s/solve", "cores": cores,
+                                    "kind": "oracle",
+                                    "sample": f"{n} applications of the oracle's FP64 fine operator at 16^3x32x16, "
+                                              f"scaled by the {applies_per_solve:.0f} fine applications per solve "
+                                              f"of the timed GPU solves (the paper's cost unit)"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(G, torch, U, bs, p, nrhs):
+    """Same metric through the public API with host buffers: links and sources
+    copied from pinned host memory, solutions read back, inside the region."""
+    Uh = torch.from_numpy(U).pin_memory()
+    # sources in the internal layout on the host (pinned)
+    tmp = G.Context(DIMS, LS, M5, MF, Uh)
+    canon = torch.from_numpy(bs).cuda()
+    bi = torch.empty(tmp.field_elems * nrhs, dtype=torch.complex128, device="cuda")
+    G.dwf_pack(tmp.h, bi, canon, G.DWF_F64, nrhs)
+    bh = bi.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    tmp.close()
+    del canon, bi
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = G.Context(DIMS, LS, M5, MF, Uh)
+    G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p)
+    G.mg_solve(ctx.h, bh, xh, TOL, nrhs)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return {"value": dt / nrhs, "unit": "s/solve", "h2d_bytes_per_step": int(Uh.numel() * 16 + 2 * bh.numel() * 16),
+            "d2h_bytes_per_step": int(xh.numel() * 16)}
+
+
+def run_plain(G, torch, ctx, b, nrhs):
+    """The plain FP64 method on the same lattice: setup + one solve."""
+    p = G.mg_default_params()
+    x = torch.zeros(ctx.field_elems, dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p)
+    t1 = time.perf_counter()
+    st = G.mg_solve(ctx.h, b[:ctx.field_elems].contiguous(), x, TOL, 1, check=False)
+    t2 = time.perf_counter()
+    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "per_solve_amortised_12": (t1 - t0) / 12 + (t2 - t1),
+            "stats": st.as_dict(), "status": st.status}
+
+
+if __name__ == "__main__":
+    main()

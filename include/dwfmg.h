@@ -86,11 +86,12 @@ typedef struct {
     double coarsest_tol;    /* S2 relative tolerance on the coarsest level (0.1) */
     int coarsest_maxiter;   /* (64) */
     int coarse_restart;     /* GCR restart length of S2 (16) */
-    int outer_restart;      /* outer flexible GCR restart length (10) */
+    int outer_restart;      /* outer flexible GCR restart length, <= 64 (20) */
     int outer_maxiter;      /* (500) */
     int setup_iters0;       /* CGNR iterations on D x = 0 for the initial vectors (20) */
-    int setup_sweeps;       /* adaptive sweeps re-applying the multigrid to D x = 0 (3) */
-    int setup_sweep_iters;  /* MG-GCR iterations per vector and sweep (4) */
+    int setup_sweeps;       /* inverse-iteration sweeps with the current multigrid (1) */
+    int setup_sweep_iters;  /* MG-GCR iterations per vector and sweep, at most (8) */
+    double setup_sweep_tol; /* MG-GCR relative tolerance of a sweep's solve D x = v (0.1) */
     int split;              /* 1: each vector split into Gamma = +-1 halves, Nvec/2 vectors (1) */
     dwf_prec smoother_prec; /* F64 (plain method) or F32 (mixed) for the fine V-cycle (F64) */
     dwf_prec coarse_prec[4];/* link precision of each coarse level's stencil: F64, F32, BF16, F16 */
@@ -192,6 +193,19 @@ dwf_status mg_coarse_apply(dwf_ctx *ctx, int level, void *out_dev, const void *i
 /* x = one fine-level V-cycle applied to b (Sec. 2), run in the smoother
  * precision; x and b are FP64.  Synchronous. */
 dwf_status mg_vcycle(dwf_ctx *ctx, void *x_dev, const void *b_dev);
+
+/* ---- Measurement -------------------------------------------------------
+ * An optional profiler brackets every launch of the timed kernel classes
+ * with CUDA events on the context's stream.  dwf_profile(ctx, 1) clears the
+ * records and starts recording, dwf_profile(ctx, 0) stops; dwf_profile_read
+ * synchronises the stream and returns the number of launches and their
+ * summed device time for one class.  Classes: 0 = fine D in FP64, 1 = fine
+ * D in FP32, 2 = restriction, 3 = prolongation, 4 = coarse stencil. */
+dwf_status dwf_profile(dwf_ctx *ctx, int enable);
+dwf_status dwf_profile_read(dwf_ctx *ctx, int kernel_class, long long *launches, double *total_ms);
+
+/* Number of kernels this library has launched in the process so far. */
+unsigned long long dwf_launch_count(void);
 
 /* Description of the last error raised on this thread (diagnostics). */
 const char *dwf_last_error(void);

@@ -433,8 +433,9 @@ class MGParams:
     coarsest_maxiter: int = 64
     coarse_restart: int = 16
     setup_iters0: int = 20             # CGNR iterations on A x = 0 for the initial vectors
-    setup_sweeps: int = 3              # adaptive refinement sweeps with the current MG
-    setup_sweep_iters: int = 4         # MG-GCR iterations per vector per sweep
+    setup_sweeps: int = 1              # inverse-iteration sweeps with the current MG
+    setup_sweep_iters: int = 8         # MG-GCR iterations per vector per sweep, at most
+    setup_sweep_tol: float = 0.1       # MG-GCR relative tolerance of a sweep's solve
     split: bool = True                 # split each vector into its Gamma = +1 / -1 halves:
                                        # Nvec/2 adaptive vectors give Nvec coarse components
 
@@ -547,29 +548,43 @@ def nvectors(p: MGParams, l: int) -> int:
     return p.nvec[l]
 
 
+def orthonormalise_global(vecs):
+    """Two passes of modified Gram-Schmidt over the whole set of vectors."""
+    out = [np.array(v, copy=True) for v in vecs]
+    for _pass in range(2):
+        for j in range(len(out)):
+            for i in range(j):
+                out[j] = out[j] - vdot(out[i], out[j]) * out[i]
+            out[j] = out[j] / norm(out[j])
+    return np.stack(out)
+
+
 def adaptive_setup(fine_op, p: MGParams, random_vectors_per_level) -> MG:
     """The adaptive setup of Sec. 2, level by level:
-      1. start vectors: Krylov iterations on A x = 0 from random vectors;
+      1. start vectors: Krylov iterations (CGNR) on A x = 0 from random
+         vectors, normalised, then orthonormalised as a set;
       2. build the transfer (block Gram-Schmidt) and R A P;
-      3. sweeps: apply the current multigrid solver (GCR preconditioned by
-         the V-cycle) to A x = 0 starting from each vector, so that what it
-         fails to remove replaces the vector; rebuild; repeat.
+      3. sweeps: each vector is replaced by an approximate solution of
+         A x = v with the current multigrid (GCR preconditioned by the
+         V-cycle, loose tolerance) -- inverse iteration, which amplifies
+         exactly the modes the solver finds hard -- the set is
+         re-orthonormalised, and the multigrid rebuilt ("repeated for as long
+         as necessary").
     random_vectors_per_level[l] holds nvectors(p, l) random fields of level l."""
     mg = MG(fine_op, p)
     nl = len(p.nvec)
     for l in range(nl):
         op = mg.levels[l].op
         nv = nvectors(p, l)
-        vecs = initial_vectors(op, nv, random_vectors_per_level[l], p)
+        vecs = orthonormalise_global(initial_vectors(op, nv, random_vectors_per_level[l], p))
         mg.build_from_vectors(l, vecs)
         for _ in range(p.setup_sweeps):
             new = []
             for k in range(nv):
-                x0 = vecs[k]
-                x, _ = gcr(op.apply, np.zeros_like(x0), x0=x0, tol=0.0, maxiter=p.setup_sweep_iters,
+                x, _ = gcr(op.apply, vecs[k], tol=p.setup_sweep_tol, maxiter=p.setup_sweep_iters,
                            restart=p.setup_sweep_iters + 1, M=lambda r, l=l: mg.vcycle(l, r))
                 new.append(x / norm(x))
-            vecs = np.stack(new)
+            vecs = orthonormalise_global(np.stack(new))
             mg.build_from_vectors(l, vecs)
     return mg
 

@@ -51,11 +51,12 @@ void mg_default_params(mg_params *p) {
     p->coarsest_tol = 0.1;
     p->coarsest_maxiter = 64;
     p->coarse_restart = 16;
-    p->outer_restart = 10;
+    p->outer_restart = 20;
     p->outer_maxiter = 500;
     p->setup_iters0 = 20;
-    p->setup_sweeps = 3;
-    p->setup_sweep_iters = 4;
+    p->setup_sweeps = 1;
+    p->setup_sweep_iters = 8;
+    p->setup_sweep_tol = 0.1;
     p->split = 1;
     p->smoother_prec = DWF_F64;
     for (int i = 0; i < 4; ++i) p->coarse_prec[i] = DWF_F64;
@@ -126,6 +127,8 @@ void dwf_destroy(dwf_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    dwf::prof_reset(c);
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
     dwf::mg_free(c);
     if (c->hscal) cudaFreeHost(c->hscal);
     delete c;
@@ -217,5 +220,36 @@ dwf_status mg_vcycle(dwf_ctx *c, void *x, const void *b) {
 }
 
 const char *dwf_last_error(void) { return dwf::last_error(); }
+
+dwf_status dwf_profile(dwf_ctx *c, int enable) {
+    if (!c) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        DWF_CUDA(cudaStreamSynchronize(c->stream));
+        dwf::prof_reset(c);
+        c->prof = enable != 0;
+        return DWF_OK;
+    });
+}
+
+dwf_status dwf_profile_read(dwf_ctx *c, int kernel_class, long long *launches, double *total_ms) {
+    if (!c || !launches || !total_ms || kernel_class < 0 || kernel_class >= dwf::K_NCLASS) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        DWF_CUDA(cudaStreamSynchronize(c->stream));
+        long long n = 0;
+        double ms = 0.0;
+        for (auto &r : c->prof_rec)
+            if (r.cls == kernel_class) {
+                float t = 0.f;
+                DWF_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+                ms += t;
+                ++n;
+            }
+        *launches = n;
+        *total_ms = ms;
+        return DWF_OK;
+    });
+}
+
+unsigned long long dwf_launch_count(void) { return dwf::launch_count(); }
 
 }  // extern "C"

@@ -62,27 +62,36 @@ __device__ void finish(double2 mine, double2 *part, unsigned *count, double *out
     }
 }
 
+// Per-thread partial sums in the storage precision (FP32 FMAs for FP32
+// fields), combined across threads and CTAs in FP64.
+template <typename T> struct Acc;
+template <> struct Acc<double2> { using type = double; };
+template <> struct Acc<float2> { using type = float; };
+
 template <typename TX, typename TY>
 __global__ void __launch_bounds__(RED_THREADS) dot_kernel(const TX *__restrict__ x, const TY *__restrict__ y, int64_t n,
                                                           double2 *part, unsigned *count, double *out) {
-    double2 a = make_double2(0, 0);
+    using A = typename Acc<TX>::type;
+    A ar = 0, ai = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 u = to_d(x[i]), v = to_d(y[i]);
-        a.x += u.x * v.x + u.y * v.y;
-        a.y += u.x * v.y - u.y * v.x;
+        TX u = x[i];
+        TY v = y[i];
+        ar += (A)u.x * (A)v.x + (A)u.y * (A)v.y;
+        ai += (A)u.x * (A)v.y - (A)u.y * (A)v.x;
     }
-    finish(a, part, count, out, true);
+    finish(make_double2((double)ar, (double)ai), part, count, out, true);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) norm2_kernel(const T *__restrict__ x, int64_t n, double2 *part,
                                                             unsigned *count, double *out) {
-    double2 a = make_double2(0, 0);
+    using A = typename Acc<T>::type;
+    A a = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 u = to_d(x[i]);
-        a.x += u.x * u.x + u.y * u.y;
+        T u = x[i];
+        a += (A)u.x * (A)u.x + (A)u.y * (A)u.y;
     }
-    finish(a, part, count, out, false);
+    finish(make_double2((double)a, 0.0), part, count, out, false);
 }
 
 template <typename T>
@@ -99,7 +108,7 @@ __global__ void copy_kernel(TO *__restrict__ out, const TI *__restrict__ in, int
 
 unsigned red_blocks(dwf_ctx *c, int64_t n) {
     int64_t b = (n + RED_THREADS - 1) / RED_THREADS;
-    int64_t cap = std::min<int64_t>(RED_MAX_BLOCKS, (int64_t)c->sm_count * 4);
+    int64_t cap = std::min<int64_t>(RED_MAX_BLOCKS, (int64_t)c->sm_count * 6);
     return (unsigned)std::max<int64_t>(1, std::min(b, cap));
 }
 
@@ -131,6 +140,41 @@ template <typename T> void bnorm2(dwf_ctx *c, int slot, const T *x, int64_t n) {
     norm2_kernel<T><<<red_blocks(c, n), RED_THREADS, 0, c->stream>>>(
         x, n, c->red_part.as<double2>(), c->red_count.as<unsigned>(), c->scal.as<double>() + slot);
     DWF_CHECK_LAUNCH();
+}
+
+static unsigned long long g_launches = 0;
+void note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+static cudaEvent_t take_event(dwf_ctx *c) {
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    DWF_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+ProfScope::ProfScope(dwf_ctx *ctx, int k) : c(ctx), cls(k) {
+    if (!c->prof) return;
+    a = take_event(c);
+    b = take_event(c);
+    DWF_CUDA(cudaEventRecord(a, c->stream));
+}
+
+ProfScope::~ProfScope() {
+    if (!a) return;
+    if (cudaEventRecord(b, c->stream) == cudaSuccess) c->prof_rec.push_back(ProfRecord{cls, a, b});
+}
+
+void prof_reset(dwf_ctx *c) {
+    for (auto &r : c->prof_rec) {
+        c->prof_pool.push_back(r.a);
+        c->prof_pool.push_back(r.b);
+    }
+    c->prof_rec.clear();
 }
 
 double read_scalar(dwf_ctx *c, int slot) {

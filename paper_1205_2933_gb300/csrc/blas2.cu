@@ -6,29 +6,46 @@ namespace dwf {
 
 namespace {
 
+// Arithmetic in the storage precision: FP32 fields are updated with FP32
+// FMAs (GB300's FP64 rate is a small fraction of its FP32 rate).
+template <typename T> struct Real;
+template <> struct Real<double2> { using type = double; };
+template <> struct Real<float2> { using type = float; };
+
 template <typename T>
-__global__ void caxpy_kernel(T *__restrict__ y, double2 a, const T *__restrict__ x, int64_t n) {
+__global__ void caxpy_kernel(T *__restrict__ y, double2 ad, const T *__restrict__ x, int64_t n) {
+    using R = typename Real<T>::type;
+    const R ar = (R)ad.x, ai = (R)ad.y;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 xv = cvt<double2, T>(x[i]), yv = cvt<double2, T>(y[i]);
-        yv.x += a.x * xv.x - a.y * xv.y;
-        yv.y += a.x * xv.y + a.y * xv.x;
-        y[i] = cvt<T, double2>(yv);
+        T xv = x[i], yv = y[i];
+        yv.x += ar * xv.x - ai * xv.y;
+        yv.y += ar * xv.y + ai * xv.x;
+        y[i] = yv;
     }
 }
 
 template <typename T>
-__global__ void cxpay_kernel(T *__restrict__ y, double2 a, const T *__restrict__ x, int64_t n) {
+__global__ void cxpay_kernel(T *__restrict__ y, double2 ad, const T *__restrict__ x, int64_t n) {
+    using R = typename Real<T>::type;
+    const R ar = (R)ad.x, ai = (R)ad.y;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 xv = cvt<double2, T>(x[i]), yv = cvt<double2, T>(y[i]);
-        y[i] = cvt<T, double2>(make_double2(xv.x + a.x * yv.x - a.y * yv.y, xv.y + a.x * yv.y + a.y * yv.x));
+        T xv = x[i], yv = y[i];
+        T o;
+        o.x = xv.x + ar * yv.x - ai * yv.y;
+        o.y = xv.y + ar * yv.y + ai * yv.x;
+        y[i] = o;
     }
 }
 
 template <typename T>
-__global__ void rscale_kernel(T *__restrict__ x, double a, int64_t n) {
+__global__ void rscale_kernel(T *__restrict__ x, double ad, int64_t n) {
+    using R = typename Real<T>::type;
+    const R a = (R)ad;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 v = cvt<double2, T>(x[i]);
-        x[i] = cvt<T, double2>(make_double2(a * v.x, a * v.y));
+        T v = x[i];
+        v.x *= a;
+        v.y *= a;
+        x[i] = v;
     }
 }
 
@@ -50,14 +67,16 @@ template <typename T> struct MultiArgs {
 
 template <typename T>
 __global__ void multiaxpy_kernel(T *__restrict__ w, MultiArgs<T> a, int64_t n) {
+    using R = typename Real<T>::type;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 v = cvt<double2, T>(w[i]);
+        T v = w[i];
         for (int j = 0; j < a.k; ++j) {
-            double2 u = cvt<double2, T>(a.p[j][i]);
-            v.x += a.b[j].x * u.x - a.b[j].y * u.y;
-            v.y += a.b[j].x * u.y + a.b[j].y * u.x;
+            T u = a.p[j][i];
+            const R br = (R)a.b[j].x, bi = (R)a.b[j].y;
+            v.x += br * u.x - bi * u.y;
+            v.y += br * u.y + bi * u.x;
         }
-        w[i] = cvt<T, double2>(v);
+        w[i] = v;
     }
 }
 

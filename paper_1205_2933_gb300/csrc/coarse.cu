@@ -13,6 +13,8 @@
 #include "mg.cuh"
 #include "spin.cuh"
 
+#include <type_traits>
+
 namespace dwf {
 
 namespace {
@@ -113,14 +115,15 @@ __device__ __forceinline__ void face_site(const FaceMap &m, int64_t xc, int mu, 
 // F[xc][dd][k][l], dd = 2*mu + (dir < 0): block-face contributions of one hop.
 // FINE: hop = -1/2 (1 -+ g_mu) U q_l(x +- mu) with boundary sign (the fine D);
 // else: hop = Y_d(x) q_l(x +- mu) of the finer coarse level's stencil.
-template <int NV, bool FINE>
-__global__ void __launch_bounds__(256) face_kernel(double2 *__restrict__ F, const double2 *__restrict__ Q,
-                                                   const double2 *__restrict__ U, const double2 *__restrict__ Yf,
+template <int NV, bool FINE, typename R>
+__global__ void __launch_bounds__(256) face_kernel(double2 *__restrict__ F, const C<R> *__restrict__ Q,
+                                                   const C<R> *__restrict__ U, const double2 *__restrict__ Yf,
                                                    Geom g, FaceMap m, int chf) {
-    extern __shared__ double2 sm[];
+    extern __shared__ unsigned char sm_raw[];
+    C<R> *sm = reinterpret_cast<C<R> *>(sm_raw);
     const int run = m.run;
-    double2 *sH = sm;                        // [NV][chf*run]
-    double2 *sA = sm + (size_t)NV * chf * run;  // [NV][chf*run]
+    C<R> *sH = sm;                        // [NV][chf*run]
+    C<R> *sA = sm + (size_t)NV * chf * run;  // [NV][chf*run]
     const int64_t xc = blockIdx.x;
     const int dd = blockIdx.y;
     const int mu = dd >> 1, dir = (dd & 1) ? -1 : +1;
@@ -136,16 +139,16 @@ __global__ void __launch_bounds__(256) face_kernel(double2 *__restrict__ F, cons
         for (int item = threadIdx.x; item < NV * chf; item += blockDim.x) {
             int l = item / chf, fl = item - l * chf;
             int64_t f = f0 + fl;
-            double2 *h = sH + (size_t)l * W + fl * run;
-            double2 *a = sA + (size_t)l * W + fl * run;
+            C<R> *h = sH + (size_t)l * W + fl * run;
+            C<R> *a = sA + (size_t)l * W + fl * run;
             if (f >= nface) {
-                for (int e = 0; e < run; ++e) { h[e] = make_double2(0, 0); a[e] = make_double2(0, 0); }
+                for (int e = 0; e < run; ++e) { h[e] = mk<R>(0, 0); a[e] = mk<R>(0, 0); }
                 continue;
             }
             int64_t site;
             int s;
             face_site(m, xc, mu, dir, f, site, s);
-            const double2 *ql = Q + (int64_t)l * m.nelem;
+            const C<R> *ql = Q + (int64_t)l * m.nelem;
             if (FINE) {
                 for (int e = 0; e < 12; ++e) a[e] = ql[(site * 12 + e) * m.Ls + s];
                 int c[4];
@@ -156,25 +159,24 @@ __global__ void __launch_bounds__(256) face_kernel(double2 *__restrict__ F, cons
                 if (cc[mu] == g.L[mu]) cc[mu] = 0;
                 if (cc[mu] < 0) cc[mu] = g.L[mu] - 1;
                 int64_t nb = site_index(g, cc);
-                double coef = (mu == 3 && g.ap && wrap) ? 0.5 : -0.5;
-                double2 acc12[12];
-                for (int e = 0; e < 12; ++e) acc12[e] = make_double2(0, 0);
-                double2 lk[9];
-                const double2 *up = U + ((dir > 0 ? site : nb) * 4 + mu) * 9;
-                for (int e = 0; e < 9; ++e) lk[e] = up[e];
+                R coef = (mu == 3 && g.ap && wrap) ? R(0.5) : R(-0.5);
+                C<R> acc12[12];
+                for (int e = 0; e < 12; ++e) acc12[e] = mk<R>(0, 0);
+                C<R> lk[9];
+                LinkIO<R>::load(U, dir > 0 ? site : nb, mu, lk);
                 if (dir > 0) {
                     switch (mu) {
-                        case 0: hop<0, false, double>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
-                        case 1: hop<1, false, double>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
-                        case 2: hop<2, false, double>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
-                        default: hop<3, false, double>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
+                        case 0: hop<0, false, R>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
+                        case 1: hop<1, false, R>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
+                        case 2: hop<2, false, R>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
+                        default: hop<3, false, R>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
                     }
                 } else {
                     switch (mu) {
-                        case 0: hop<0, true, double>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
-                        case 1: hop<1, true, double>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
-                        case 2: hop<2, true, double>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
-                        default: hop<3, true, double>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
+                        case 0: hop<0, true, R>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
+                        case 1: hop<1, true, R>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
+                        case 2: hop<2, true, R>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
+                        default: hop<3, true, R>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
                     }
                 }
                 for (int e = 0; e < 12; ++e) h[e] = acc12[e];
@@ -182,10 +184,10 @@ __global__ void __launch_bounds__(256) face_kernel(double2 *__restrict__ F, cons
                 for (int e = 0; e < run; ++e) a[e] = ql[site * run + e];
                 int64_t nb = shift_site(g, site, mu, dir);
                 const double2 *Yrow = Yf + (site * 9 + 1 + dd) * (int64_t)run * run;
-                const double2 *qn = ql + nb * run;
+                const C<R> *qn = ql + nb * run;
                 for (int e = 0; e < run; ++e) {
-                    double2 z = make_double2(0, 0);
-                    for (int m2 = 0; m2 < run; ++m2) cfma(z, Yrow[e * run + m2], qn[m2]);
+                    C<R> z = mk<R>(0, 0);
+                    for (int m2 = 0; m2 < run; ++m2) cfma(z, cvt<C<R>, double2>(Yrow[e * run + m2]), qn[m2]);
                     h[e] = z;
                 }
             }
@@ -196,10 +198,11 @@ __global__ void __launch_bounds__(256) face_kernel(double2 *__restrict__ F, cons
             int p = threadIdx.x + q * 256;
             if (p < NP) {
                 int k = p / NV, l = p - k * NV;
-                const double2 *ak = sA + (size_t)k * W, *hl = sH + (size_t)l * W;
-                double2 s = acc[q];
+                const C<R> *ak = sA + (size_t)k * W, *hl = sH + (size_t)l * W;
+                C<R> s = mk<R>(0, 0);
                 for (int e = 0; e < W; ++e) cfmac(s, ak[e], hl[e]);
-                acc[q] = s;
+                acc[q].x += (double)s.x;
+                acc[q].y += (double)s.y;
             }
         }
         __syncthreads();
@@ -274,6 +277,7 @@ void coarse_apply_t(dwf_ctx *c, const Level &L, C<R> *y, const C<R> *x, const LT
 }  // namespace
 
 template <typename R> void coarse_apply(dwf_ctx *c, const Level &L, C<R> *y, const C<R> *x, bool dag) {
+    ProfScope ps(c, K_COARSE);
     switch (L.yprec) {
         case DWF_F64: coarse_apply_t<R, double2>(c, L, y, x, L.Y64.as<double2>(), dag, 1); break;
         case DWF_F32: coarse_apply_t<R, float2>(c, L, y, x, L.Y32.as<float2>(), dag, 1); break;
@@ -298,22 +302,23 @@ void convert_coarse_links(dwf_ctx *c, Level &L) {
     DWF_CHECK_LAUNCH();
 }
 
-// Build Y of level l+1 from level l's FP64 basis Q64 (W = scratch of nv fields).
-void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, double2 *W) {
+// Build Y of level Lc = L+1 (FP64) from level L's basis Q in precision R:
+// FP32 products with FP64 accumulation across chunks when R = float.
+template <typename R> void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, const C<R> *Q, C<R> *W) {
     const int nv = L.nv;
     // W_l = A_l q_l for every basis vector
     if (L.index == 0) {
-        dslash(c, W, L.Q64.as<double2>(), false, nv);
+        dslash(c, W, Q, false, nv);
     } else {
         for (int l = 0; l < nv; ++l)
-            coarse_apply_t<double, double2>(c, L, W + (int64_t)l * L.lg.nelem, L.Q64.as<double2>() + (int64_t)l * L.lg.nelem,
-                                            L.Y64.as<double2>(), false, 1);
+            coarse_apply_t<R, double2>(c, L, W + (int64_t)l * L.lg.nelem, Q + (int64_t)l * L.lg.nelem,
+                                       L.Y64.as<double2>(), false, 1);
     }
     const int64_t nc = Lc.lg.g.V;
     const int64_t np = (int64_t)nv * nv;
     if (L.G.bytes < sizeof(double2) * nc * np) L.G.alloc(sizeof(double2) * nc * np);
     if (L.F.bytes < sizeof(double2) * nc * np * 8) L.F.alloc(sizeof(double2) * nc * np * 8);
-    block_gram<double>(c, L, L.G.as<double2>(), L.Q64.as<double2>(), W);
+    block_gram<R>(c, L, L.G.as<double2>(), Q, W);
     FaceMap m;
     for (int i = 0; i < 4; ++i) {
         m.L[i] = L.lg.g.L[i];
@@ -323,15 +328,16 @@ void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, double2 *W) {
     m.Ls = L.lg.g.Ls;
     m.run = L.lg.ncomp;
     m.nelem = L.lg.nelem;
-    int chf = (int)std::max<int64_t>(1, (46 * 1024) / ((int64_t)2 * nv * m.run * sizeof(double2)));
-    size_t smem = (size_t)2 * nv * chf * m.run * sizeof(double2);
+    int chf = (int)std::max<int64_t>(1, (46 * 1024) / ((int64_t)2 * nv * m.run * sizeof(C<R>)));
+    size_t smem = (size_t)2 * nv * chf * m.run * sizeof(C<R>);
     dim3 grid((unsigned)nc, 8);
     bool fine = (L.index == 0);
-#define FK(NV)                                                                                                       \
-    if (fine) face_kernel<NV, true><<<grid, 256, smem, c->stream>>>(L.F.as<double2>(), L.Q64.as<double2>(),        \
-                                                                  c->U64.as<double2>(), nullptr, L.lg.g, m, chf);  \
-    else face_kernel<NV, false><<<grid, 256, smem, c->stream>>>(L.F.as<double2>(), L.Q64.as<double2>(), nullptr,   \
-                                                              L.Y64.as<double2>(), L.lg.g, m, chf)
+    const C<R> *Ul = std::is_same<R, double>::value ? (const C<R> *)c->U64.p : (const C<R> *)c->U32.p;
+#define FK(NV)                                                                                               \
+    if (fine) face_kernel<NV, true, R><<<grid, 256, smem, c->stream>>>(L.F.as<double2>(), Q, Ul, nullptr,     \
+                                                                      L.lg.g, m, chf);                       \
+    else face_kernel<NV, false, R><<<grid, 256, smem, c->stream>>>(L.F.as<double2>(), Q, nullptr,            \
+                                                                  L.Y64.as<double2>(), L.lg.g, m, chf)
     NV_DISPATCH2(nv, FK);
 #undef FK
     DWF_CHECK_LAUNCH();
@@ -342,6 +348,9 @@ void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, double2 *W) {
     DWF_CHECK_LAUNCH();
     convert_coarse_links(c, Lc);
 }
+
+template void build_coarse_from<double>(dwf_ctx *, Level &, Level &, const double2 *, double2 *);
+template void build_coarse_from<float>(dwf_ctx *, Level &, Level &, const float2 *, float2 *);
 
 template void coarse_apply<double>(dwf_ctx *, const Level &, double2 *, const double2 *, bool);
 template void coarse_apply<float>(dwf_ctx *, const Level &, float2 *, const float2 *, bool);

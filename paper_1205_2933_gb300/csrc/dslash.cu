@@ -16,110 +16,178 @@ namespace dwf {
 
 namespace {
 
-template <int MU, bool DAG, typename R>
-__device__ __forceinline__ void hops_mu(C<R> acc[12], const C<R> *__restrict__ in, const Geom &g,
-                                        const int c[4], int64_t site, int s, const C<R> *sUsite) {
-    // forward neighbour x + mu
-    {
-        int cc[4] = {c[0], c[1], c[2], c[3]};
-        cc[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
-        R coef = (MU == 3 && g.ap && c[3] == g.L[3] - 1) ? R(0.5) : R(-0.5);
-        hop<MU, false, R>(acc, in, site_index(g, cc), g.Ls, s, sUsite + MU * 9, DAG ? +1 : -1, coef);
-    }
-    // backward neighbour x - mu
-    {
-        int cc[4] = {c[0], c[1], c[2], c[3]};
-        cc[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
-        R coef = (MU == 3 && g.ap && c[3] == 0) ? R(0.5) : R(-0.5);
-        hop<MU, true, R>(acc, in, site_index(g, cc), g.Ls, s, sUsite + (4 + MU) * 9, DAG ? -1 : +1, coef);
-    }
+// One 4D hop for the thread's (site, s): spinor at neighbour row `p`
+// (already offset to s), stride Ls between components.
+template <int MU, bool ADJ, typename R>
+__device__ __forceinline__ void hop_row(C<R> acc[12], const C<R> *__restrict__ p, int Ls, const C<R> *m, int sig,
+                                        R coef) {
+    C<R> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = p[k * Ls];
+    C<R> h[6], u[6];
+    project<MU>(v, sig, h);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            C<R> z = mk<R>(0, 0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (ADJ) cfmac(z, m[b * 3 + a], h[sp * 3 + b]);
+                else cfma(z, m[a * 3 + b], h[sp * 3 + b]);
+            }
+            u[sp * 3 + a] = z;
+        }
+    reconstruct_add<MU>(acc, u, sig, coef);
 }
 
-template <typename R, bool DAG>
-__global__ void __launch_bounds__(256) dslash_kernel(C<R> *__restrict__ out, const C<R> *__restrict__ in,
+// CTA = spb whole 4D sites x Ls threads.  Phase 1 (spb*8 threads): each
+// stages one link (U_mu(x) forward, U_mu(x-mu) backward) into shared memory
+// together with the neighbour's site index and the hop coefficient
+// -1/2 (times -1 across an antiperiodic t boundary).  Phase 2: every thread
+// computes its 5D site.  SHFL: the Ls threads of a site sit inside one warp
+// (Ls divides 32) and the fifth-dimension neighbours come from shuffles.
+template <typename R, bool DAG, bool SHFL>
+__global__ void __launch_bounds__(128) dslash_kernel(C<R> *__restrict__ out, const C<R> *__restrict__ in,
                                                      const C<R> *__restrict__ U, Geom g, R diag, R mf,
                                                      int spb, int64_t field) {
     extern __shared__ unsigned char smem_raw[];
-    C<R> *sU = reinterpret_cast<C<R> *>(smem_raw);
-    const int64_t site0 = (int64_t)blockIdx.x * spb;
-    const int64_t rhs_off = (int64_t)blockIdx.y * field;
+    C<R> *sU = reinterpret_cast<C<R> *>(smem_raw);               // [spb][8][9]
+    int *sN = reinterpret_cast<int *>(sU + (size_t)spb * 72);       // [spb][8]
+    R *sC = reinterpret_cast<R *>(sN + spb * 8);                    // [spb][8]
+    const int Ls = g.Ls;
+    const int V = (int)g.V;
+    const int site0 = blockIdx.x * spb;
+    const size_t rhs_off = (size_t)blockIdx.y * (size_t)field;
     in += rhs_off;
     out += rhs_off;
-    // stage the 8 links of every site of this CTA
     for (int j = threadIdx.x; j < spb * 8; j += blockDim.x) {
-        int ls = j >> 3, k = j & 7, mu = k & 3;
-        int64_t site = site0 + ls;
-        if (site < g.V) {
-            int64_t lsite = site;
-            if (k >= 4) {
-                int c[4];
-                site_coords(g, site, c);
-                c[mu] = (c[mu] == 0) ? g.L[mu] - 1 : c[mu] - 1;
-                lsite = site_index(g, c);
-            }
+        const int ls = j >> 3, k = j & 7, mu = k & 3;
+        const int site = site0 + ls;
+        if (site < V) {
+            // coordinate along mu, extent and site stride of direction mu
+            const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+            int cmu, Lmu, stride;
+            if (mu == 0) { cmu = site % L0; Lmu = L0; stride = 1; }
+            else if (mu == 1) { cmu = (site / L0) % L1; Lmu = L1; stride = L0; }
+            else if (mu == 2) { cmu = (site / (L0 * L1)) % L2; Lmu = L2; stride = L0 * L1; }
+            else { cmu = site / (L0 * L1 * L2); Lmu = L3; stride = L0 * L1 * L2; }
+            int n = cmu + (k < 4 ? 1 : -1);
+            const bool wrap = (n == Lmu) || (n < 0);
+            n = (n == Lmu) ? 0 : (n < 0 ? Lmu - 1 : n);
+            const int nb = site + (n - cmu) * stride;
             C<R> m[9];
-            LinkIO<R>::load(U, lsite, mu, m);
+            LinkIO<R>::load(U, k < 4 ? site : nb, mu, m);
 #pragma unroll
             for (int e = 0; e < 9; ++e) sU[(ls * 8 + k) * 9 + e] = m[e];
+            sN[ls * 8 + k] = nb;
+            sC[ls * 8 + k] = (mu == 3 && g.ap && wrap) ? R(0.5) : R(-0.5);
         }
     }
     __syncthreads();
-    const int ls = threadIdx.x / g.Ls;
-    const int s = threadIdx.x - ls * g.Ls;
-    const int64_t site = site0 + ls;
-    if (ls >= spb || site >= g.V) return;
-    int c[4];
-    site_coords(g, site, c);
-    const C<R> *sUsite = sU + ls * 8 * 9;
-    C<R> acc[12];
+    const int ls = threadIdx.x / Ls;
+    const int s = threadIdx.x - ls * Ls;
+    const int site = site0 + ls;
+    const bool active = (ls < spb) && (site < V);
+    if (!SHFL && !active) return;
+    const int row = 12 * Ls;
+    C<R> acc[12], self[12];
+    if (active) {
+        const C<R> *p = in + (size_t)site * row + s;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = diag * in[(site * 12 + k) * g.Ls + s];
-    hops_mu<0, DAG, R>(acc, in, g, c, site, s, sUsite);
-    hops_mu<1, DAG, R>(acc, in, g, c, site, s, sUsite);
-    hops_mu<2, DAG, R>(acc, in, g, c, site, s, sUsite);
-    hops_mu<3, DAG, R>(acc, in, g, c, site, s, sUsite);
+        for (int k = 0; k < 12; ++k) self[k] = p[k * Ls];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) self[k] = mk<R>(0, 0);
+    }
     // fifth dimension: D has -P_- psi(s+1) and -P_+ psi(s-1) (wrap: +mf);
     // D^+ has -P_+ psi(s+1) and -P_- psi(s-1) (wrap: +mf).
-    {
-        int sp = (s == g.Ls - 1) ? 0 : s + 1;
-        R cp = (s == g.Ls - 1) ? mf : R(-1);
-        int sm = (s == 0) ? g.Ls - 1 : s - 1;
-        R cm = (s == 0) ? mf : R(-1);
-        const int up_lo = DAG ? 0 : 6;   // components taken from s+1
-        const int dn_lo = DAG ? 6 : 0;   // components taken from s-1
+    const int up_lo = DAG ? 0 : 6;   // components taken from s+1
+    const int dn_lo = DAG ? 6 : 0;   // components taken from s-1
+    const R cp = (s == Ls - 1) ? mf : R(-1);
+    const R cm = (s == 0) ? mf : R(-1);
+    C<R> up[6], dn[6];
+    if (SHFL) {
+        const int lane = threadIdx.x & 31;
+        const int base = lane - s;
+        const int lup = base + ((s == Ls - 1) ? 0 : s + 1);
+        const int ldn = base + ((s == 0) ? Ls - 1 : s - 1);
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            acc[up_lo + k] = acc[up_lo + k] + cp * in[(site * 12 + up_lo + k) * g.Ls + sp];
-            acc[dn_lo + k] = acc[dn_lo + k] + cm * in[(site * 12 + dn_lo + k) * g.Ls + sm];
+            up[k].x = __shfl_sync(0xffffffffu, self[up_lo + k].x, lup);
+            up[k].y = __shfl_sync(0xffffffffu, self[up_lo + k].y, lup);
+            dn[k].x = __shfl_sync(0xffffffffu, self[dn_lo + k].x, ldn);
+            dn[k].y = __shfl_sync(0xffffffffu, self[dn_lo + k].y, ldn);
+        }
+        if (!active) return;
+    } else {
+        const C<R> *p = in + (size_t)site * row;
+        const int sp = (s == Ls - 1) ? 0 : s + 1;
+        const int sm = (s == 0) ? Ls - 1 : s - 1;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            up[k] = p[(up_lo + k) * Ls + sp];
+            dn[k] = p[(dn_lo + k) * Ls + sm];
         }
     }
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[(site * 12 + k) * g.Ls + s] = acc[k];
+    for (int k = 0; k < 12; ++k) acc[k] = diag * self[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        acc[up_lo + k] = acc[up_lo + k] + cp * up[k];
+        acc[dn_lo + k] = acc[dn_lo + k] + cm * dn[k];
+    }
+    const C<R> *sUs = sU + ls * 72;
+    const int *sNs = sN + ls * 8;
+    const R *sCs = sC + ls * 8;
+    const int fs = DAG ? +1 : -1;  // sig of the forward hops
+    hop_row<0, false, R>(acc, in + (size_t)sNs[0] * row + s, Ls, sUs + 0 * 9, fs, sCs[0]);
+    hop_row<0, true, R>(acc, in + (size_t)sNs[4] * row + s, Ls, sUs + 4 * 9, -fs, sCs[4]);
+    hop_row<1, false, R>(acc, in + (size_t)sNs[1] * row + s, Ls, sUs + 1 * 9, fs, sCs[1]);
+    hop_row<1, true, R>(acc, in + (size_t)sNs[5] * row + s, Ls, sUs + 5 * 9, -fs, sCs[5]);
+    hop_row<2, false, R>(acc, in + (size_t)sNs[2] * row + s, Ls, sUs + 2 * 9, fs, sCs[2]);
+    hop_row<2, true, R>(acc, in + (size_t)sNs[6] * row + s, Ls, sUs + 6 * 9, -fs, sCs[6]);
+    hop_row<3, false, R>(acc, in + (size_t)sNs[3] * row + s, Ls, sUs + 3 * 9, fs, sCs[3]);
+    hop_row<3, true, R>(acc, in + (size_t)sNs[7] * row + s, Ls, sUs + 7 * 9, -fs, sCs[7]);
+    C<R> *o = out + (size_t)site * row + s;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k * Ls] = acc[k];
 }
 
 template <typename R>
 void launch(dwf_ctx *c, C<R> *out, const C<R> *in, const C<R> *U, bool dag, int nrhs) {
     const Geom &g = c->g;
+    DWF_REQUIRE(g.V * g.Ls * 12 < (int64_t)1 << 31 && g.V < (int64_t)1 << 31, DWF_EINVAL,
+                "lattice too large for 32-bit element offsets of one field");
+    // sites per CTA: about 128 threads, staging within 46 KB of shared memory
     int spb = g.Ls >= 128 ? 1 : 128 / g.Ls;
+    const size_t per_site = 72 * sizeof(C<R>) + 8 * sizeof(int) + 8 * sizeof(R);
+    const int max_spb = (int)((46 * 1024) / per_site);
+    if (spb > max_spb) spb = max_spb;
+    const bool shfl = (32 % g.Ls) == 0;
     int threads = spb * g.Ls;
+    if (shfl) threads = (threads + 31) / 32 * 32;  // whole warps for the shuffles
     dim3 grid((unsigned)((g.V + spb - 1) / spb), (unsigned)nrhs);
-    size_t smem = (size_t)spb * 8 * 9 * sizeof(C<R>);
+    size_t smem = (size_t)spb * per_site;
     int64_t field = g.V * g.Ls * 12;
-    if (dag)
-        dslash_kernel<R, true><<<grid, threads, smem, c->stream>>>(out, in, U, g, R(5.0 - c->M5), R(c->mf), spb, field);
-    else
-        dslash_kernel<R, false><<<grid, threads, smem, c->stream>>>(out, in, U, g, R(5.0 - c->M5), R(c->mf), spb, field);
+    R diag = R(5.0 - c->M5), mf = R(c->mf);
+#define DL(D, S) dslash_kernel<R, D, S><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, spb, field)
+    if (dag) { if (shfl) DL(true, true); else DL(true, false); }
+    else { if (shfl) DL(false, true); else DL(false, false); }
+#undef DL
     DWF_CHECK_LAUNCH();
 }
 
 }  // namespace
 
 void dslash(dwf_ctx *c, double2 *out, const double2 *in, bool dag, int nrhs) {
+    ProfScope ps(c, K_DSLASH_F64);
     launch<double>(c, out, in, c->U64.as<double2>(), dag, nrhs);
     c->applies64 += nrhs;
 }
 
 void dslash(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs) {
+    ProfScope ps(c, K_DSLASH_F32);
     launch<float>(c, out, in, c->U32.as<float2>(), dag, nrhs);
     c->applies32 += nrhs;
 }

@@ -70,7 +70,12 @@ struct Error {
                                std::string(#call) + ": " + cudaGetErrorString(e_)};           \
     } while (0)
 
-#define DWF_CHECK_LAUNCH() DWF_CUDA(cudaGetLastError())
+void note_launch();
+#define DWF_CHECK_LAUNCH()               \
+    do {                                 \
+        DWF_CUDA(cudaGetLastError());    \
+        ::dwf::note_launch();            \
+    } while (0)
 
 #define DWF_REQUIRE(cond, code, text)                                                         \
     do {                                                                                      \
@@ -129,8 +134,15 @@ __host__ __device__ __forceinline__ int64_t site_index(const Geom &g, const int 
 // Device scalar slots used by solver kernels (coefficients stay on the GPU).
 constexpr int NSCALAR = 8192;
 
-struct Workspace;
 struct MGState;
+
+// Kernel classes timed by the optional event profiler (see dwf_profile).
+enum KernelClass { K_DSLASH_F64 = 0, K_DSLASH_F32 = 1, K_RESTRICT = 2, K_PROLONG = 3, K_COARSE = 4, K_NCLASS = 5 };
+
+struct ProfRecord {
+    int cls;
+    cudaEvent_t a, b;
+};
 
 }  // namespace dwf
 
@@ -151,10 +163,24 @@ struct dwf_ctx {
     dwf::DevBuf red_part, red_count;
     dwf::MGState *mg = nullptr;
     long long applies64 = 0, applies32 = 0;
-    std::vector<dwf::DevBuf *> owned;
+    // event profiler
+    bool prof = false;
+    std::vector<dwf::ProfRecord> prof_rec;
+    std::vector<cudaEvent_t> prof_pool;
 };
 
 namespace dwf {
+
+// Brackets one kernel launch with profiling events when the profiler is on.
+struct ProfScope {
+    dwf_ctx *c;
+    int cls;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(dwf_ctx *ctx, int k);
+    ~ProfScope();
+};
+void prof_reset(dwf_ctx *c);
+unsigned long long launch_count();
 
 // ---- pack.cu ----
 void pack(dwf_ctx *c, void *internal, const double2 *canonical, dwf_prec prec, int nrhs);

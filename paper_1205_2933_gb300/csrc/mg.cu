@@ -118,7 +118,7 @@ template <typename R> class Runner {
     // the oracle, done as classical Gram-Schmidt twice (same span, FP64 dots).
     GcrInfo gcr(int l, T *x, const T *b, double tol, int maxit, int restart, bool pc, bool x_zero, bool b_zero) {
         const int64_t N = n(l);
-        DWF_REQUIRE(restart >= 1 && restart <= 32, DWF_EINVAL, "GCR restart must be in 1..32");
+        DWF_REQUIRE(restart >= 1 && restart <= MAX_RESTART + 1, DWF_EINVAL, "GCR restart out of range");
         T *r = ws(l, 10);
         std::vector<T *> Z(restart), W(restart);
         for (int i = 0; i < restart; ++i) {
@@ -158,8 +158,11 @@ template <typename R> class Runner {
                 std::vector<double> v(2 * k);
                 read_scalars(c, SLOT_A, 2 * k, v.data());
                 for (int i = 0; i < k; ++i) beta[i] = make_double2(-v[2 * i], -v[2 * i + 1]);
-                multiaxpy<T>(c, W[k], beta.data(), W.data(), k, N);
-                multiaxpy<T>(c, Z[k], beta.data(), Z.data(), k, N);
+                for (int i0 = 0; i0 < k; i0 += 32) {
+                    int kk = std::min(32, k - i0);
+                    multiaxpy<T>(c, W[k], beta.data() + i0, W.data() + i0, kk, N);
+                    multiaxpy<T>(c, Z[k], beta.data() + i0, Z.data() + i0, kk, N);
+                }
             }
             bnorm2<T>(c, SLOT_A, W[k], N);
             bdot<T, T>(c, SLOT_A + 2, W[k], r, N);
@@ -232,15 +235,16 @@ template <typename R> class Runner {
     }
 
     // block Gram-Schmidt, basis copies and the coarse operator of level l+1
+    // Gamma split, block Gram-Schmidt (FP64 accumulation) and the coarse
+    // operator of level l+1, all from the basis in precision R.
     void build(int l) {
         Level &L = mg.lev[l];
         const int64_t N = n(l);
-        gamma_split<double>(c, L, L.Q64.as<double2>(), L.vec64.as<double2>(), L.nadapt, mg.p.split != 0);
-        if (!block_orthonormalise<double>(c, L, L.Q64.as<double2>()))
+        gamma_split<R>(c, L, Q(l), L.vec64.as<double2>(), L.nadapt, mg.p.split != 0);
+        if (!block_orthonormalise<R>(c, L, Q(l)))
             throw Error{DWF_EBREAKDOWN, "block Gram-Schmidt met linearly dependent near-null vectors"};
-        if (std::is_same<R, float>::value) bcopy<float2, double2>(c, L.Q32.as<float2>(), L.Q64.as<double2>(), N * L.nv);
-        DevBuf W(sizeof(double2) * N * L.nv);
-        build_coarse_from(c, L, mg.lev[l + 1], W.as<double2>());
+        DevBuf W(sizeof(T) * N * L.nv);
+        build_coarse_from<R>(c, L, mg.lev[l + 1], Q(l), W.as<T>());
         mg.nlevels = l + 2;
         DWF_CUDA(cudaStreamSynchronize(c->stream));
     }
@@ -250,8 +254,7 @@ template <typename R> class Runner {
         const mg_params &p = mg.p;
         const int64_t N = n(l);
         L.vec64.alloc(sizeof(double2) * N * L.nadapt);
-        L.Q64.alloc(sizeof(double2) * N * L.nv);
-        if (std::is_same<R, float>::value) L.Q32.alloc(sizeof(float2) * N * L.nv);
+        Qbuf<R>(L).alloc(sizeof(T) * N * L.nv);
         double2 *v = L.vec64.as<double2>();
         if (l == 0 && start) {
             DevBuf canon(sizeof(double2) * N * L.nadapt);
@@ -263,22 +266,44 @@ template <typename R> class Runner {
             gauss_fill<double2>(c, v, L.nadapt, N, L.lg.g.Ls, L.lg.g.V, l == 0, p.seed + (uint32_t)l, 4u);
         }
         // start vectors: CGNR on A x = 0 from each random vector
-        T *xv = ws(l, 9);
+        T *xv = ws(l, 9), *bv = ws(l, 8);
         for (int j = 0; j < L.nadapt; ++j) {
             bcopy<T, double2>(c, xv, v + (int64_t)j * N, N);
             cgnr(l, xv, nullptr, p.setup_iters0, false, true);
             store_normalised(l, v + (int64_t)j * N, xv);
         }
+        orthonormalise_global(l, v, L.nadapt);
         build(l);
-        // sweeps: the current multigrid applied to A x = 0 from each vector
+        // inverse-iteration sweeps: v <- (approximate) A^-1 v with the current
+        // multigrid-preconditioned GCR, then the set is re-orthonormalised
         for (int sw = 0; sw < p.setup_sweeps; ++sw) {
             for (int j = 0; j < L.nadapt; ++j) {
-                bcopy<T, double2>(c, xv, v + (int64_t)j * N, N);
-                gcr(l, xv, nullptr, 0.0, p.setup_sweep_iters, p.setup_sweep_iters + 1, true, false, true);
+                bcopy<T, double2>(c, bv, v + (int64_t)j * N, N);
+                gcr(l, xv, bv, p.setup_sweep_tol, p.setup_sweep_iters, p.setup_sweep_iters + 1, true, true, false);
                 store_normalised(l, v + (int64_t)j * N, xv);
             }
+            orthonormalise_global(l, v, L.nadapt);
             build(l);
         }
+    }
+
+    // Two passes of modified Gram-Schmidt over the whole set of FP64 vectors.
+    void orthonormalise_global(int l, double2 *v, int nv) {
+        const int64_t N = n(l);
+        for (int pass = 0; pass < 2; ++pass)
+            for (int j = 0; j < nv; ++j) {
+                double2 *vj = v + (int64_t)j * N;
+                for (int i = 0; i < j; ++i) {
+                    bdot<double2, double2>(c, SLOT_A, v + (int64_t)i * N, vj, N);
+                    double d[2];
+                    read_scalars(c, SLOT_A, 2, d);
+                    caxpy<double2>(c, vj, make_double2(-d[0], -d[1]), v + (int64_t)i * N, N);
+                }
+                bnorm2<double2>(c, SLOT_A, vj, N);
+                double nn = std::sqrt(read_scalar(c, SLOT_A));
+                DWF_REQUIRE(nn > 0.0 && std::isfinite(nn), DWF_EBREAKDOWN, "adaptive vectors became linearly dependent");
+                rscale<double2>(c, vj, 1.0 / nn, N);
+            }
     }
 
     // Outer flexible GCR in FP64: each cycle solves A e = r approximately with
@@ -381,9 +406,9 @@ dwf_status mg_setup_impl(dwf_ctx *c, int levels, const int *nvec, const int (*bl
                          const void *start, bool start_on_host) {
     mg_free(c);
     DWF_REQUIRE(p.smoother_prec == DWF_F64 || p.smoother_prec == DWF_F32, DWF_EINVAL, "smoother_prec must be F64 or F32");
-    DWF_REQUIRE(p.nu_post >= 0 && p.nu_pre >= 0 && p.coarse_restart >= 1 && p.coarse_restart <= 32 &&
-                    p.outer_restart >= 1 && p.outer_restart <= 31 && p.setup_sweep_iters >= 1 &&
-                    p.setup_sweep_iters <= 31,
+    DWF_REQUIRE(p.nu_post >= 0 && p.nu_pre >= 0 && p.coarse_restart >= 1 &&
+                    p.outer_restart >= 1 && p.outer_restart <= MAX_RESTART && p.setup_sweep_iters >= 1 &&
+                    p.setup_sweep_iters <= MAX_RESTART && p.coarse_restart <= MAX_RESTART,
                 DWF_EINVAL, "iteration parameters out of range");
     MGState *mg = new MGState();
     mg->p = p;
@@ -472,7 +497,10 @@ void mg_level_info_impl(dwf_ctx *c, int level, int dims[4], int *ncomp) {
 void mg_get_vectors_impl(dwf_ctx *c, int level, double2 *out) {
     MGState &mg = need_mg(c, level, 0, mg_nlevels_minus1(c));
     const Level &L = mg.lev[level];
-    DWF_CUDA(cudaMemcpyAsync(out, L.Q64.p, sizeof(double2) * L.lg.nelem * L.nv, cudaMemcpyDeviceToDevice, c->stream));
+    if (L.Q64.p)
+        DWF_CUDA(cudaMemcpyAsync(out, L.Q64.p, sizeof(double2) * L.lg.nelem * L.nv, cudaMemcpyDeviceToDevice, c->stream));
+    else
+        bcopy<double2, float2>(c, out, L.Q32.as<float2>(), L.lg.nelem * L.nv);
 }
 
 void mg_get_coarse_links_impl(dwf_ctx *c, int level, double2 *out) {
@@ -484,12 +512,32 @@ void mg_get_coarse_links_impl(dwf_ctx *c, int level, double2 *out) {
 
 void mg_restrict_impl(dwf_ctx *c, int level, double2 *cout, const double2 *fin) {
     MGState &mg = need_mg(c, level, 0, mg_nlevels_minus1(c));
-    restrict_<double>(c, mg.lev[level], cout, fin, mg.lev[level].Q64.as<double2>());
+    Level &L = mg.lev[level];
+    if (L.Q64.p) {
+        restrict_<double>(c, L, cout, fin, L.Q64.as<double2>());
+        return;
+    }
+    const int64_t nf = L.lg.nelem, nc = mg.lev[level + 1].lg.nelem;
+    DevBuf f32(sizeof(float2) * nf), c32(sizeof(float2) * nc);
+    bcopy<float2, double2>(c, f32.as<float2>(), fin, nf);
+    restrict_<float>(c, L, c32.as<float2>(), f32.as<float2>(), L.Q32.as<float2>());
+    bcopy<double2, float2>(c, cout, c32.as<float2>(), nc);
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
 }
 
 void mg_prolong_impl(dwf_ctx *c, int level, double2 *fout, const double2 *cin) {
     MGState &mg = need_mg(c, level, 0, mg_nlevels_minus1(c));
-    prolong_<double>(c, mg.lev[level], fout, cin, mg.lev[level].Q64.as<double2>(), false);
+    Level &L = mg.lev[level];
+    if (L.Q64.p) {
+        prolong_<double>(c, L, fout, cin, L.Q64.as<double2>(), false);
+        return;
+    }
+    const int64_t nf = L.lg.nelem, nc = mg.lev[level + 1].lg.nelem;
+    DevBuf f32(sizeof(float2) * nf), c32(sizeof(float2) * nc);
+    bcopy<float2, double2>(c, c32.as<float2>(), cin, nc);
+    prolong_<float>(c, L, f32.as<float2>(), c32.as<float2>(), L.Q32.as<float2>(), false);
+    bcopy<double2, float2>(c, fout, f32.as<float2>(), nf);
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
 }
 
 void mg_coarse_apply_impl(dwf_ctx *c, int level, void *out, const void *in, bool dag, dwf_prec prec) {

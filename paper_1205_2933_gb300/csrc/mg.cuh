@@ -74,9 +74,9 @@ template <typename R> void gamma_split(dwf_ctx *c, const Level &L, C<R> *Q, cons
 // ---- coarse.cu ----
 // y = A_l c on coarse level l (l >= 1), or A_l^+ c
 template <typename R> void coarse_apply(dwf_ctx *c, const Level &L, C<R> *y, const C<R> *x, bool dag);
-// Build the Galerkin coarse operator Y of level Lc = l+1 from level L's FP64
-// basis Q64 (W: scratch of L.nv fields of level L, FP64)
-void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, double2 *W);
+// Build the Galerkin coarse operator Y (FP64) of level Lc = l+1 from level L's
+// basis Q (W: scratch of L.nv fields of level L, same precision)
+template <typename R> void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, const C<R> *Q, C<R> *W);
 // refresh the reduced-precision copies of Y on level l
 void convert_coarse_links(dwf_ctx *c, Level &L);
 
@@ -88,6 +88,7 @@ template <typename T> void rscale(dwf_ctx *c, T *x, double a, int64_t n);       
 template <typename T, typename U> void caxpy_mixed(dwf_ctx *c, T *y, double2 a, const U *x, int64_t n);
 // w += sum_i beta_i V_i, k <= 32 (pointers and coefficients from the host)
 template <typename T> void multiaxpy(dwf_ctx *c, T *w, const double2 *beta, T *const *V, int k, int64_t n);
+constexpr int MAX_RESTART = 64;
 // x = a * x + b * y (real a, complex b) fused for two pairs: used by GCR updates
 template <typename T> void gauss_fill(dwf_ctx *c, double2 *out, int nfields, int64_t nelem, int Ls, int64_t V,
                                       bool canonical_fine, uint32_t seed, uint32_t stream);

@@ -273,6 +273,7 @@ __global__ void gamma_split_kernel(C<R> *__restrict__ Q, const double2 *__restri
 
 template <typename R> void restrict_(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const C<R> *Q) {
     BlockMap m = make_map(L);
+    ProfScope ps(c, K_RESTRICT);
 #define RK(NV) restrict_kernel<R, NV><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(cout, fin, Q, m)
     NV_DISPATCH(L.nv, RK);
 #undef RK
@@ -281,6 +282,7 @@ template <typename R> void restrict_(dwf_ctx *c, const Level &L, C<R> *cout, con
 
 template <typename R> void prolong_(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const C<R> *Q, bool acc) {
     BlockMap m = make_map(L);
+    ProfScope ps(c, K_PROLONG);
 #define PK(NV) prolong_kernel<R, NV><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(fout, cin, Q, m, acc ? 1 : 0)
     NV_DISPATCH(L.nv, PK);
 #undef PK

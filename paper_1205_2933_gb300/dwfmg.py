@@ -32,6 +32,7 @@ class mg_params(ctypes.Structure):
         ("setup_iters0", ctypes.c_int),
         ("setup_sweeps", ctypes.c_int),
         ("setup_sweep_iters", ctypes.c_int),
+        ("setup_sweep_tol", ctypes.c_double),
         ("split", ctypes.c_int),
         ("smoother_prec", ctypes.c_int),
         ("coarse_prec", ctypes.c_int * 4),
@@ -91,7 +92,11 @@ def _load():
     L.mg_prolong.argtypes = [vp, i, vp, vp]
     L.mg_coarse_apply.argtypes = [vp, i, vp, vp, i, st]
     L.mg_vcycle.argtypes = [vp, vp, vp]
-    for name in ("dwf_create", "dwf_apply", "dwf_pack", "dwf_unpack", "mg_setup", "mg_solve", "mg_level_info",
+    L.dwf_profile.argtypes = [vp, i]
+    L.dwf_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+    L.dwf_launch_count.argtypes = []
+    L.dwf_launch_count.restype = ctypes.c_ulonglong
+    for name in ("dwf_profile", "dwf_profile_read", "dwf_create", "dwf_apply", "dwf_pack", "dwf_unpack", "mg_setup", "mg_solve", "mg_level_info",
                  "mg_get_vectors", "mg_get_coarse_links", "mg_restrict", "mg_prolong", "mg_coarse_apply",
                  "mg_vcycle"):
         getattr(L, name).restype = st
@@ -206,6 +211,25 @@ def mg_coarse_apply(ctx, level, out, inp, dagger=False, prec=DWF_F64):
 
 def mg_vcycle(ctx, x, b):
     return _check(_lib.mg_vcycle(ctx, _ptr(x), _ptr(b)), "mg_vcycle")
+
+
+K_DSLASH_F64, K_DSLASH_F32, K_RESTRICT, K_PROLONG, K_COARSE = 0, 1, 2, 3, 4
+
+
+def dwf_profile(ctx, enable):
+    return _check(_lib.dwf_profile(ctx, 1 if enable else 0), "dwf_profile")
+
+
+def dwf_profile_read(ctx, kernel_class):
+    """(launches, total device milliseconds) of one kernel class since dwf_profile(ctx, True)."""
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(_lib.dwf_profile_read(ctx, int(kernel_class), ctypes.byref(n), ctypes.byref(ms)), "dwf_profile_read")
+    return n.value, ms.value
+
+
+def dwf_launch_count():
+    return int(_lib.dwf_launch_count())
 
 
 class Context:

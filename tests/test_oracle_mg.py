@@ -164,8 +164,8 @@ def test_mg_solve_matches_dense_lu():
 def test_adaptive_setup_finds_near_null_vectors():
     """Sec. 2 adaptive setup: Krylov iterations on A x = 0 leave near-null
     vectors (Rayleigh quotients |D v| / |v| far below those of the random
-    start vectors); the sweeps re-apply the multigrid solver to A x = 0 and
-    rebuild from what it leaves, and the rebuilt solver converges.""" 
+    start vectors); inverse-iteration sweeps with the current multigrid keep
+    an orthonormal set, and the rebuilt solver converges."""
     op = _op((4, 4, 4, 4), 4, 0.05, 0.3, 1)
     rv = _vectors(op, 3)
     rq = lambda v: M.norm(op.apply(v)) / M.norm(v)
@@ -177,7 +177,10 @@ def test_adaptive_setup_finds_near_null_vectors():
     p = M.MGParams(nvec=(6,), block=((2, 2, 2, 2),), setup_sweeps=2)
     mg = M.adaptive_setup(op, p, [rv])
     assert len(mg.vectors[0]) == 3
-    assert all(abs(M.norm(v) - 1) < 1e-12 for v in mg.vectors[0])
+    G = np.array([[M.vdot(a, b) for b in mg.vectors[0]] for a in mg.vectors[0]])
+    assert np.abs(G - np.eye(3)).max() < 1e-12
+    # still a near-null set after the sweep
+    assert np.mean([rq(v) for v in mg.vectors[0]]) < 0.35 * r0
     _, info = M.mg_solve(mg, b, tol=1e-8)
     assert info.converged
 
