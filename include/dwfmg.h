@@ -80,7 +80,7 @@ typedef enum { DWF_F64 = 0, DWF_F32 = 1, DWF_BF16 = 2, DWF_F16 = 3 } dwf_prec;
  * in this library's choices.  Level 0 is the fine lattice. */
 typedef struct {
     int nu_pre;             /* nu_1: CGNR smoothing steps before restriction (default 0) */
-    int nu_post;            /* nu_3: CGNR smoothing steps after prolongation (default 4) */
+    int nu_post;            /* nu_3: CGNR smoothing steps after prolongation (default 8) */
     double coarse_tol;      /* S2 relative tolerance on intermediate levels (0.1) */
     int coarse_maxiter;     /* (24) */
     double coarsest_tol;    /* S2 relative tolerance on the coarsest level (0.1) */
@@ -88,8 +88,9 @@ typedef struct {
     int coarse_restart;     /* GCR restart length of S2 (16) */
     int outer_restart;      /* outer flexible GCR restart length, <= 64 (20) */
     int outer_maxiter;      /* (500) */
-    int setup_iters0;       /* CGNR iterations on D x = 0 for the initial vectors (20) */
-    int setup_sweeps;       /* inverse-iteration sweeps with the current multigrid (1) */
+    int setup_iters0;       /* CGNR iterations on D x = 0 for the initial vectors, at most (500) */
+    double setup_tol0;      /* ... or until |D x| <= setup_tol0 |D x_0|, tested every 8 iterations (1e-5) */
+    int setup_sweeps;       /* inverse-iteration sweeps with the current multigrid (0) */
     int setup_sweep_iters;  /* MG-GCR iterations per vector and sweep, at most (8) */
     double setup_sweep_tol; /* MG-GCR relative tolerance of a sweep's solve D x = v (0.1) */
     int split;              /* 1: each vector split into Gamma = +-1 halves, Nvec/2 vectors (1) */
@@ -209,6 +210,16 @@ unsigned long long dwf_launch_count(void);
 
 /* Description of the last error raised on this thread (diagnostics). */
 const char *dwf_last_error(void);
+
+/* The paper's comparison solver (Sec. 3: conjugate gradient on the squared
+ * operator): CG on D^+ D x = D^+ b in precision prec (DWF_F64 or DWF_F32),
+ * with a reliable update (FP64 true residual, search direction kept) every
+ * 200 iterations, until
+ * |b - D x| / |b| <= tol or maxiter iterations.  Same buffers and stats as
+ * mg_solve (iters = CG iterations; each costs one D and one D^+).  Needs no
+ * mg_setup.  Synchronous. */
+dwf_status dwf_cg_solve(dwf_ctx *ctx, const void *b, void *x, double tol, int maxiter, int nrhs, dwf_prec prec,
+                        mg_stats *stats);
 
 /* Description of a status code (static string). */
 const char *dwf_strerror(dwf_status s);

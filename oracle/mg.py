@@ -379,21 +379,23 @@ def mr(A: Callable, b, nsteps: int, omega: float = 1.0, x0=None):
     return x
 
 
-def cgnr(A: Callable, Adag: Callable, b, tol=1e-10, maxiter=100000, x0=None, info=None):
+def cgnr(A: Callable, Adag: Callable, b, tol=1e-10, maxiter=100000, x0=None, info=None, check_every=1):
     """CG on the normal equations A^+ A x = A^+ b (the paper's comparison solver,
     Sec. 3: CG on the squared operator).  Stops on |b - A x| / |b| <= tol,
-    using the recursively updated residual of the unsquared system."""
+    using the recursively updated residual of the unsquared system, tested
+    every `check_every` iterations.  For A x = 0 from a nonzero start the
+    test is relative to the initial residual |A x0|."""
     info = info if info is not None else SolveInfo()
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - A(x) if x0 is not None else b.copy()
-    bnorm = norm(b) or 1.0  # A x = 0 from a nonzero start: absolute residual
+    bnorm = norm(b) or norm(r) or 1.0
     z = Adag(r)
     p = z.copy()
     zz = vdot(z, z).real
     it = 0
     rn = norm(r)
     info.history.append(rn / bnorm)
-    while it < maxiter and rn / bnorm > tol:
+    while it < maxiter and (rn / bnorm > tol or it % check_every):
         w = A(p)
         a = zz / vdot(w, w).real
         x = x + a * p
@@ -426,14 +428,15 @@ class MGParams:
     nvec: tuple = (8,)                 # coarse components per site (Nvec) per transfer
     block: tuple = ((2, 2, 2, 2),)     # 4D block per transfer (fifth dim collapsed)
     nu_pre: int = 0                    # nu_1
-    nu_post: int = 4                   # nu_3
+    nu_post: int = 8                   # nu_3
     coarse_tol: float = 0.1            # S2 tolerance on intermediate levels
     coarse_maxiter: int = 24
     coarsest_tol: float = 0.1          # S2 on the coarsest level
     coarsest_maxiter: int = 64
     coarse_restart: int = 16
-    setup_iters0: int = 20             # CGNR iterations on A x = 0 for the initial vectors
-    setup_sweeps: int = 1              # inverse-iteration sweeps with the current MG
+    setup_iters0: int = 500            # CGNR iterations on A x = 0 for the initial vectors, at most
+    setup_tol0: float = 1e-5           # ... or until |A x| <= setup_tol0 |A x0| (tested every 8)
+    setup_sweeps: int = 0              # inverse-iteration sweeps with the current MG
     setup_sweep_iters: int = 8         # MG-GCR iterations per vector per sweep, at most
     setup_sweep_tol: float = 0.1       # MG-GCR relative tolerance of a sweep's solve
     split: bool = True                 # split each vector into its Gamma = +1 / -1 halves:
@@ -533,8 +536,8 @@ def initial_vectors(op, nvec, random_vectors, p: MGParams):
     out = []
     for k in range(nvec):
         x0 = random_vectors[k].reshape(op.shape)
-        x, _ = cgnr(op.apply, op.apply_dag, np.zeros_like(x0), x0=x0, tol=0.0,
-                    maxiter=p.setup_iters0)
+        x, _ = cgnr(op.apply, op.apply_dag, np.zeros_like(x0), x0=x0, tol=p.setup_tol0,
+                    maxiter=p.setup_iters0, check_every=8)
         out.append(x / norm(x))
     return np.stack(out)
 
@@ -589,7 +592,7 @@ def adaptive_setup(fine_op, p: MGParams, random_vectors_per_level) -> MG:
     return mg
 
 
-def mg_solve(mg: MG, b, tol=1e-10, maxiter=500, restart=10, x0=None):
+def mg_solve(mg: MG, b, tol=1e-10, maxiter=500, restart=20, x0=None):
     """Outer flexible GCR on the fine operator, preconditioned by one V-cycle
     per iteration (Sec. 3)."""
     A = mg.levels[0].op.apply

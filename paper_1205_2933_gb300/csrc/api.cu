@@ -45,7 +45,7 @@ void mg_default_params(mg_params *p) {
     if (!p) return;
     std::memset(p, 0, sizeof(*p));
     p->nu_pre = 0;
-    p->nu_post = 4;
+    p->nu_post = 8;
     p->coarse_tol = 0.1;
     p->coarse_maxiter = 24;
     p->coarsest_tol = 0.1;
@@ -53,8 +53,9 @@ void mg_default_params(mg_params *p) {
     p->coarse_restart = 16;
     p->outer_restart = 20;
     p->outer_maxiter = 500;
-    p->setup_iters0 = 20;
-    p->setup_sweeps = 1;
+    p->setup_iters0 = 500;
+    p->setup_tol0 = 1e-5;
+    p->setup_sweeps = 0;
     p->setup_sweep_iters = 8;
     p->setup_sweep_tol = 0.1;
     p->split = 1;
@@ -109,7 +110,7 @@ dwf_status dwf_create(dwf_ctx **out, const int dims[4], int Ls, double M5, doubl
         c->scal.alloc(sizeof(double) * dwf::NSCALAR);
         DWF_CUDA(cudaMemsetAsync(c->scal.p, 0, c->scal.bytes, c->stream));
         DWF_CUDA(cudaMallocHost((void **)&c->hscal, sizeof(double) * dwf::NSCALAR));
-        c->red_part.alloc(sizeof(double2) * 1024);
+        c->red_part.alloc(sizeof(double2) * 1024 * 8);
         c->red_count.alloc(sizeof(unsigned));
         DWF_CUDA(cudaMemsetAsync(c->red_count.p, 0, sizeof(unsigned), c->stream));
         DWF_CUDA(cudaStreamSynchronize(c->stream));
@@ -181,6 +182,15 @@ dwf_status mg_solve(dwf_ctx *c, const void *b, void *x, double tol, int nrhs, mg
     return guarded(c, [&]() -> dwf_status {
         bool host = !is_device_ptr(b) || !is_device_ptr(x);
         return dwf::mg_solve_impl(c, b, x, tol, nrhs, stats, host);
+    });
+}
+
+dwf_status dwf_cg_solve(dwf_ctx *c, const void *b, void *x, double tol, int maxiter, int nrhs, dwf_prec prec,
+                        mg_stats *stats) {
+    if (!c || !b || !x || nrhs < 1 || !(tol > 0.0) || maxiter < 1) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        bool host = !is_device_ptr(b) || !is_device_ptr(x);
+        return dwf::cg_solve_impl(c, b, x, tol, maxiter, nrhs, prec, stats, host);
     });
 }
 

@@ -94,6 +94,57 @@ __global__ void __launch_bounds__(RED_THREADS) norm2_kernel(const T *__restrict_
     finish(make_double2((double)a, 0.0), part, count, out, false);
 }
 
+// out[2j], out[2j+1] = <V_j, w> for j < K: w is read once for K vectors.
+template <typename T, int K> struct MultiDotArgs {
+    const T *v[K];
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(RED_THREADS) multidot_kernel(MultiDotArgs<T, K> a, const T *__restrict__ w, int64_t n,
+                                                               double2 *part, unsigned *count, double *out) {
+    using A = typename Acc<T>::type;
+    A ar[K], ai[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) ar[j] = ai[j] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T y = w[i];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            T u = a.v[j][i];
+            ar[j] += (A)u.x * (A)y.x + (A)u.y * (A)y.y;
+            ai[j] += (A)u.x * (A)y.y - (A)u.y * (A)y.x;
+        }
+    }
+    __shared__ double2 sh[32];
+    __shared__ bool last;
+    for (int j = 0; j < K; ++j) {
+        double2 t = block_sum(make_double2((double)ar[j], (double)ai[j]), sh);
+        if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = t;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned ticket = atomicAdd(count, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = 0; j < K; ++j) {
+        double2 v = make_double2(0, 0);
+        for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+            const volatile double *pp = reinterpret_cast<const volatile double *>(&part[(size_t)j * gridDim.x + i]);
+            v.x += pp[0];
+            v.y += pp[1];
+        }
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) {
+            out[2 * j] = v.x;
+            out[2 * j + 1] = v.y;
+        }
+    }
+    if (threadIdx.x == 0) *count = 0u;
+}
+
 template <typename T>
 __global__ void zero_kernel(T *x, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -177,6 +228,33 @@ void prof_reset(dwf_ctx *c) {
     c->prof_rec.clear();
 }
 
+template <typename T> void bmultidot(dwf_ctx *c, int slot, T *const *V, int k, const T *w, int64_t n) {
+    for (int j0 = 0; j0 < k; j0 += 8) {
+        int kk = std::min(8, k - j0);
+        unsigned nb = red_blocks(c, n);
+#define MD(K)                                                                                            \
+    {                                                                                                    \
+        MultiDotArgs<T, K> a;                                                                            \
+        for (int j = 0; j < K; ++j) a.v[j] = V[j0 + j];                                                  \
+        multidot_kernel<T, K><<<nb, RED_THREADS, 0, c->stream>>>(a, w, n, c->red_part.as<double2>(),     \
+                                                                 c->red_count.as<unsigned>(),            \
+                                                                 c->scal.as<double>() + slot + 2 * j0);  \
+    }
+        switch (kk) {
+            case 1: MD(1) break;
+            case 2: MD(2) break;
+            case 3: MD(3) break;
+            case 4: MD(4) break;
+            case 5: MD(5) break;
+            case 6: MD(6) break;
+            case 7: MD(7) break;
+            default: MD(8) break;
+        }
+#undef MD
+        DWF_CHECK_LAUNCH();
+    }
+}
+
 double read_scalar(dwf_ctx *c, int slot) {
     double v;
     read_scalars(c, slot, 1, &v);
@@ -204,6 +282,8 @@ INST2(float2, float2)
 template void bzero<double2>(dwf_ctx *, double2 *, int64_t);
 template void bzero<float2>(dwf_ctx *, float2 *, int64_t);
 template void bnorm2<double2>(dwf_ctx *, int, const double2 *, int64_t);
+template void bmultidot<double2>(dwf_ctx *, int, double2 *const *, int, const double2 *, int64_t);
+template void bmultidot<float2>(dwf_ctx *, int, float2 *const *, int, const float2 *, int64_t);
 template void bnorm2<float2>(dwf_ctx *, int, const float2 *, int64_t);
 
 }  // namespace dwf

@@ -80,6 +80,88 @@ __global__ void multiaxpy_kernel(T *__restrict__ w, MultiArgs<T> a, int64_t n) {
     }
 }
 
+// Solver updates whose coefficients stay in device scalar slots (no host
+// round trip).  s[] is the context's scalar array.
+//   cg_xr:  a = s[izz] / s[iww] (0 if s[iww] <= 0); x += a p; r -= a w
+//   cg_p:   b = s[inew] / s[iold] (0 if s[iold] <= 0); p = z + b p
+template <typename T>
+__global__ void cg_xr_kernel(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ w,
+                             const double *__restrict__ s, int izz, int iww, int64_t n) {
+    using R = typename Real<T>::type;
+    const double ww = s[iww];
+    const R a = ww > 0.0 ? (R)(s[izz] / ww) : R(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T pv = p[i], wv = w[i], xv = x[i], rv = r[i];
+        xv.x += a * pv.x;
+        xv.y += a * pv.y;
+        rv.x -= a * wv.x;
+        rv.y -= a * wv.y;
+        x[i] = xv;
+        r[i] = rv;
+    }
+}
+
+template <typename T>
+__global__ void cg_p_kernel(T *__restrict__ p, const T *__restrict__ z, const double *__restrict__ s, int inew,
+                            int iold, int64_t n) {
+    using R = typename Real<T>::type;
+    const double old = s[iold];
+    const R bta = old > 0.0 ? (R)(s[inew] / old) : R(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T pv = p[i], zv = z[i];
+        pv.x = zv.x + bta * pv.x;
+        pv.y = zv.y + bta * pv.y;
+        p[i] = pv;
+    }
+}
+
+// w += sum_j c_j V_j with c_j = sgn * (s[ibase + 2j], s[ibase + 2j + 1])
+template <typename T>
+__global__ void multiaxpy_dev_kernel(T *__restrict__ w, MultiArgs<T> a, const double *__restrict__ s, int ibase,
+                                     double sgn, int64_t n) {
+    using R = typename Real<T>::type;
+    R cr[32], ci[32];
+    for (int j = 0; j < a.k; ++j) {
+        cr[j] = (R)(sgn * s[ibase + 2 * j]);
+        ci[j] = (R)(sgn * s[ibase + 2 * j + 1]);
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T v = w[i];
+        for (int j = 0; j < a.k; ++j) {
+            T u = a.p[j][i];
+            v.x += cr[j] * u.x - ci[j] * u.y;
+            v.y += cr[j] * u.y + ci[j] * u.x;
+        }
+        w[i] = v;
+    }
+}
+
+// GCR step with device coefficients: ww = s[iww] = |w|^2, (s[ia], s[ia+1]) =
+// <w, r>.  w, z are normalised by 1/|w|; x += al z; r -= al w with
+// al = <w, r> / |w| (the coefficient of the normalised direction).
+template <typename T>
+__global__ void gcr_step_kernel(T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, T *__restrict__ w,
+                                const double *__restrict__ s, int iww, int ia, int64_t n) {
+    using R = typename Real<T>::type;
+    const double ww = s[iww];
+    const double inv = ww > 0.0 ? 1.0 / sqrt(ww) : 0.0;
+    const R sc = (R)inv;
+    const R ar = (R)(s[ia] * inv), ai = (R)(s[ia + 1] * inv);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T zv = z[i], wv = w[i], xv = x[i], rv = r[i];
+        zv.x *= sc; zv.y *= sc;
+        wv.x *= sc; wv.y *= sc;
+        xv.x += ar * zv.x - ai * zv.y;
+        xv.y += ar * zv.y + ai * zv.x;
+        rv.x -= ar * wv.x - ai * wv.y;
+        rv.y -= ar * wv.y + ai * wv.x;
+        z[i] = zv;
+        w[i] = wv;
+        x[i] = xv;
+        r[i] = rv;
+    }
+}
+
 // Philox-4x32-10 (Salmon et al., SC'11) and Box-Muller, matching the host
 // input generator's addressing: key (seed, stream), counter (i, 0, 0, i>>32).
 __device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -153,6 +235,32 @@ template <typename T> void multiaxpy(dwf_ctx *c, T *w, const double2 *beta, T *c
     multiaxpy_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(w, a, n);
     DWF_CHECK_LAUNCH();
 }
+template <typename T> void cg_xr(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int izz, int iww, int64_t n) {
+    cg_xr_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(x, r, p, w, c->scal.as<double>(), izz, iww, n);
+    DWF_CHECK_LAUNCH();
+}
+template <typename T> void cg_p(dwf_ctx *c, T *p, const T *z, int inew, int iold, int64_t n) {
+    cg_p_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(p, z, c->scal.as<double>(), inew, iold, n);
+    DWF_CHECK_LAUNCH();
+}
+template <typename T> void multiaxpy_dev(dwf_ctx *c, T *w, T *const *V, int k, int ibase, double sgn, int64_t n) {
+    for (int j0 = 0; j0 < k; j0 += 32) {
+        MultiArgs<T> a;
+        a.k = std::min(32, k - j0);
+        for (int j = 0; j < a.k; ++j) {
+            a.p[j] = V[j0 + j];
+            a.b[j] = make_double2(0, 0);
+        }
+        multiaxpy_dev_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(w, a, c->scal.as<double>(), ibase + 2 * j0,
+                                                                          sgn, n);
+        DWF_CHECK_LAUNCH();
+    }
+}
+template <typename T> void gcr_step(dwf_ctx *c, T *x, T *r, T *z, T *w, int iww, int ia, int64_t n) {
+    gcr_step_kernel<T><<<blocks_for(c, n), 256, 0, c->stream>>>(x, r, z, w, c->scal.as<double>(), iww, ia, n);
+    DWF_CHECK_LAUNCH();
+}
+
 template <typename T> void gauss_fill(dwf_ctx *c, double2 *out, int nfields, int64_t nelem, int Ls, int64_t V,
                                       bool canonical_fine, uint32_t seed, uint32_t stream) {
     gauss_kernel<<<blocks_for(c, nelem * nfields), 256, 0, c->stream>>>(out, nfields, nelem, Ls, V,
@@ -170,6 +278,14 @@ template void caxpy_mixed<double2, float2>(dwf_ctx *, double2 *, double2, const 
 template void caxpy_mixed<double2, double2>(dwf_ctx *, double2 *, double2, const double2 *, int64_t);
 template void multiaxpy<double2>(dwf_ctx *, double2 *, const double2 *, double2 *const *, int, int64_t);
 template void multiaxpy<float2>(dwf_ctx *, float2 *, const double2 *, float2 *const *, int, int64_t);
+template void cg_xr<double2>(dwf_ctx *, double2 *, double2 *, const double2 *, const double2 *, int, int, int64_t);
+template void cg_xr<float2>(dwf_ctx *, float2 *, float2 *, const float2 *, const float2 *, int, int, int64_t);
+template void cg_p<double2>(dwf_ctx *, double2 *, const double2 *, int, int, int64_t);
+template void cg_p<float2>(dwf_ctx *, float2 *, const float2 *, int, int, int64_t);
+template void multiaxpy_dev<double2>(dwf_ctx *, double2 *, double2 *const *, int, int, double, int64_t);
+template void multiaxpy_dev<float2>(dwf_ctx *, float2 *, float2 *const *, int, int, double, int64_t);
+template void gcr_step<double2>(dwf_ctx *, double2 *, double2 *, double2 *, double2 *, int, int, int64_t);
+template void gcr_step<float2>(dwf_ctx *, float2 *, float2 *, float2 *, float2 *, int, int, int64_t);
 template void gauss_fill<double2>(dwf_ctx *, double2 *, int, int64_t, int, int64_t, bool, uint32_t, uint32_t);
 
 }  // namespace dwf

@@ -10,22 +10,28 @@
 // stores two rows per link and rebuilds the third as conj(row0 x row1).
 //
 // Spin projection: see spin.cuh.
+#include <cstdlib>
+
 #include "spin.cuh"
 
 namespace dwf {
 
 namespace {
 
-// One 4D hop for the thread's (site, s): spinor at neighbour row `p`
-// (already offset to s), stride Ls between components.
-template <int MU, bool ADJ, typename R>
-__device__ __forceinline__ void hop_row(C<R> acc[12], const C<R> *__restrict__ p, int Ls, const C<R> *m, int sig,
-                                        R coef) {
+// One 4D hop for the thread's (site, s): spinor row `p` (already offset to s),
+// component stride LS; the staged link `m` already carries the hop
+// coefficient (-1/2, or +1/2 across an antiperiodic t boundary).
+template <int MU, bool ADJ, typename R, int LS>
+__device__ __forceinline__ void hop_row(C<R> acc[12], const C<R> *__restrict__ p, int ls_rt, const C<R> *m, int sig) {
+    const int Ls = LS > 0 ? LS : ls_rt;
     C<R> v[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = p[k * Ls];
     C<R> h[6], u[6];
     project<MU>(v, sig, h);
+    C<R> mm[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) mm[e] = m[e];
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
@@ -33,29 +39,29 @@ __device__ __forceinline__ void hop_row(C<R> acc[12], const C<R> *__restrict__ p
             C<R> z = mk<R>(0, 0);
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                if (ADJ) cfmac(z, m[b * 3 + a], h[sp * 3 + b]);
-                else cfma(z, m[a * 3 + b], h[sp * 3 + b]);
+                if (ADJ) cfmac(z, mm[b * 3 + a], h[sp * 3 + b]);
+                else cfma(z, mm[a * 3 + b], h[sp * 3 + b]);
             }
             u[sp * 3 + a] = z;
         }
-    reconstruct_add<MU>(acc, u, sig, coef);
+    reconstruct_add<MU>(acc, u, sig, R(1));
 }
 
 // CTA = spb whole 4D sites x Ls threads.  Phase 1 (spb*8 threads): each
-// stages one link (U_mu(x) forward, U_mu(x-mu) backward) into shared memory
-// together with the neighbour's site index and the hop coefficient
-// -1/2 (times -1 across an antiperiodic t boundary).  Phase 2: every thread
-// computes its 5D site.  SHFL: the Ls threads of a site sit inside one warp
-// (Ls divides 32) and the fifth-dimension neighbours come from shuffles.
-template <typename R, bool DAG, bool SHFL>
-__global__ void __launch_bounds__(128) dslash_kernel(C<R> *__restrict__ out, const C<R> *__restrict__ in,
-                                                     const C<R> *__restrict__ U, Geom g, R diag, R mf,
-                                                     int spb, int64_t field) {
-    extern __shared__ unsigned char smem_raw[];
-    C<R> *sU = reinterpret_cast<C<R> *>(smem_raw);               // [spb][8][9]
-    int *sN = reinterpret_cast<int *>(sU + (size_t)spb * 72);       // [spb][8]
-    R *sC = reinterpret_cast<R *>(sN + spb * 8);                    // [spb][8]
-    const int Ls = g.Ls;
+// stages one link (U_mu(x) forward, U_mu(x-mu) backward), scaled by its hop
+// coefficient, into shared memory with the neighbour's site index.  Phase 2:
+// every thread computes its 5D site.  SHFL: the Ls threads of a site sit
+// inside one warp (Ls divides 32) and the fifth-dimension neighbours come
+// from shuffles.  LS > 0: the fifth extent is a compile-time constant, so
+// every component load uses an immediate offset.
+template <typename R, bool DAG, bool SHFL, int LS, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+dslash_kernel(C<R> *__restrict__ out, const C<R> *__restrict__ in, const C<R> *__restrict__ U, Geom g, R diag, R mf,
+              int spb, int64_t field) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<R> *sU = reinterpret_cast<C<R> *>(smem_raw);               // [spb][8][10] (9 used)
+    int *sN = reinterpret_cast<int *>(sU + (size_t)spb * 80);       // [spb][8]
+    const int Ls = LS > 0 ? LS : g.Ls;
     const int V = (int)g.V;
     const int site0 = blockIdx.x * spb;
     const size_t rhs_off = (size_t)blockIdx.y * (size_t)field;
@@ -78,10 +84,10 @@ __global__ void __launch_bounds__(128) dslash_kernel(C<R> *__restrict__ out, con
             const int nb = site + (n - cmu) * stride;
             C<R> m[9];
             LinkIO<R>::load(U, k < 4 ? site : nb, mu, m);
+            const R coef = (mu == 3 && g.ap && wrap) ? R(0.5) : R(-0.5);
 #pragma unroll
-            for (int e = 0; e < 9; ++e) sU[(ls * 8 + k) * 9 + e] = m[e];
+            for (int e = 0; e < 9; ++e) sU[(ls * 8 + k) * 10 + e] = coef * m[e];
             sN[ls * 8 + k] = nb;
-            sC[ls * 8 + k] = (mu == 3 && g.ap && wrap) ? R(0.5) : R(-0.5);
         }
     }
     __syncthreads();
@@ -137,18 +143,17 @@ __global__ void __launch_bounds__(128) dslash_kernel(C<R> *__restrict__ out, con
         acc[up_lo + k] = acc[up_lo + k] + cp * up[k];
         acc[dn_lo + k] = acc[dn_lo + k] + cm * dn[k];
     }
-    const C<R> *sUs = sU + ls * 72;
+    const C<R> *sUs = sU + ls * 80;
     const int *sNs = sN + ls * 8;
-    const R *sCs = sC + ls * 8;
     const int fs = DAG ? +1 : -1;  // sig of the forward hops
-    hop_row<0, false, R>(acc, in + (size_t)sNs[0] * row + s, Ls, sUs + 0 * 9, fs, sCs[0]);
-    hop_row<0, true, R>(acc, in + (size_t)sNs[4] * row + s, Ls, sUs + 4 * 9, -fs, sCs[4]);
-    hop_row<1, false, R>(acc, in + (size_t)sNs[1] * row + s, Ls, sUs + 1 * 9, fs, sCs[1]);
-    hop_row<1, true, R>(acc, in + (size_t)sNs[5] * row + s, Ls, sUs + 5 * 9, -fs, sCs[5]);
-    hop_row<2, false, R>(acc, in + (size_t)sNs[2] * row + s, Ls, sUs + 2 * 9, fs, sCs[2]);
-    hop_row<2, true, R>(acc, in + (size_t)sNs[6] * row + s, Ls, sUs + 6 * 9, -fs, sCs[6]);
-    hop_row<3, false, R>(acc, in + (size_t)sNs[3] * row + s, Ls, sUs + 3 * 9, fs, sCs[3]);
-    hop_row<3, true, R>(acc, in + (size_t)sNs[7] * row + s, Ls, sUs + 7 * 9, -fs, sCs[7]);
+    hop_row<0, false, R, LS>(acc, in + (size_t)sNs[0] * row + s, Ls, sUs + 0 * 10, fs);
+    hop_row<0, true, R, LS>(acc, in + (size_t)sNs[4] * row + s, Ls, sUs + 4 * 10, -fs);
+    hop_row<1, false, R, LS>(acc, in + (size_t)sNs[1] * row + s, Ls, sUs + 1 * 10, fs);
+    hop_row<1, true, R, LS>(acc, in + (size_t)sNs[5] * row + s, Ls, sUs + 5 * 10, -fs);
+    hop_row<2, false, R, LS>(acc, in + (size_t)sNs[2] * row + s, Ls, sUs + 2 * 10, fs);
+    hop_row<2, true, R, LS>(acc, in + (size_t)sNs[6] * row + s, Ls, sUs + 6 * 10, -fs);
+    hop_row<3, false, R, LS>(acc, in + (size_t)sNs[3] * row + s, Ls, sUs + 3 * 10, fs);
+    hop_row<3, true, R, LS>(acc, in + (size_t)sNs[7] * row + s, Ls, sUs + 7 * 10, -fs);
     C<R> *o = out + (size_t)site * row + s;
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[k * Ls] = acc[k];
@@ -161,7 +166,7 @@ void launch(dwf_ctx *c, C<R> *out, const C<R> *in, const C<R> *U, bool dag, int 
                 "lattice too large for 32-bit element offsets of one field");
     // sites per CTA: about 128 threads, staging within 46 KB of shared memory
     int spb = g.Ls >= 128 ? 1 : 128 / g.Ls;
-    const size_t per_site = 72 * sizeof(C<R>) + 8 * sizeof(int) + 8 * sizeof(R);
+    const size_t per_site = 80 * sizeof(C<R>) + 8 * sizeof(int);
     const int max_spb = (int)((46 * 1024) / per_site);
     if (spb > max_spb) spb = max_spb;
     const bool shfl = (32 % g.Ls) == 0;
@@ -171,9 +176,29 @@ void launch(dwf_ctx *c, C<R> *out, const C<R> *in, const C<R> *U, bool dag, int 
     size_t smem = (size_t)spb * per_site;
     int64_t field = g.V * g.Ls * 12;
     R diag = R(5.0 - c->M5), mf = R(c->mf);
-#define DL(D, S) dslash_kernel<R, D, S><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, spb, field)
-    if (dag) { if (shfl) DL(true, true); else DL(true, false); }
-    else { if (shfl) DL(false, true); else DL(false, false); }
+    // register budget: 8 CTAs/SM (64 registers, small spills) or 6 (80);
+    // DWF_DSLASH_MINB=6 selects the latter
+    static const int minb = [] {
+        const char *e = getenv("DWF_DSLASH_MINB");
+        return (e && atoi(e) == 6) ? 6 : 8;
+    }();
+#define DLM(D, S, L, M) dslash_kernel<R, D, S, L, M><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, spb, field)
+#define DL(D, S, L)                                          \
+    do {                                                     \
+        if constexpr (sizeof(R) == 8) DLM(D, S, L, 4);       \
+        else if (minb == 6) DLM(D, S, L, 6);                 \
+        else DLM(D, S, L, 8);                                \
+    } while (0)
+    if (g.Ls == 16) {
+        if (dag) DL(true, true, 16); else DL(false, true, 16);
+    } else if (g.Ls == 8) {
+        if (dag) DL(true, true, 8); else DL(false, true, 8);
+    } else if (dag) {
+        if (shfl) DL(true, true, 0); else DL(true, false, 0);
+    } else {
+        if (shfl) DL(false, true, 0); else DL(false, false, 0);
+    }
+#undef DLM
 #undef DL
     DWF_CHECK_LAUNCH();
 }

@@ -197,6 +197,8 @@ template <typename T> void bzero(dwf_ctx *c, T *x, int64_t n);
 template <typename TO, typename TI> void bcopy(dwf_ctx *c, TO *out, const TI *in, int64_t n);
 // slot[k] (double2 view at double index 2k) = <x, y> = sum conj(x) y
 template <typename TX, typename TY> void bdot(dwf_ctx *c, int slot, const TX *x, const TY *y, int64_t n);
+// slots slot + 2j, slot + 2j + 1 = <V_j, w> for j < k (w read once per 8 vectors)
+template <typename T> void bmultidot(dwf_ctx *c, int slot, T *const *V, int k, const T *w, int64_t n);
 // slot (double at index k) = |x|^2
 template <typename T> void bnorm2(dwf_ctx *c, int slot, const T *x, int64_t n);
 double read_scalar(dwf_ctx *c, int dslot);  // synchronises the stream

@@ -82,8 +82,10 @@ template <typename R> class Runner {
     }
 
     // nu CGNR iterations on A_l x = b.  x_zero: start from x = 0 (else from x).
-    // b_zero: b = 0 (the adaptive setup's A x = 0).
-    void cgnr(int l, T *x, const T *b, int iters, bool x_zero, bool b_zero) {
+    // b_zero: b = 0 (the adaptive setup's A x = 0).  The step coefficients
+    // stay on the device: no host round trip inside the loop.
+    // rtol > 0: also stop once |r| <= rtol |r_0| (tested every 8 iterations).
+    void cgnr(int l, T *x, const T *b, int iters, bool x_zero, bool b_zero, double rtol = 0.0) {
         const int64_t N = n(l);
         T *r = ws(l, 0), *z = ws(l, 1), *p = ws(l, 2), *w = ws(l, 3);
         if (x_zero) {
@@ -97,19 +99,28 @@ template <typename R> class Runner {
         }
         apply(l, z, r, true);
         bcopy<T, T>(c, p, z, N);
-        double zz = norm2(l, z);
-        for (int it = 0; it < iters && zz > 0.0; ++it) {
+        const int S_ZZ0 = 64, S_ZZ1 = 65, S_WW = 66;
+        int izz = S_ZZ0, inew = S_ZZ1;
+        bnorm2<T>(c, izz, z, N);
+        const int S_RR = 67;
+        double r0 = 0.0;
+        if (rtol > 0.0) {
+            bnorm2<T>(c, S_RR, r, N);
+            r0 = std::sqrt(read_scalar(c, S_RR));
+        }
+        for (int it = 0; it < iters; ++it) {
             apply(l, w, p, false);
-            double ww = norm2(l, w);
-            if (!(ww > 0.0)) break;
-            double a = zz / ww;
-            caxpy<T>(c, x, make_double2(a, 0), p, N);
-            caxpy<T>(c, r, make_double2(-a, 0), w, N);
+            bnorm2<T>(c, S_WW, w, N);
+            cg_xr<T>(c, x, r, p, w, izz, S_WW, N);
             if (it + 1 == iters) break;
+            if (rtol > 0.0 && (it + 1) % 8 == 0) {
+                bnorm2<T>(c, S_RR, r, N);
+                if (std::sqrt(read_scalar(c, S_RR)) <= rtol * r0) break;
+            }
             apply(l, z, r, true);
-            double zz2 = norm2(l, z);
-            cxpay<T>(c, p, make_double2(zz2 / zz, 0), z, N);  // p = z + beta p
-            zz = zz2;
+            bnorm2<T>(c, inew, z, N);
+            cg_p<T>(c, p, z, inew, izz, N);
+            std::swap(izz, inew);
         }
     }
 
@@ -148,36 +159,26 @@ template <typename R> class Runner {
         double rn = std::sqrt(norm2(l, r));
         GcrInfo info;
         int k = 0;
-        std::vector<double2> beta(restart);
+        const int S_G = 128, S_WW = 124, S_A = 126;  // scalar slots: Gram-Schmidt coefficients, |w|^2, <w,r>
         while (info.iters < maxit && rn > tol * bnorm) {
             if (pc) vcycle(l, Z[k], r);
             else bcopy<T, T>(c, Z[k], r, N);
             apply(l, W[k], Z[k], false);
-            for (int pass = 0; pass < 2 && k > 0; ++pass) {
-                for (int i = 0; i < k; ++i) bdot<T, T>(c, SLOT_A + 2 * i, W[i], W[k], N);
-                std::vector<double> v(2 * k);
-                read_scalars(c, SLOT_A, 2 * k, v.data());
-                for (int i = 0; i < k; ++i) beta[i] = make_double2(-v[2 * i], -v[2 * i + 1]);
-                for (int i0 = 0; i0 < k; i0 += 32) {
-                    int kk = std::min(32, k - i0);
-                    multiaxpy<T>(c, W[k], beta.data() + i0, W.data() + i0, kk, N);
-                    multiaxpy<T>(c, Z[k], beta.data() + i0, Z.data() + i0, kk, N);
-                }
+            for (int pass = 0; pass < 2 && k > 0; ++pass) {  // classical Gram-Schmidt, twice
+                bmultidot<T>(c, S_G, W.data(), k, W[k], N);
+                multiaxpy_dev<T>(c, W[k], W.data(), k, S_G, -1.0, N);
+                multiaxpy_dev<T>(c, Z[k], Z.data(), k, S_G, -1.0, N);
             }
-            bnorm2<T>(c, SLOT_A, W[k], N);
-            bdot<T, T>(c, SLOT_A + 2, W[k], r, N);
+            bnorm2<T>(c, S_WW, W[k], N);
+            bdot<T, T>(c, S_A, W[k], r, N);
+            gcr_step<T>(c, x, r, Z[k], W[k], S_WW, S_A, N);
             double s[4];
-            read_scalars(c, SLOT_A, 4, s);
+            read_scalars(c, S_WW, 4, s);  // |w|^2, (unused), <w, r>
             double ww = s[0];
             if (!std::isfinite(ww) || !std::isfinite(s[2])) throw Error{DWF_ENAN, "NaN or Inf in GCR"};
             if (!(ww > 0.0)) break;
-            double inv = 1.0 / std::sqrt(ww);
-            rscale<T>(c, W[k], inv, N);
-            rscale<T>(c, Z[k], inv, N);
-            double2 alpha = make_double2(s[2] * inv, s[3] * inv);  // <w_unit, r>
-            caxpy<T>(c, x, alpha, Z[k], N);
-            caxpy<T>(c, r, make_double2(-alpha.x, -alpha.y), W[k], N);
-            double r2 = rn * rn - (alpha.x * alpha.x + alpha.y * alpha.y);
+            double a2 = (s[2] * s[2] + s[3] * s[3]) / ww;
+            double r2 = rn * rn - a2;
             rn = r2 > 0 ? std::sqrt(r2) : 0.0;
             ++info.iters;
             ++k;
@@ -269,7 +270,7 @@ template <typename R> class Runner {
         T *xv = ws(l, 9), *bv = ws(l, 8);
         for (int j = 0; j < L.nadapt; ++j) {
             bcopy<T, double2>(c, xv, v + (int64_t)j * N, N);
-            cgnr(l, xv, nullptr, p.setup_iters0, false, true);
+            cgnr(l, xv, nullptr, p.setup_iters0, false, true, p.setup_tol0);
             store_normalised(l, v + (int64_t)j * N, xv);
         }
         orthonormalise_global(l, v, L.nadapt);
@@ -357,6 +358,67 @@ template <typename R> class Runner {
         return status;
     }
 
+    // The paper's comparison solver (Sec. 3): CG on the normal equations of
+    // the fine operator in precision R.  Every `cycle` iterations a reliable
+    // update folds the low-precision correction into the FP64 solution and
+    // replaces the iterated residual by the FP64 true residual, keeping the
+    // search direction (the Krylov recurrence is not restarted).
+    dwf_status cgnr_solve_one(double2 *b, double2 *x, double tol, int maxiter, int cycle, mg_stats &st) {
+        const int64_t N = n(0);
+        double2 *r64 = mg_ws64(0, 12), *t64 = mg_ws64(0, 13);
+        bnorm2<double2>(c, SLOT_A, b, N);
+        double bn = std::sqrt(read_scalar(c, SLOT_A));
+        if (bn == 0.0) {
+            bzero<double2>(c, x, N);
+            return DWF_OK;
+        }
+        auto true_residual = [&]() {
+            dslash(c, t64, x, false, 1);
+            bcopy<double2, double2>(c, r64, b, N);
+            caxpy<double2>(c, r64, make_double2(-1.0, 0.0), t64, N);
+            bnorm2<double2>(c, SLOT_A, r64, N);
+            double v = read_scalar(c, SLOT_A);
+            if (!std::isfinite(v)) throw Error{DWF_ENAN, "NaN or Inf in the residual"};
+            return std::sqrt(v);
+        };
+        T *r = ws(0, 0), *z = ws(0, 1), *p = ws(0, 2), *w = ws(0, 3), *xr = ws(0, 9);
+        const int S_ZZ0 = 64, S_ZZ1 = 65, S_WW = 66, S_RR = 67;
+        double rn = true_residual();
+        int iters = 0;
+        bcopy<T, double2>(c, r, r64, N);
+        bzero<T>(c, xr, N);
+        apply(0, z, r, true);
+        bcopy<T, T>(c, p, z, N);
+        int izz = S_ZZ0, inew = S_ZZ1;
+        bnorm2<T>(c, izz, z, N);
+        while (rn > tol * bn && iters < maxiter) {
+            apply(0, w, p, false);
+            bnorm2<T>(c, S_WW, w, N);
+            cg_xr<T>(c, xr, r, p, w, izz, S_WW, N);
+            ++iters;
+            bool reliable = (iters % cycle == 0);
+            if (iters % 16 == 0 || reliable) {
+                bnorm2<T>(c, S_RR, r, N);
+                rn = std::sqrt(read_scalar(c, S_RR));
+            }
+            if (reliable || rn <= tol * bn || iters >= maxiter) {
+                caxpy_mixed<double2, T>(c, x, make_double2(1.0, 0.0), xr, N);
+                bzero<T>(c, xr, N);
+                rn = true_residual();
+                bcopy<T, double2>(c, r, r64, N);
+                st.restarts++;
+                if (rn <= tol * bn || iters >= maxiter) break;
+            }
+            apply(0, z, r, true);
+            bnorm2<T>(c, inew, z, N);
+            cg_p<T>(c, p, z, inew, izz, N);
+            std::swap(izz, inew);
+        }
+        st.iters += iters;
+        st.true_res = std::max(st.true_res, rn / bn);
+        return rn <= tol * bn ? DWF_OK : DWF_ENOCONV;
+    }
+
     double2 *mg_ws64(int l, int i) {
         auto &v = mg.ws64[l];
         if ((int)v.size() <= i) v.resize(i + 1);
@@ -383,6 +445,18 @@ dwf_status solve_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, 
         if (s != DWF_OK && worst == DWF_OK) worst = s;
     }
     for (int l = 0; l < MAX_LEVELS; ++l) st.coarse_applies[l] += run.coarse_applies[l];
+    return worst;
+}
+
+template <typename R>
+dwf_status cgnr_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, int maxiter, int nrhs, mg_stats &st) {
+    Runner<R> run(c, mg);
+    dwf_status worst = DWF_OK;
+    const int64_t N = mg.lev[0].lg.nelem;
+    for (int r = 0; r < nrhs; ++r) {
+        dwf_status s = run.cgnr_solve_one(b + r * N, x + r * N, tol, maxiter, 200, st);
+        if (s != DWF_OK && worst == DWF_OK) worst = s;
+    }
     return worst;
 }
 
@@ -563,6 +637,47 @@ void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b) {
     MGState &mg = need_mg(c, 0, 0, 1);
     if (mg.p.smoother_prec == DWF_F32) vcycle_t<float>(c, mg, x, b);
     else vcycle_t<double>(c, mg, x, b);
+}
+
+dwf_status cg_solve_impl(dwf_ctx *c, const void *b, void *x, double tol, int maxiter, int nrhs, dwf_prec prec,
+                         mg_stats *stats, bool host) {
+    DWF_REQUIRE(prec == DWF_F64 || prec == DWF_F32, DWF_EINVAL, "CG precision must be F64 or F32");
+    auto t0 = std::chrono::steady_clock::now();
+    // the solver needs only level-0 workspaces: a private state when no setup exists
+    MGState local;
+    MGState *mg = c->mg;
+    if (!mg) {
+        mg = &local;
+        Level &L0 = local.lev[0];
+        L0.index = 0;
+        L0.lg.g = c->g;
+        L0.lg.ncomp = 12;
+        L0.lg.nelem = c->g.V * 12 * c->g.Ls;
+        local.nlevels = 1;
+    }
+    mg_stats st;
+    std::memset(&st, 0, sizeof(st));
+    long long a64 = c->applies64, a32 = c->applies32;
+    const int64_t N = c->g.V * 12 * c->g.Ls;
+    DevBuf bd, xd;
+    double2 *bp = (double2 *)b, *xp = (double2 *)x;
+    if (host) {
+        bd.alloc(sizeof(double2) * N * nrhs);
+        xd.alloc(sizeof(double2) * N * nrhs);
+        DWF_CUDA(cudaMemcpyAsync(bd.p, b, bd.bytes, cudaMemcpyDefault, c->stream));
+        DWF_CUDA(cudaMemcpyAsync(xd.p, x, xd.bytes, cudaMemcpyDefault, c->stream));
+        bp = bd.as<double2>();
+        xp = xd.as<double2>();
+    }
+    dwf_status s = (prec == DWF_F32) ? cgnr_t<float>(c, *mg, bp, xp, tol, maxiter, nrhs, st)
+                                     : cgnr_t<double>(c, *mg, bp, xp, tol, maxiter, nrhs, st);
+    if (host) DWF_CUDA(cudaMemcpyAsync(x, xd.p, xd.bytes, cudaMemcpyDefault, c->stream));
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+    st.fine_applies_f64 = c->applies64 - a64;
+    st.fine_applies_f32 = c->applies32 - a32;
+    st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = st;
+    return s;
 }
 
 }  // namespace dwf

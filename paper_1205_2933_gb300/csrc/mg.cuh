@@ -50,6 +50,8 @@ int mg_nlevels_minus1(dwf_ctx *c);
 dwf_status mg_setup_impl(dwf_ctx *c, int levels, const int *nvec, const int (*block)[4], const mg_params &p,
                          const void *start, bool start_on_host);
 dwf_status mg_solve_impl(dwf_ctx *c, const void *b, void *x, double tol, int nrhs, mg_stats *stats, bool host);
+dwf_status cg_solve_impl(dwf_ctx *c, const void *b, void *x, double tol, int maxiter, int nrhs, dwf_prec prec,
+                         mg_stats *stats, bool host);
 // component calls of the C ABI (see dwfmg.h); throw Error on bad arguments
 void mg_level_info_impl(dwf_ctx *c, int level, int dims[4], int *ncomp);
 void mg_get_vectors_impl(dwf_ctx *c, int level, double2 *out);
@@ -89,6 +91,11 @@ template <typename T, typename U> void caxpy_mixed(dwf_ctx *c, T *y, double2 a, 
 // w += sum_i beta_i V_i, k <= 32 (pointers and coefficients from the host)
 template <typename T> void multiaxpy(dwf_ctx *c, T *w, const double2 *beta, T *const *V, int k, int64_t n);
 constexpr int MAX_RESTART = 64;
+// device-coefficient solver updates (scalar slots index ctx->scal)
+template <typename T> void cg_xr(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int izz, int iww, int64_t n);
+template <typename T> void cg_p(dwf_ctx *c, T *p, const T *z, int inew, int iold, int64_t n);
+template <typename T> void multiaxpy_dev(dwf_ctx *c, T *w, T *const *V, int k, int ibase, double sgn, int64_t n);
+template <typename T> void gcr_step(dwf_ctx *c, T *x, T *r, T *z, T *w, int iww, int ia, int64_t n);
 // x = a * x + b * y (real a, complex b) fused for two pairs: used by GCR updates
 template <typename T> void gauss_fill(dwf_ctx *c, double2 *out, int nfields, int64_t nelem, int Ls, int64_t V,
                                       bool canonical_fine, uint32_t seed, uint32_t stream);

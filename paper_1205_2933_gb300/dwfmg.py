@@ -30,6 +30,7 @@ class mg_params(ctypes.Structure):
         ("outer_restart", ctypes.c_int),
         ("outer_maxiter", ctypes.c_int),
         ("setup_iters0", ctypes.c_int),
+        ("setup_tol0", ctypes.c_double),
         ("setup_sweeps", ctypes.c_int),
         ("setup_sweep_iters", ctypes.c_int),
         ("setup_sweep_tol", ctypes.c_double),
@@ -92,6 +93,8 @@ def _load():
     L.mg_prolong.argtypes = [vp, i, vp, vp]
     L.mg_coarse_apply.argtypes = [vp, i, vp, vp, i, st]
     L.mg_vcycle.argtypes = [vp, vp, vp]
+    L.dwf_cg_solve.argtypes = [vp, vp, vp, ctypes.c_double, i, i, st, ctypes.POINTER(mg_stats)]
+    L.dwf_cg_solve.restype = st
     L.dwf_profile.argtypes = [vp, i]
     L.dwf_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
     L.dwf_launch_count.argtypes = []
@@ -177,6 +180,15 @@ def mg_solve(ctx, b, x, tol, nrhs=1, check=True) -> mg_stats:
     status = _lib.mg_solve(ctx, _ptr(b), _ptr(x), float(tol), int(nrhs), ctypes.byref(st))
     if check:
         _check(status, "mg_solve")
+    st.status = status
+    return st
+
+
+def dwf_cg_solve(ctx, b, x, tol, maxiter, nrhs=1, prec=DWF_F32, check=True) -> mg_stats:
+    st = mg_stats()
+    status = _lib.dwf_cg_solve(ctx, _ptr(b), _ptr(x), float(tol), int(maxiter), int(nrhs), prec, ctypes.byref(st))
+    if check:
+        _check(status, "dwf_cg_solve")
     st.status = status
     return st
 
