@@ -135,6 +135,7 @@ def gen_inputs(nrhs, rank=0):
 
 
 def mixed_params(G):
+    """Mixed precision: FP32 fine V-cycle, BF16 coarse stencil, FP64 outer GCR."""
     p = G.mg_default_params()
     p.smoother_prec = G.DWF_F32
     p.coarse_prec[0] = G.DWF_BF16

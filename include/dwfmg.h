@@ -88,8 +88,8 @@ typedef struct {
     int coarse_restart;     /* GCR restart length of S2 (16) */
     int outer_restart;      /* outer flexible GCR restart length, <= 64 (20) */
     int outer_maxiter;      /* (500) */
-    int setup_iters0;       /* CGNR iterations on D x = 0 for the initial vectors, at most (500) */
-    double setup_tol0;      /* ... or until |D x| <= setup_tol0 |D x_0|, tested every 8 iterations (1e-5) */
+    int setup_iters0;       /* CGNR iterations on D x = 0 for the initial vectors, at most (1000) */
+    double setup_tol0;      /* ... or until |D x| <= setup_tol0 |D x_0|, tested every 8 iterations (1e-6) */
     int setup_sweeps;       /* inverse-iteration sweeps with the current multigrid (0) */
     int setup_sweep_iters;  /* MG-GCR iterations per vector and sweep, at most (8) */
     double setup_sweep_tol; /* MG-GCR relative tolerance of a sweep's solve D x = v (0.1) */

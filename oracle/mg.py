@@ -434,8 +434,8 @@ class MGParams:
     coarsest_tol: float = 0.1          # S2 on the coarsest level
     coarsest_maxiter: int = 64
     coarse_restart: int = 16
-    setup_iters0: int = 500            # CGNR iterations on A x = 0 for the initial vectors, at most
-    setup_tol0: float = 1e-5           # ... or until |A x| <= setup_tol0 |A x0| (tested every 8)
+    setup_iters0: int = 1000           # CGNR iterations on A x = 0 for the initial vectors, at most
+    setup_tol0: float = 1e-6           # ... or until |A x| <= setup_tol0 |A x0| (tested every 8)
     setup_sweeps: int = 0              # inverse-iteration sweeps with the current MG
     setup_sweep_iters: int = 8         # MG-GCR iterations per vector per sweep, at most
     setup_sweep_tol: float = 0.1       # MG-GCR relative tolerance of a sweep's solve

@@ -53,8 +53,8 @@ void mg_default_params(mg_params *p) {
     p->coarse_restart = 16;
     p->outer_restart = 20;
     p->outer_maxiter = 500;
-    p->setup_iters0 = 500;
-    p->setup_tol0 = 1e-5;
+    p->setup_iters0 = 1000;
+    p->setup_tol0 = 1e-6;
     p->setup_sweeps = 0;
     p->setup_sweep_iters = 8;
     p->setup_sweep_tol = 0.1;

@@ -223,8 +223,33 @@ template <typename R> class Runner {
     void coarse_solve(int l, T *x, const T *b) {
         const mg_params &p = mg.p;
         bool coarsest = (l == mg.nlevels - 1);
+        Level &L = mg.lev[l];
+        if (coarsest && coarse_gcr_fused_ok(L, p.coarse_restart)) {
+            const int64_t N = n(l);
+            const size_t zb = sizeof(T) * N * p.coarse_restart;
+            if (L.cgZ.bytes < zb) { L.cgZ.alloc(zb); L.cgW.alloc(zb); }
+            if (!L.cgPart.p) L.cgPart.alloc(coarse_gcr_part_bytes(c));
+            if (!L.cgIters.p) {
+                L.cgIters.alloc(sizeof(int));
+                DWF_CUDA(cudaMemsetAsync(L.cgIters.p, 0, sizeof(int), c->stream));
+            }
+            coarse_gcr_fused<R>(c, L, x, b, ws(l, 10), L.cgZ.as<T>(), L.cgW.as<T>(), L.cgPart.as<double2>(),
+                                L.cgIters.as<int>(), p.coarsest_tol, p.coarsest_maxiter, p.coarse_restart);
+            return;
+        }
         gcr(l, x, b, coarsest ? p.coarsest_tol : p.coarse_tol, coarsest ? p.coarsest_maxiter : p.coarse_maxiter,
             p.coarse_restart, !coarsest, true, false);
+    }
+
+    // iterations run by the fused coarsest solver since the last call (resets the counter)
+    long long fused_iters(int l) {
+        Level &L = mg.lev[l];
+        if (!L.cgIters.p) return 0;
+        int v = 0;
+        DWF_CUDA(cudaMemcpyAsync(&v, L.cgIters.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        DWF_CUDA(cudaStreamSynchronize(c->stream));
+        DWF_CUDA(cudaMemsetAsync(L.cgIters.p, 0, sizeof(int), c->stream));
+        return v;
     }
 
     // normalise x (level l) and store it as FP64 into dst
@@ -384,6 +409,7 @@ template <typename R> class Runner {
         T *r = ws(0, 0), *z = ws(0, 1), *p = ws(0, 2), *w = ws(0, 3), *xr = ws(0, 9);
         const int S_ZZ0 = 64, S_ZZ1 = 65, S_WW = 66, S_RR = 67;
         double rn = true_residual();
+        double r_last = rn;
         int iters = 0;
         bcopy<T, double2>(c, r, r64, N);
         bzero<T>(c, xr, N);
@@ -400,11 +426,14 @@ template <typename R> class Runner {
             if (iters % 16 == 0 || reliable) {
                 bnorm2<T>(c, S_RR, r, N);
                 rn = std::sqrt(read_scalar(c, S_RR));
+                // reliable update once the iterated residual fell by 10x since the last one
+                if (rn < 0.1 * r_last) reliable = true;
             }
             if (reliable || rn <= tol * bn || iters >= maxiter) {
                 caxpy_mixed<double2, T>(c, x, make_double2(1.0, 0.0), xr, N);
                 bzero<T>(c, xr, N);
                 rn = true_residual();
+                r_last = rn;
                 bcopy<T, double2>(c, r, r64, N);
                 st.restarts++;
                 if (rn <= tol * bn || iters >= maxiter) break;
@@ -444,7 +473,10 @@ dwf_status solve_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, 
         dwf_status s = run.solve_one(b + r * N, x + r * N, tol, st);
         if (s != DWF_OK && worst == DWF_OK) worst = s;
     }
-    for (int l = 0; l < MAX_LEVELS; ++l) st.coarse_applies[l] += run.coarse_applies[l];
+    for (int l = 0; l < MAX_LEVELS; ++l) {
+        long long f = (l < mg.nlevels) ? run.fused_iters(l) : 0;
+        st.coarse_applies[l] += run.coarse_applies[l] + f;
+    }
     return worst;
 }
 

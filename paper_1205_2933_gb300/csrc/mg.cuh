@@ -34,6 +34,8 @@ struct Level {
     // block reductions scratch: [Vc][nv][nv] complex FP64
     DevBuf G, F, Rinv;
     DevBuf info;           // int per coarse site: Cholesky status
+    // fused coarsest-level GCR: contiguous direction vectors, partial sums, counter
+    DevBuf cgZ, cgW, cgPart, cgIters;
 };
 
 struct MGState {
@@ -81,6 +83,13 @@ template <typename R> void coarse_apply(dwf_ctx *c, const Level &L, C<R> *y, con
 template <typename R> void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, const C<R> *Q, C<R> *W);
 // refresh the reduced-precision copies of Y on level l
 void convert_coarse_links(dwf_ctx *c, Level &L);
+
+// ---- coarse_gcr.cu ----  fused coarsest-level GCR (one cooperative launch)
+bool coarse_gcr_fused_ok(const Level &L, int restart);
+size_t coarse_gcr_part_bytes(dwf_ctx *c);
+template <typename R>
+void coarse_gcr_fused(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, C<R> *r, C<R> *Z, C<R> *W, double2 *part,
+                      int *iters, double tol, int maxiter, int restart);
 
 // ---- blas2.cu ----  (host scalars; FP64 accumulate inside reductions)
 template <typename T> void caxpy(dwf_ctx *c, T *y, double2 a, const T *x, int64_t n);       // y += a x

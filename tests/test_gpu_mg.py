@@ -246,7 +246,7 @@ def test_solve_host_buffers_and_multi_rhs(G):
 def test_three_level_solve(G):
     """Recursion (Sec. 2): S2 is a V-cycle of the second coarse level."""
     c = Case(G, dims=(4, 4, 4, 8), Ls=4, mf=0.1, nvec=[8, 8], block=[(2, 2, 2, 2), (2, 2, 2, 2)],
-             setup_sweeps=1)
+             setup_sweeps=1, setup_iters0=20, setup_tol0=0.0)
     from gpu_util import to_internal, to_canonical, rel_norm
     b = I.gaussian_source(c.dims, c.Ls, 2)
     bt = to_internal(c.ctx, b)
