@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="also time the plain FP64 method (1 solve)")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="profiling mode: setup, then one solve inside cudaProfilerStart/Stop (for ncu)")
+    ap.add_argument("--dslash-only", action="store_true",
+                    help="profiling mode: a few FP32 Dslash applications of the workload (for ncu)")
     return ap.parse_args()
 
 
@@ -191,10 +195,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_modes(args):
+    """Small commands for ncu captures of the workload's kernels."""
+    import torch
+    from paper_1205_2933_gb300 import dwfmg as G
+    U, bs = gen_inputs(1)
+    ctx = G.Context(DIMS, LS, M5, MF, torch.from_numpy(U).cuda())
+    canon = torch.from_numpy(bs).cuda()
+    if args.dslash_only:
+        f = torch.empty(ctx.field_elems, dtype=torch.complex64, device="cuda")
+        G.dwf_pack(ctx.h, f, canon, G.DWF_F32, 1)
+        out = torch.empty_like(f)
+        for _ in range(4):
+            G.dwf_apply(ctx.h, out, f, G.DWF_F32)
+        torch.cuda.synchronize()
+        print("dslash-only ok")
+    else:
+        b = torch.empty(ctx.field_elems, dtype=torch.complex128, device="cuda")
+        G.dwf_pack(ctx.h, b, canon, G.DWF_F64, 1)
+        G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], mixed_params(G))
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        st = G.mg_solve(ctx.h, b, x, TOL, 1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("profile-solve ok", st.iters, st.true_res)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_solve or args.dslash_only:
+        profile_modes(args)
         return
     import torch
     from paper_1205_2933_gb300 import dwfmg as G

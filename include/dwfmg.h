@@ -96,6 +96,8 @@ typedef struct {
     int split;              /* 1: each vector split into Gamma = +-1 halves, Nvec/2 vectors (1) */
     dwf_prec smoother_prec; /* F64 (plain method) or F32 (mixed) for the fine V-cycle (F64) */
     dwf_prec coarse_prec[4];/* link precision of each coarse level's stencil: F64, F32, BF16, F16 */
+    dwf_prec basis_prec;    /* with smoother_prec = F32: F16 keeps an FP16 copy of the block basis for
+                               the V-cycle's restriction and prolongation (FP32 arithmetic), F32 none (F32) */
     uint32_t seed;          /* Philox seed of the random start vectors when none are given */
 } mg_params;
 

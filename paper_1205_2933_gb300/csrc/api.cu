@@ -61,6 +61,7 @@ void mg_default_params(mg_params *p) {
     p->split = 1;
     p->smoother_prec = DWF_F64;
     for (int i = 0; i < 4; ++i) p->coarse_prec[i] = DWF_F64;
+    p->basis_prec = DWF_F32;
     p->seed = 1u;
 }
 

@@ -63,28 +63,51 @@ __device__ __forceinline__ int64_t nbr(const Geom &g, int64_t site, int mu, int 
     return site_index(g, c);
 }
 
-// out[e] = (A in)[e] for the owned elements
+// out = A in on the owned sites [s0, s1): one warp per site, lane l holds
+// column l of every link row (coalesced loads) and the 9 neighbour values
+// in[nbr_d][l]; each output row is a warp-wide sum over l.
 template <typename R, typename LT, int NV>
-__device__ void apply_owned(const Args<R, LT> &a, C<R> *out, const C<R> *in, int64_t e0, int64_t e1) {
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) {
-        const int64_t site = e / NV;
-        const int k = (int)(e - site * NV);
-        R accx = 0, accy = 0;
+__device__ void apply_owned(const Args<R, LT> &a, C<R> *out, const C<R> *in, int64_t s0, int64_t s1) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool on = lane < NV;
+    for (int64_t site = s0 + warp; site < s1; site += CT / 32) {
+        C<R> xv[9];
+#pragma unroll
         for (int d = 0; d < 9; ++d) {
             int64_t o = site;
             if (d > 0) o = nbr(a.g, site, (d - 1) >> 1, ((d - 1) & 1) ? -1 : +1);
-            const C<R> *v = in + o * NV;
-            const int64_t row = ((site * 9 + d) * NV + k) * NV;
-#pragma unroll 8
-            for (int l = 0; l < NV; ++l) {
-                C<R> y = LRead<LT>::template get<R>(a.Y, row + l);
-                C<R> u = v[l];
-                accx += y.x * u.x - y.y * u.y;
-                accy += y.x * u.y + y.y * u.x;
+            xv[d] = on ? in[o * NV + lane] : mk<R>(0, 0);
+        }
+        const LT *Ys = a.Y + site * 9 * NV * NV;
+        for (int k = 0; k < NV; k += 2) {
+            R r0 = 0, i0 = 0, r1 = 0, i1 = 0;
+            if (on) {
+#pragma unroll
+                for (int d = 0; d < 9; ++d) {
+                    C<R> y0 = LRead<LT>::template get<R>(Ys, ((int64_t)d * NV + k) * NV + lane);
+                    C<R> y1 = LRead<LT>::template get<R>(Ys, ((int64_t)d * NV + k + 1) * NV + lane);
+                    r0 += y0.x * xv[d].x - y0.y * xv[d].y;
+                    i0 += y0.x * xv[d].y + y0.y * xv[d].x;
+                    r1 += y1.x * xv[d].x - y1.y * xv[d].y;
+                    i1 += y1.x * xv[d].y + y1.y * xv[d].x;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+                i0 += __shfl_xor_sync(0xffffffffu, i0, o);
+                r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+                i1 += __shfl_xor_sync(0xffffffffu, i1, o);
+            }
+            if (lane == 0) {
+                out[site * NV + k] = mk<R>(r0, i0);
+                out[site * NV + k + 1] = mk<R>(r1, i1);
             }
         }
-        out[e] = mk<R>(accx, accy);
     }
+    // rows were written by lane 0 of each warp; the element loops that follow
+    // read them from other threads of the CTA
+    __syncthreads();
 }
 
 // Sum over CTAs of part[slot][i][*] for i < k into tot[i] (shared), same
@@ -115,9 +138,11 @@ __global__ void __launch_bounds__(CT) coarse_gcr_kernel(Args<R, LT> a) {
     __shared__ double2 tot[MAXR + 2];
     const int nb = gridDim.x;
     const int64_t N = a.g.V * NV;
-    const int64_t chunk = (N + nb - 1) / nb;
-    const int64_t e0 = blockIdx.x * chunk;
-    const int64_t e1 = e0 + chunk < N ? e0 + chunk : N;
+    const int64_t sites = (a.g.V + nb - 1) / nb;   // whole sites per CTA
+    const int64_t s0 = blockIdx.x * sites;
+    const int64_t s1 = s0 + sites < a.g.V ? s0 + sites : a.g.V;
+    const int64_t e0 = s0 * NV;
+    const int64_t e1 = s1 > s0 ? s1 * NV : e0;
     const size_t ps = (size_t)(MAXR + 2) * nb;   // size of one partial-sum region
     double2 *P[3] = {a.part, a.part + ps, a.part + 2 * ps};
 
@@ -167,7 +192,7 @@ __global__ void __launch_bounds__(CT) coarse_gcr_kernel(Args<R, LT> a) {
             for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) Zk[e] = a.r[e];
             __threadfence();
             grid.sync();
-            apply_owned<R, LT, NV>(a, Wk, Zk, e0, e1);
+            apply_owned<R, LT, NV>(a, Wk, Zk, s0, s1);
             for (int pass = 0; pass < 2 && k > 0; ++pass) {
                 for (int i = 0; i < k; ++i) v[i] = make_double2(0, 0);
                 for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) {
@@ -224,7 +249,7 @@ __global__ void __launch_bounds__(CT) coarse_gcr_kernel(Args<R, LT> a) {
                 // true residual r = b - A x
                 __threadfence();
                 grid.sync();
-                apply_owned<R, LT, NV>(a, a.r, a.x, e0, e1);
+                apply_owned<R, LT, NV>(a, a.r, a.x, s0, s1);
                 v[0] = make_double2(0, 0);
                 for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) {
                     C<R> bv = a.b[e], ax = a.r[e];

@@ -211,8 +211,24 @@ void dslash(dwf_ctx *c, double2 *out, const double2 *in, bool dag, int nrhs) {
     c->applies64 += nrhs;
 }
 
+bool dslash_pair_supported(int Ls);
+void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb);
+
 void dslash(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs) {
     ProfScope ps(c, K_DSLASH_F32);
+    // two slices per thread with packed FP32x2 arithmetic where Ls allows;
+    // DWF_DSLASH_PAIR=0 selects the one-slice kernel
+    static const int pair_minb = [] {
+        const char *e = getenv("DWF_DSLASH_PAIR");
+        if (e && atoi(e) == 0) return 0;
+        const char *m = getenv("DWF_DSLASH_PAIR_MINB");
+        return (m && atoi(m) == 5) ? 5 : 4;
+    }();
+    if (pair_minb && dslash_pair_supported(c->g.Ls)) {
+        dslash_pair_f32(c, out, in, dag, nrhs, pair_minb);
+        c->applies32 += nrhs;
+        return;
+    }
     launch<float>(c, out, in, c->U32.as<float2>(), dag, nrhs);
     c->applies32 += nrhs;
 }

@@ -125,8 +125,12 @@ template <typename R> class Runner {
     }
 
     // Flexible GCR on level l, right-preconditioned by the V-cycle of level l
-    // when pc is set.  Modified Gram-Schmidt on the stored directions as in
-    // the oracle, done as classical Gram-Schmidt twice (same span, FP64 dots).
+    // when pc is set.  The directions w_k = A z_k are orthonormalised by
+    // classical Gram-Schmidt (a second pass only when the first removed more
+    // than 3/4 of |w|^2); the preconditioned vectors z_k are kept raw and the
+    // triangular Gram-Schmidt transform T is kept on the host, so that the
+    // solution update x += sum_k alpha_k T^-1 z is one pass per cycle.  This
+    // spans the same directions as the oracle's modified Gram-Schmidt GCR.
     GcrInfo gcr(int l, T *x, const T *b, double tol, int maxit, int restart, bool pc, bool x_zero, bool b_zero) {
         const int64_t N = n(l);
         DWF_REQUIRE(restart >= 1 && restart <= MAX_RESTART + 1, DWF_EINVAL, "GCR restart out of range");
@@ -159,35 +163,74 @@ template <typename R> class Runner {
         double rn = std::sqrt(norm2(l, r));
         GcrInfo info;
         int k = 0;
-        const int S_G = 128, S_WW = 124, S_A = 126;  // scalar slots: Gram-Schmidt coefficients, |w|^2, <w,r>
+        // host copy of the transform: Tm[i][j] (i <= j), and the step coefficients
+        std::vector<double2> Tm((size_t)restart * restart), alpha(restart);
+        auto finish_cycle = [&]() {
+            if (k == 0) return;
+            // gamma = T^-1 alpha (back substitution), x += sum_j gamma_j z_j
+            std::vector<double2> g(k);
+            for (int i = k - 1; i >= 0; --i) {
+                double2 s = alpha[i];
+                for (int j = i + 1; j < k; ++j) {
+                    double2 t = cmul(Tm[(size_t)i * restart + j], g[j]);
+                    s.x -= t.x;
+                    s.y -= t.y;
+                }
+                double d = Tm[(size_t)i * restart + i].x;
+                g[i] = make_double2(s.x / d, s.y / d);
+            }
+            for (int j0 = 0; j0 < k; j0 += 32) {
+                int kk = std::min(32, k - j0);
+                multiaxpy<T>(c, x, g.data() + j0, Z.data() + j0, kk, N);
+            }
+        };
+        const int S_G = 128, S_WW = 124, S_A = 126;  // scalar slots
         while (info.iters < maxit && rn > tol * bnorm) {
             if (pc) vcycle(l, Z[k], r);
             else bcopy<T, T>(c, Z[k], r, N);
             apply(l, W[k], Z[k], false);
-            for (int pass = 0; pass < 2 && k > 0; ++pass) {  // classical Gram-Schmidt, twice
-                bmultidot<T>(c, S_G, W.data(), k, W[k], N);
-                multiaxpy_dev<T>(c, W[k], W.data(), k, S_G, -1.0, N);
-                multiaxpy_dev<T>(c, Z[k], Z.data(), k, S_G, -1.0, N);
+            for (int i = 0; i <= k; ++i) Tm[(size_t)i * restart + k] = make_double2(0, 0);
+            // <W_i, W_k> for i < k and |W_k|^2 (as <W_k, W_k>) in one pass
+            for (int pass = 0; pass < 2; ++pass) {
+                bmultidot<T>(c, S_G, W.data(), k + 1, W[k], N);
+                if (k > 0) multiaxpy_dev<T>(c, W[k], W.data(), k, S_G, -1.0, N);
+                std::vector<double> v(2 * (k + 1));
+                read_scalars(c, S_G, 2 * (k + 1), v.data());
+                double before = v[2 * k], removed = 0.0;
+                for (int i = 0; i < k; ++i) {
+                    Tm[(size_t)i * restart + k].x += v[2 * i];
+                    Tm[(size_t)i * restart + k].y += v[2 * i + 1];
+                    removed += v[2 * i] * v[2 * i] + v[2 * i + 1] * v[2 * i + 1];
+                }
+                if (!std::isfinite(before)) throw Error{DWF_ENAN, "NaN or Inf in GCR"};
+                if (k == 0 || removed < 0.75 * before) break;  // orthogonal enough
             }
             bnorm2<T>(c, S_WW, W[k], N);
             bdot<T, T>(c, S_A, W[k], r, N);
-            gcr_step<T>(c, x, r, Z[k], W[k], S_WW, S_A, N);
             double s[4];
             read_scalars(c, S_WW, 4, s);  // |w|^2, (unused), <w, r>
             double ww = s[0];
             if (!std::isfinite(ww) || !std::isfinite(s[2])) throw Error{DWF_ENAN, "NaN or Inf in GCR"};
             if (!(ww > 0.0)) break;
-            double a2 = (s[2] * s[2] + s[3] * s[3]) / ww;
+            double nw = std::sqrt(ww);
+            Tm[(size_t)k * restart + k] = make_double2(nw, 0.0);
+            alpha[k] = make_double2(s[2] / nw, s[3] / nw);  // <w_unit, r>
+            // w_k <- w_k / |w_k|;  r -= alpha_k w_k
+            rscale<T>(c, W[k], 1.0 / nw, N);
+            caxpy<T>(c, r, make_double2(-alpha[k].x, -alpha[k].y), W[k], N);
+            double a2 = alpha[k].x * alpha[k].x + alpha[k].y * alpha[k].y;
             double r2 = rn * rn - a2;
             rn = r2 > 0 ? std::sqrt(r2) : 0.0;
             ++info.iters;
             ++k;
-            if (k == restart || rn <= tol * bnorm) {
+            if (k == restart || rn <= tol * bnorm || info.iters >= maxit) {
+                finish_cycle();
                 residual();
                 rn = std::sqrt(norm2(l, r));
                 k = 0;
             }
         }
+        finish_cycle();
         info.rel = rn / bnorm;
         return info;
     }
@@ -205,12 +248,12 @@ template <typename R> class Runner {
             cgnr(l, x, b, p.nu_pre, true, false);
             apply(l, res, x, false);
             cxpay<T>(c, res, make_double2(-1.0, 0.0), b, N);  // b - A x1
-            restrict_<R>(c, L, b2, res, Q(l));
+            restrict_any(L, b2, res, l);
         } else {
-            restrict_<R>(c, L, b2, b, Q(l));
+            restrict_any(L, b2, b, l);
         }
         coarse_solve(l + 1, x2, b2);
-        prolong_<R>(c, L, x, x2, Q(l), p.nu_pre > 0);
+        prolong_any(L, x, x2, l, p.nu_pre > 0);
         if (p.nu_post > 0) {
             apply(l, res, x, false);
             bcopy<T, T>(c, b3, b, N);
@@ -218,6 +261,18 @@ template <typename R> class Runner {
             cgnr(l, sm, b3, p.nu_post, true, false);
             caxpy<T>(c, x, make_double2(1.0, 0.0), sm, N);
         }
+    }
+
+    // transfers with the FP16 basis copy when there is one (FP32 V-cycle only)
+    void restrict_any(const Level &L, T *cout, const T *fin, int l) {
+        if constexpr (std::is_same<R, float>::value)
+            if (L.Q16.p) return restrict_h(c, L, cout, fin, L.Q16.as<__half2>());
+        restrict_<R>(c, L, cout, fin, Q(l));
+    }
+    void prolong_any(const Level &L, T *fout, const T *cin, int l, bool acc) {
+        if constexpr (std::is_same<R, float>::value)
+            if (L.Q16.p) return prolong_h(c, L, fout, cin, L.Q16.as<__half2>(), acc);
+        prolong_<R>(c, L, fout, cin, Q(l), acc);
     }
 
     void coarse_solve(int l, T *x, const T *b) {
@@ -271,6 +326,12 @@ template <typename R> class Runner {
             throw Error{DWF_EBREAKDOWN, "block Gram-Schmidt met linearly dependent near-null vectors"};
         DevBuf W(sizeof(T) * N * L.nv);
         build_coarse_from<R>(c, L, mg.lev[l + 1], Q(l), W.as<T>());
+        if (std::is_same<R, float>::value && mg.p.basis_prec == DWF_F16) {
+            if (L.Q16.bytes < sizeof(__half2) * N * L.nv) L.Q16.alloc(sizeof(__half2) * N * L.nv);
+            basis_to_half(c, L.Q16.as<__half2>(), L.Q32.as<float2>(), N * L.nv);
+        } else {
+            L.Q16.release();
+        }
         mg.nlevels = l + 2;
         DWF_CUDA(cudaStreamSynchronize(c->stream));
     }

@@ -27,6 +27,7 @@ struct Level {
     int nv = 0;            // coarse components per site of level + 1
     int nadapt = 0;        // adaptive vectors (nv / 2 when split)
     DevBuf Q64, Q32;       // nv block-orthonormalised fields of this level
+    DevBuf Q16;            // FP16 copy used by the FP32 V-cycle's transfers (basis_prec = F16)
     DevBuf vec64;          // nadapt adaptive vectors (unsplit, normalised), FP64
     // coarse operator of this level (levels >= 1): [V][9][n][n] complex
     DevBuf Y64, Y32, Y16;  // Y16 holds bf16 or fp16 pairs per coarse_prec
@@ -67,6 +68,10 @@ void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b);
 // c[Vc][nv] = R f  (R = P^+) ; f = P c (accumulate: f += P c)
 template <typename R> void restrict_(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const C<R> *Q);
 template <typename R> void prolong_(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const C<R> *Q, bool accumulate);
+// the same with an FP16 copy of the basis (FP32 fields and arithmetic)
+void restrict_h(dwf_ctx *c, const Level &L, float2 *cout, const float2 *fin, const __half2 *Q);
+void prolong_h(dwf_ctx *c, const Level &L, float2 *fout, const float2 *cin, const __half2 *Q, bool accumulate);
+void basis_to_half(dwf_ctx *c, __half2 *out, const float2 *in, int64_t n);
 // G[Vc][nv][nv] = block inner products <A_k, B_l> over each block (FP64 accumulate)
 template <typename R> void block_gram(dwf_ctx *c, const Level &L, double2 *G, const C<R> *A, const C<R> *B);
 // In-place block orthonormalisation of the nv fields Q (CholQR2, FP64); returns false on breakdown

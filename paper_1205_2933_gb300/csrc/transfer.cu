@@ -63,9 +63,18 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 
 constexpr int TT = 256;  // threads per CTA of the block kernels
 
-template <typename R, int NV>
+// basis element in the vector precision; the basis may be stored in FP16
+template <typename R, typename QT> struct QLoad;
+template <typename R> struct QLoad<R, C<R>> {
+    static __device__ __forceinline__ C<R> get(const C<R> *Q, int64_t i) { return Q[i]; }
+};
+template <> struct QLoad<float, __half2> {
+    static __device__ __forceinline__ float2 get(const __half2 *Q, int64_t i) { return __half22float2(Q[i]); }
+};
+
+template <typename R, typename QT, int NV>
 __global__ void __launch_bounds__(TT) restrict_kernel(C<R> *__restrict__ cout, const C<R> *__restrict__ f,
-                                                      const C<R> *__restrict__ Q, BlockMap m) {
+                                                      const QT *__restrict__ Q, BlockMap m) {
     __shared__ C<R> red[TT / 32][NV];
     const int64_t xc = blockIdx.x;
     const int64_t ne = m.bsites * m.run;
@@ -76,7 +85,7 @@ __global__ void __launch_bounds__(TT) restrict_kernel(C<R> *__restrict__ cout, c
         int64_t a = block_elem_addr(m, xc, e);
         C<R> v = f[a];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) cfmac(acc[k], Q[k * m.nelem + a], v);
+        for (int k = 0; k < NV; ++k) cfmac(acc[k], QLoad<R, QT>::get(Q, k * m.nelem + a), v);
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
@@ -93,9 +102,9 @@ __global__ void __launch_bounds__(TT) restrict_kernel(C<R> *__restrict__ cout, c
     }
 }
 
-template <typename R, int NV>
+template <typename R, typename QT, int NV>
 __global__ void __launch_bounds__(TT) prolong_kernel(C<R> *__restrict__ f, const C<R> *__restrict__ cin,
-                                                     const C<R> *__restrict__ Q, BlockMap m, int accumulate) {
+                                                     const QT *__restrict__ Q, BlockMap m, int accumulate) {
     __shared__ C<R> cs[NV];
     const int64_t xc = blockIdx.x;
     if (threadIdx.x < NV) cs[threadIdx.x] = cin[xc * NV + threadIdx.x];
@@ -105,7 +114,7 @@ __global__ void __launch_bounds__(TT) prolong_kernel(C<R> *__restrict__ f, const
         int64_t a = block_elem_addr(m, xc, e);
         C<R> v = accumulate ? f[a] : mk<R>(0, 0);
 #pragma unroll
-        for (int k = 0; k < NV; ++k) cfma(v, Q[k * m.nelem + a], cs[k]);
+        for (int k = 0; k < NV; ++k) cfma(v, QLoad<R, QT>::get(Q, k * m.nelem + a), cs[k]);
         f[a] = v;
     }
 }
@@ -271,21 +280,49 @@ __global__ void gamma_split_kernel(C<R> *__restrict__ Q, const double2 *__restri
 
 }  // namespace
 
-template <typename R> void restrict_(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const C<R> *Q) {
+template <typename R, typename QT>
+void restrict_q(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const QT *Q) {
     BlockMap m = make_map(L);
     ProfScope ps(c, K_RESTRICT);
-#define RK(NV) restrict_kernel<R, NV><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(cout, fin, Q, m)
+#define RK(NV) restrict_kernel<R, QT, NV><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(cout, fin, Q, m)
     NV_DISPATCH(L.nv, RK);
 #undef RK
     DWF_CHECK_LAUNCH();
 }
 
-template <typename R> void prolong_(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const C<R> *Q, bool acc) {
+template <typename R, typename QT>
+void prolong_q(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const QT *Q, bool acc) {
     BlockMap m = make_map(L);
     ProfScope ps(c, K_PROLONG);
-#define PK(NV) prolong_kernel<R, NV><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(fout, cin, Q, m, acc ? 1 : 0)
+#define PK(NV) prolong_kernel<R, QT, NV><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(fout, cin, Q, m, acc ? 1 : 0)
     NV_DISPATCH(L.nv, PK);
 #undef PK
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename R> void restrict_(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const C<R> *Q) {
+    restrict_q<R, C<R>>(c, L, cout, fin, Q);
+}
+template <typename R> void prolong_(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const C<R> *Q, bool acc) {
+    prolong_q<R, C<R>>(c, L, fout, cin, Q, acc);
+}
+void restrict_h(dwf_ctx *c, const Level &L, float2 *cout, const float2 *fin, const __half2 *Q) {
+    restrict_q<float, __half2>(c, L, cout, fin, Q);
+}
+void prolong_h(dwf_ctx *c, const Level &L, float2 *fout, const float2 *cin, const __half2 *Q, bool acc) {
+    prolong_q<float, __half2>(c, L, fout, cin, Q, acc);
+}
+
+namespace {
+__global__ void to_half_kernel(__half2 *__restrict__ out, const float2 *__restrict__ in, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __floats2half2_rn(in[i].x, in[i].y);
+}
+}  // namespace
+
+void basis_to_half(dwf_ctx *c, __half2 *out, const float2 *in, int64_t n) {
+    unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
+    to_half_kernel<<<blocks, 256, 0, c->stream>>>(out, in, n);
     DWF_CHECK_LAUNCH();
 }
 

@@ -37,6 +37,7 @@ class mg_params(ctypes.Structure):
         ("split", ctypes.c_int),
         ("smoother_prec", ctypes.c_int),
         ("coarse_prec", ctypes.c_int * 4),
+        ("basis_prec", ctypes.c_int),
         ("seed", ctypes.c_uint32),
     ]
 

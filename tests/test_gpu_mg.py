@@ -211,11 +211,12 @@ def test_solve_fp64_matches_oracle(G):
     c.close()
 
 
-@pytest.mark.parametrize("cp", [1, 2, 3], ids=["f32", "bf16", "f16"])
-def test_solve_mixed_precision(G, cp):
-    """FP32 V-cycle with reduced-precision coarse stencil, FP64 outer GCR with
-    reliable updates: still |r|/|b| <= 1e-10 and the oracle's solution."""
-    c = Case(G, **SMALL, setup_sweeps=1, smoother_prec=G.DWF_F32, coarse_prec=[cp])
+@pytest.mark.parametrize("cp,bp", [(1, 1), (2, 1), (3, 1), (2, 3)], ids=["f32", "bf16", "f16", "bf16-f16basis"])
+def test_solve_mixed_precision(G, cp, bp):
+    """FP32 V-cycle with reduced-precision coarse stencil (and optionally an
+    FP16 basis for the transfers), FP64 outer GCR with reliable updates:
+    still |r|/|b| <= 1e-10 and the oracle's solution."""
+    c = Case(G, **SMALL, setup_sweeps=1, smoother_prec=G.DWF_F32, coarse_prec=[cp], basis_prec=bp)
     from gpu_util import to_internal, to_canonical, rel_norm
     b = I.gaussian_source(c.dims, c.Ls, 2)
     bt = to_internal(c.ctx, b)
