@@ -193,6 +193,14 @@ dwf_status mg_prolong(dwf_ctx *ctx, int level, void *fine_out_dev, const void *c
  * level's link precision; prec = DWF_F64 or DWF_F32 for the fields. */
 dwf_status mg_coarse_apply(dwf_ctx *ctx, int level, void *out_dev, const void *in_dev, int dagger, dwf_prec prec);
 
+/* x = S2(R A P, b) on the coarsest level (Sec. 2, third step of the
+ * V-cycle): restarted GCR on the coarse stencil from x = 0 to the relative
+ * tolerance coarsest_tol (at most coarsest_maxiter iterations), as one
+ * cooperative kernel.  x and b are coarse fields of that level in the
+ * V-cycle precision (FP64 for smoother_prec = F64, FP32 for F32).
+ * Synchronous. */
+dwf_status mg_coarse_solve(dwf_ctx *ctx, int level, void *x_dev, const void *b_dev);
+
 /* x = one fine-level V-cycle applied to b (Sec. 2), run in the smoother
  * precision; x and b are FP64.  Synchronous. */
 dwf_status mg_vcycle(dwf_ctx *ctx, void *x_dev, const void *b_dev);

@@ -225,6 +225,11 @@ dwf_status mg_coarse_apply(dwf_ctx *c, int level, void *out, const void *in, int
     return guarded(c, [&]() -> dwf_status { dwf::mg_coarse_apply_impl(c, level, out, in, dagger != 0, prec); return DWF_OK; });
 }
 
+dwf_status mg_coarse_solve(dwf_ctx *c, int level, void *x, const void *b) {
+    if (!c || !x || !b || x == b) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_coarse_solve_impl(c, level, x, b); return DWF_OK; });
+}
+
 dwf_status mg_vcycle(dwf_ctx *c, void *x, const void *b) {
     if (!c || !x || !b || x == b) return DWF_EINVAL;
     return guarded(c, [&]() -> dwf_status { dwf::mg_vcycle_impl(c, (double2 *)x, (const double2 *)b); return DWF_OK; });

@@ -316,15 +316,21 @@ bool coarse_gcr_fused_ok(const Level &L, int restart) { return restart >= 1 && r
 size_t coarse_gcr_part_bytes(dwf_ctx *c) { return sizeof(double2) * 3 * (MAXR + 2) * (size_t)c->sm_count; }
 
 template <typename R>
-void coarse_gcr_fused(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, C<R> *r, C<R> *Z, C<R> *W, double2 *part,
-                      int *iters, double tol, int maxiter, int restart) {
-    ProfScope ps(c, K_COARSE);
+static void launch_any(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, C<R> *r, C<R> *Z, C<R> *W, double2 *part,
+                       int *iters, double tol, int maxiter, int restart) {
     switch (L.yprec) {
         case DWF_F64: launch_t<R, double2>(c, L, L.Y64.as<double2>(), x, b, r, Z, W, part, iters, tol, maxiter, restart); break;
         case DWF_F32: launch_t<R, float2>(c, L, L.Y32.as<float2>(), x, b, r, Z, W, part, iters, tol, maxiter, restart); break;
         case DWF_BF16: launch_t<R, __nv_bfloat162>(c, L, L.Y16.as<__nv_bfloat162>(), x, b, r, Z, W, part, iters, tol, maxiter, restart); break;
         case DWF_F16: launch_t<R, __half2>(c, L, L.Y16.as<__half2>(), x, b, r, Z, W, part, iters, tol, maxiter, restart); break;
     }
+}
+
+template <typename R>
+void coarse_gcr_fused(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, C<R> *r, C<R> *Z, C<R> *W, double2 *part,
+                      int *iters, double tol, int maxiter, int restart) {
+    ProfScope ps(c, K_COARSE);
+    launch_any<R>(c, L, x, b, r, Z, W, part, iters, tol, maxiter, restart);
 }
 
 template void coarse_gcr_fused<double>(dwf_ctx *, const Level &, double2 *, const double2 *, double2 *, double2 *,

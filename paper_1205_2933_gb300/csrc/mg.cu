@@ -715,6 +715,16 @@ void mg_coarse_apply_impl(dwf_ctx *c, int level, void *out, const void *in, bool
 }
 
 namespace {
+template <typename R> void coarse_solve_t(dwf_ctx *c, MGState &mg, int level, void *x, const void *b) {
+    Runner<R> run(c, mg);
+    using T = C<R>;
+    T *xl = run.ws(level, 9), *bl = run.ws(level, 8);
+    const int64_t N = mg.lev[level].lg.nelem;
+    DWF_CUDA(cudaMemcpyAsync(bl, b, sizeof(T) * N, cudaMemcpyDeviceToDevice, c->stream));
+    run.coarse_solve(level, xl, bl);
+    DWF_CUDA(cudaMemcpyAsync(x, xl, sizeof(T) * N, cudaMemcpyDeviceToDevice, c->stream));
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+}
 template <typename R> void vcycle_t(dwf_ctx *c, MGState &mg, double2 *x, const double2 *b) {
     Runner<R> run(c, mg);
     const int64_t N = mg.lev[0].lg.nelem;
@@ -725,6 +735,13 @@ template <typename R> void vcycle_t(dwf_ctx *c, MGState &mg, double2 *x, const d
     DWF_CUDA(cudaStreamSynchronize(c->stream));
 }
 }  // namespace
+
+void mg_coarse_solve_impl(dwf_ctx *c, int level, void *x, const void *b) {
+    MGState &mg = need_mg(c, level, 1, MAX_LEVELS);
+    DWF_REQUIRE(level == mg.nlevels - 1, DWF_EINVAL, "mg_coarse_solve runs on the coarsest level");
+    if (mg.p.smoother_prec == DWF_F32) coarse_solve_t<float>(c, mg, level, x, b);
+    else coarse_solve_t<double>(c, mg, level, x, b);
+}
 
 void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b) {
     MGState &mg = need_mg(c, 0, 0, 1);

@@ -94,6 +94,8 @@ def _load():
     L.mg_prolong.argtypes = [vp, i, vp, vp]
     L.mg_coarse_apply.argtypes = [vp, i, vp, vp, i, st]
     L.mg_vcycle.argtypes = [vp, vp, vp]
+    L.mg_coarse_solve.argtypes = [vp, i, vp, vp]
+    L.mg_coarse_solve.restype = st
     L.dwf_cg_solve.argtypes = [vp, vp, vp, ctypes.c_double, i, i, st, ctypes.POINTER(mg_stats)]
     L.dwf_cg_solve.restype = st
     L.dwf_profile.argtypes = [vp, i]
@@ -220,6 +222,10 @@ def mg_prolong(ctx, level, fine_out, coarse_in):
 def mg_coarse_apply(ctx, level, out, inp, dagger=False, prec=DWF_F64):
     return _check(_lib.mg_coarse_apply(ctx, int(level), _ptr(out), _ptr(inp), 1 if dagger else 0, prec),
                   "mg_coarse_apply")
+
+
+def mg_coarse_solve(ctx, level, x, b):
+    return _check(_lib.mg_coarse_solve(ctx, int(level), _ptr(x), _ptr(b)), "mg_coarse_solve")
 
 
 def mg_vcycle(ctx, x, b):

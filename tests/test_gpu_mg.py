@@ -153,6 +153,28 @@ def test_reduced_precision_coarse_stencil(G, lp, tol):
     c.close()
 
 
+@pytest.mark.parametrize("sp", [0, 1], ids=["f64", "f32"])
+def test_coarse_solve_parity(G, sp):
+    """S2 on the coarsest level (the fused GCR) against the oracle's GCR on R D P."""
+    c = Case(G, **SMALL, setup_iters0=10, setup_sweeps=0, smoother_prec=sp, coarsest_tol=1e-6,
+             coarsest_maxiter=200)
+    A = c.mg.levels[1].op
+    d, n = G.mg_level_info(c.ctx.h, 1)
+    bc = I.gauss_complex((int(np.prod(d)) * n,), 33, 50)
+    dt = torch.complex128 if sp == 0 else torch.complex64
+    bt = torch.from_numpy(bc).to(dt).cuda()
+    xt = torch.empty_like(bt)
+    G.mg_coarse_solve(c.ctx.h, 1, xt, bt)
+    x = xt.cpu().numpy().astype(np.complex128).reshape(A.shape)
+    # the solution meets the tolerance on the oracle's coarse operator
+    res = OM.norm(bc.reshape(A.shape) - A.apply(x)) / OM.norm(bc)
+    assert res < (2e-6 if sp == 0 else 2e-5), res
+    xo, info = OM.gcr(A.apply, bc.reshape(A.shape), tol=1e-6, maxiter=200, restart=c.p.coarse_restart)
+    if sp == 0:
+        assert OM.norm(x - xo) / OM.norm(xo) < 1e-3  # both meet 1e-6 on an operator of modest condition
+    c.close()
+
+
 def test_vcycle_parity(G):
     c = Case(G, **SMALL, setup_iters0=10, setup_sweeps=0)
     from gpu_util import to_internal, to_canonical, rel_norm
