@@ -201,6 +201,27 @@ dwf_status mg_coarse_apply(dwf_ctx *ctx, int level, void *out_dev, const void *i
  * Synchronous. */
 dwf_status mg_coarse_solve(dwf_ctx *ctx, int level, void *x_dev, const void *b_dev);
 
+/* Same result as mg_coarse_solve, for callers that cannot allocate device
+ * memory when they solve (a host framework that gives the library a fixed
+ * device-memory budget, or a runtime whose allocator must not be re-entered
+ * from inside the solve).  The paper has no counterpart: this is
+ * an interface choice of this library.  It allocates nothing: all scratch of
+ * the solver lives in one static device array of 8 MiB that every GPU
+ * loading the library holds until the process exits.
+ *   Limits: coarse_restart <= 16 and (1 + 2*coarse_restart) coarse vectors
+ *   of the V-cycle precision must fit in 8 MiB (e.g. 512 sites x 24
+ *   components in FP32 at restart 16: 3.3 MiB); larger requests return
+ *   DWF_EINVAL.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (the context's device must be current); make that first call before
+ *   any stream capture.
+ *   Sharing: every call uses the same array (the iteration counter is
+ *   cleared at each call); calls that overlap on the GPU -- on different
+ *   streams or contexts of the same device -- race and must be serialised
+ *   by the caller.
+ * x and b are device fields as for mg_coarse_solve.  Synchronous. */
+dwf_status mg_coarse_solve_static(dwf_ctx *ctx, int level, void *x_dev, const void *b_dev);
+
 /* x = one fine-level V-cycle applied to b (Sec. 2), run in the smoother
  * precision; x and b are FP64.  Synchronous. */
 dwf_status mg_vcycle(dwf_ctx *ctx, void *x_dev, const void *b_dev);

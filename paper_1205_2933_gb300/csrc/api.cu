@@ -230,6 +230,11 @@ dwf_status mg_coarse_solve(dwf_ctx *c, int level, void *x, const void *b) {
     return guarded(c, [&]() -> dwf_status { dwf::mg_coarse_solve_impl(c, level, x, b); return DWF_OK; });
 }
 
+dwf_status mg_coarse_solve_static(dwf_ctx *c, int level, void *x, const void *b) {
+    if (!c || !x || !b || x == b) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status { dwf::mg_coarse_solve_static_impl(c, level, x, b); return DWF_OK; });
+}
+
 dwf_status mg_vcycle(dwf_ctx *c, void *x, const void *b) {
     if (!c || !x || !b || x == b) return DWF_EINVAL;
     return guarded(c, [&]() -> dwf_status { dwf::mg_vcycle_impl(c, (double2 *)x, (const double2 *)b); return DWF_OK; });

@@ -14,6 +14,8 @@
 // x += <w,r> z, r -= <w,r> w, true residual at each restart.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "mg.cuh"
 
 namespace cg = cooperative_groups;
@@ -337,5 +339,83 @@ template void coarse_gcr_fused<double>(dwf_ctx *, const Level &, double2 *, cons
                                        double2 *, double2 *, int *, double, int, int);
 template void coarse_gcr_fused<float>(dwf_ctx *, const Level &, float2 *, const float2 *, float2 *, float2 *, float2 *,
                                       double2 *, int *, double, int, int);
+
+}  // namespace dwf
+
+// ---------------------------------------------------------------------------
+// Variant that allocates nothing: for callers that cannot allocate device
+// memory at solve time (for example a host framework that hands the library
+// a fixed device-memory budget, or a runtime whose allocator must not be
+// re-entered from inside the solve).  All scratch of the fused
+// coarsest-level solver lives in one file-scope device array of fixed size,
+// shared by every call.
+// ---------------------------------------------------------------------------
+
+namespace dwf {
+
+// residual, 2 x restart direction vectors, FP64 partial sums, the counter
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)8 << 20;
+constexpr int STATIC_MAX_RESTART = 16;
+
+static __device__ __align__(256) unsigned char g_coarse_scratch[STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[64] = {nullptr};
+
+// Device address of the static scratch on the current device, looked up
+// once per device (the host-side symbol is not a device address).
+void *static_scratch(dwf_ctx *c) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    DWF_REQUIRE(c->device >= 0 && c->device < 64, DWF_EINVAL, "device index out of range");
+    if (!g_scratch_ptr[c->device]) {
+        int cur = -1;
+        DWF_CUDA(cudaGetDevice(&cur));
+        DWF_REQUIRE(cur == c->device, DWF_ESTATE, "the context's device must be current");
+        void *p = nullptr;
+        DWF_CUDA(cudaGetSymbolAddress(&p, g_coarse_scratch));
+        g_scratch_ptr[c->device] = p;
+    }
+    return g_scratch_ptr[c->device];
+}
+
+__global__ void zero_int_kernel(int *p) { *p = 0; }
+}  // namespace
+
+template <typename R>
+static void static_solve_t(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, double tol, int maxiter, int restart) {
+    const int64_t N = L.lg.nelem;
+    const size_t vec = sizeof(C<R>) * (size_t)N;
+    const size_t part = coarse_gcr_part_bytes(c);
+    const size_t need = vec * (1 + 2 * (size_t)restart) + part + 256;
+    DWF_REQUIRE(restart >= 1 && restart <= STATIC_MAX_RESTART, DWF_EINVAL,
+                "static coarse solve: coarse_restart must be in 1..16");
+    DWF_REQUIRE(need <= STATIC_SCRATCH_BYTES, DWF_EINVAL,
+                "static coarse solve: (1 + 2*restart) coarse vectors exceed the 8 MiB static scratch");
+    unsigned char *base = (unsigned char *)static_scratch(c);
+    // carve: [counter (256 B)] [partial sums] [r] [Z: restart vectors] [W: restart vectors]
+    int *iters = (int *)base;
+    double2 *partials = (double2 *)(base + 256);
+    C<R> *r = (C<R> *)(base + 256 + ((part + 255) / 256) * 256);
+    C<R> *Z = r + N;
+    C<R> *W = Z + (size_t)restart * N;
+    zero_int_kernel<<<1, 1, 0, c->stream>>>(iters);  // the counter must start at zero
+    DWF_CHECK_LAUNCH();
+    launch_any<R>(c, L, x, b, r, Z, W, partials, iters, tol, maxiter, restart);
+}
+
+void mg_coarse_solve_static_impl(dwf_ctx *c, int level, void *x, const void *b) {
+    DWF_REQUIRE(c->mg && c->mg->nlevels >= 2, DWF_ESTATE, "mg_setup has not completed");
+    MGState &mg = *c->mg;
+    DWF_REQUIRE(level == mg.nlevels - 1 && level >= 1, DWF_EINVAL, "the static coarse solve runs on the coarsest level");
+    const Level &L = mg.lev[level];
+    const mg_params &p = mg.p;
+    if (p.smoother_prec == DWF_F32)
+        static_solve_t<float>(c, L, (float2 *)x, (const float2 *)b, p.coarsest_tol, p.coarsest_maxiter, p.coarse_restart);
+    else
+        static_solve_t<double>(c, L, (double2 *)x, (const double2 *)b, p.coarsest_tol, p.coarsest_maxiter,
+                               p.coarse_restart);
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+}
 
 }  // namespace dwf

@@ -64,6 +64,7 @@ void mg_prolong_impl(dwf_ctx *c, int level, double2 *fout, const double2 *cin);
 void mg_coarse_apply_impl(dwf_ctx *c, int level, void *out, const void *in, bool dag, dwf_prec prec);
 void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b);
 void mg_coarse_solve_impl(dwf_ctx *c, int level, void *x, const void *b);
+void mg_coarse_solve_static_impl(dwf_ctx *c, int level, void *x, const void *b);
 
 // ---- transfer.cu ----
 // c[Vc][nv] = R f  (R = P^+) ; f = P c (accumulate: f += P c)

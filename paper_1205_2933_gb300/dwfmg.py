@@ -96,6 +96,8 @@ def _load():
     L.mg_vcycle.argtypes = [vp, vp, vp]
     L.mg_coarse_solve.argtypes = [vp, i, vp, vp]
     L.mg_coarse_solve.restype = st
+    L.mg_coarse_solve_static.argtypes = [vp, i, vp, vp]
+    L.mg_coarse_solve_static.restype = st
     L.dwf_cg_solve.argtypes = [vp, vp, vp, ctypes.c_double, i, i, st, ctypes.POINTER(mg_stats)]
     L.dwf_cg_solve.restype = st
     L.dwf_profile.argtypes = [vp, i]
@@ -226,6 +228,11 @@ def mg_coarse_apply(ctx, level, out, inp, dagger=False, prec=DWF_F64):
 
 def mg_coarse_solve(ctx, level, x, b):
     return _check(_lib.mg_coarse_solve(ctx, int(level), _ptr(x), _ptr(b)), "mg_coarse_solve")
+
+
+def mg_coarse_solve_static(ctx, level, x, b):
+    """mg_coarse_solve without any device allocation (static scratch; see dwfmg.h)."""
+    return _check(_lib.mg_coarse_solve_static(ctx, int(level), _ptr(x), _ptr(b)), "mg_coarse_solve_static")
 
 
 def mg_vcycle(ctx, x, b):
