@@ -1,0 +1,348 @@
+// Batched vector kernels: nrhs fields of n elements stored one after the
+// other, blockIdx.y = right-hand side.  Every right-hand side has its own
+// coefficients, read from device memory (scalar slots or coefficient
+// arrays), and its own deterministic FP64-accumulated reductions.
+#include "mg.cuh"
+
+namespace dwf {
+
+namespace {
+
+constexpr int BT = 256;
+
+template <typename T> struct RealB;
+template <> struct RealB<float2> { using type = float; };
+template <> struct RealB<double2> { using type = double; };
+
+__device__ __forceinline__ double2 bsum(double2 v, double2 *sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < (blockDim.x + 31) / 32) ? sh[threadIdx.x] : make_double2(0, 0);
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        }
+    __syncthreads();
+    return v;
+}
+
+// K complex reductions per right-hand side: out[base + r*stride + 2j (+1)]
+template <int K>
+__device__ void finish_b(const double2 (&mine)[K], double2 *part, unsigned *count, double *s, int base, int stride) {
+    __shared__ double2 sh[32];
+    __shared__ bool last;
+    const int r = blockIdx.y, nb = gridDim.x;
+    double2 *pr = part + (size_t)r * K * nb;
+    for (int j = 0; j < K; ++j) {
+        double2 t = bsum(mine[j], sh);
+        if (threadIdx.x == 0) pr[(size_t)j * nb + blockIdx.x] = t;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned ticket = atomicAdd(count + r, 1u);
+        last = (ticket == nb - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = 0; j < K; ++j) {
+        double2 v = make_double2(0, 0);
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const volatile double *pp = reinterpret_cast<const volatile double *>(&pr[(size_t)j * nb + i]);
+            v.x += pp[0];
+            v.y += pp[1];
+        }
+        v = bsum(v, sh);
+        if (threadIdx.x == 0) {
+            s[base + r * stride + 2 * j] = v.x;
+            s[base + r * stride + 2 * j + 1] = v.y;
+        }
+    }
+    if (threadIdx.x == 0) count[r] = 0u;
+}
+
+// s[base + r*stride] = |x_r|^2
+template <typename T>
+__global__ void __launch_bounds__(BT) norm2_b_kernel(const T *__restrict__ x, int64_t n, double2 *part, unsigned *count,
+                                                     double *s, int base, int stride) {
+    using A = typename RealB<T>::type;
+    x += (size_t)blockIdx.y * n;
+    A a = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T u = x[i];
+        a += u.x * u.x + u.y * u.y;
+    }
+    double2 m[1] = {make_double2((double)a, 0.0)};
+    finish_b<1>(m, part, count, s, base, stride);
+}
+
+// s[base + r*stride + 2j (+1)] = <V_j,r, w_r>, j < K (w read once)
+template <typename T, int K> struct VArgs {
+    const T *v[K];
+};
+template <typename T, int K>
+__global__ void __launch_bounds__(BT) multidot_b_kernel(VArgs<T, K> va, const T *__restrict__ w, int64_t n,
+                                                        double2 *part, unsigned *count, double *s, int base,
+                                                        int stride) {
+    using A = typename RealB<T>::type;
+    const size_t off = (size_t)blockIdx.y * n;
+    A ar[K], ai[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) ar[j] = ai[j] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T y = w[off + i];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            T u = va.v[j][off + i];
+            ar[j] += u.x * y.x + u.y * y.y;
+            ai[j] += u.x * y.y - u.y * y.x;
+        }
+    }
+    double2 m[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) m[j] = make_double2((double)ar[j], (double)ai[j]);
+    finish_b<K>(m, part, count, s, base, stride);
+}
+
+// w_r += sgn * sum_j c_{r,j} V_j,r with c from slots s[base + r*stride + 2j]
+template <typename T> struct MArgs {
+    const T *v[32];
+    int k;
+};
+template <typename T>
+__global__ void multiaxpy_b_kernel(T *__restrict__ w, MArgs<T> a, const double *__restrict__ s, int base, int stride,
+                                   double sgn, int64_t n) {
+    using R = typename RealB<T>::type;
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    R cr[32], ci[32];
+    for (int j = 0; j < a.k; ++j) {
+        cr[j] = (R)(sgn * s[base + r * stride + 2 * j]);
+        ci[j] = (R)(sgn * s[base + r * stride + 2 * j + 1]);
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T v = w[off + i];
+        for (int j = 0; j < a.k; ++j) {
+            T u = a.v[j][off + i];
+            v.x += cr[j] * u.x - ci[j] * u.y;
+            v.y += cr[j] * u.y + ci[j] * u.x;
+        }
+        w[off + i] = v;
+    }
+}
+
+// CGNR steps with per-RHS scalars at slot blocks base + r*stride:
+//   xr:  a = s[izz] / s[iww]; x += a p; r -= a w
+//   p :  b = s[inew] / s[iold]; p = z + b p
+template <typename T>
+__global__ void cg_xr_b_kernel(T *__restrict__ x, T *__restrict__ rr, const T *__restrict__ p, const T *__restrict__ w,
+                               const double *__restrict__ s, int base, int stride, int izz, int iww, int64_t n) {
+    using R = typename RealB<T>::type;
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    const double ww = s[base + r * stride + iww];
+    const R a = ww > 0.0 ? (R)(s[base + r * stride + izz] / ww) : R(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T pv = p[off + i], wv = w[off + i], xv = x[off + i], rv = rr[off + i];
+        xv.x += a * pv.x;
+        xv.y += a * pv.y;
+        rv.x -= a * wv.x;
+        rv.y -= a * wv.y;
+        x[off + i] = xv;
+        rr[off + i] = rv;
+    }
+}
+template <typename T>
+__global__ void cg_p_b_kernel(T *__restrict__ p, const T *__restrict__ z, const double *__restrict__ s, int base,
+                              int stride, int inew, int iold, int64_t n) {
+    using R = typename RealB<T>::type;
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    const double old = s[base + r * stride + iold];
+    const R b = old > 0.0 ? (R)(s[base + r * stride + inew] / old) : R(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T pv = p[off + i], zv = z[off + i];
+        pv.x = zv.x + b * pv.x;
+        pv.y = zv.y + b * pv.y;
+        p[off + i] = pv;
+    }
+}
+
+// y_r += coef[r] * x_r (complex coefficients in device memory)
+template <typename T>
+__global__ void axpy_b_kernel(T *__restrict__ y, const T *__restrict__ x, const double2 *__restrict__ coef, int64_t n) {
+    using R = typename RealB<T>::type;
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    const R ar = (R)coef[r].x, ai = (R)coef[r].y;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T xv = x[off + i], yv = y[off + i];
+        yv.x += ar * xv.x - ai * xv.y;
+        yv.y += ar * xv.y + ai * xv.x;
+        y[off + i] = yv;
+    }
+}
+
+// w_r *= sc[r];  res_r -= al[r] * w_r   (GCR direction normalisation and residual update)
+template <typename T>
+__global__ void gcr_wr_b_kernel(T *__restrict__ w, T *__restrict__ res, const double *__restrict__ sc,
+                                const double2 *__restrict__ al, int64_t n) {
+    using R = typename RealB<T>::type;
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    const R s = (R)sc[r], ar = (R)al[r].x, ai = (R)al[r].y;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T wv = w[off + i], rv = res[off + i];
+        wv.x *= s;
+        wv.y *= s;
+        rv.x -= ar * wv.x - ai * wv.y;
+        rv.y -= ar * wv.y + ai * wv.x;
+        w[off + i] = wv;
+        res[off + i] = rv;
+    }
+}
+
+// x_r += sum_j g[r*k + j] V_j,r (per-RHS coefficient arrays, k <= 32)
+template <typename T>
+__global__ void combo_b_kernel(T *__restrict__ x, MArgs<T> a, const double2 *__restrict__ g, int64_t n) {
+    using R = typename RealB<T>::type;
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    R cr[32], ci[32];
+    for (int j = 0; j < a.k; ++j) {
+        cr[j] = (R)g[r * a.k + j].x;
+        ci[j] = (R)g[r * a.k + j].y;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T v = x[off + i];
+        for (int j = 0; j < a.k; ++j) {
+            T u = a.v[j][off + i];
+            v.x += cr[j] * u.x - ci[j] * u.y;
+            v.y += cr[j] * u.y + ci[j] * u.x;
+        }
+        x[off + i] = v;
+    }
+}
+
+dim3 grid_b(dwf_ctx *c, int64_t n, int nrhs, int cap_per_sm) {
+    int64_t b = (n + BT - 1) / BT;
+    int64_t cap = std::max<int64_t>(1, (int64_t)c->sm_count * cap_per_sm / std::max(1, nrhs));
+    cap = std::min<int64_t>(cap, 1024);  // partial-sum buffers hold 1024 blocks per value
+    return dim3((unsigned)std::max<int64_t>(1, std::min(b, cap)), (unsigned)nrhs);
+}
+
+}  // namespace
+
+// Buffers of batched reductions: partial sums [nrhs][8][blocks] and counters.
+void BatchScratch::ensure(int nrhs) {
+    size_t need = sizeof(double2) * (size_t)nrhs * 8 * 1024;
+    if (part.bytes < need) part.alloc(need);
+    if (count.bytes < sizeof(unsigned) * (size_t)nrhs) {
+        count.alloc(sizeof(unsigned) * (size_t)nrhs);
+        DWF_CUDA(cudaMemset(count.p, 0, count.bytes));
+    }
+}
+
+template <typename T> void norm2_b(dwf_ctx *c, BatchScratch &bs, int base, int stride, const T *x, int64_t n, int nrhs) {
+    dim3 g = grid_b(c, n, nrhs, 8);
+    norm2_b_kernel<T><<<g, BT, 0, c->stream>>>(x, n, bs.part.as<double2>(), bs.count.as<unsigned>(), c->scal.as<double>(),
+                                               base, stride);
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename T>
+void multidot_b(dwf_ctx *c, BatchScratch &bs, int base, int stride, T *const *V, int k, const T *w, int64_t n, int nrhs) {
+    dim3 g = grid_b(c, n, nrhs, 8);
+    for (int j0 = 0; j0 < k; j0 += 8) {
+        int kk = std::min(8, k - j0);
+#define MDB(K)                                                                                              \
+    {                                                                                                       \
+        VArgs<T, K> a;                                                                                      \
+        for (int j = 0; j < K; ++j) a.v[j] = V[j0 + j];                                                     \
+        multidot_b_kernel<T, K><<<g, BT, 0, c->stream>>>(a, w, n, bs.part.as<double2>(), bs.count.as<unsigned>(), \
+                                                         c->scal.as<double>(), base + 2 * j0, stride);      \
+    }
+        switch (kk) {
+            case 1: MDB(1) break;
+            case 2: MDB(2) break;
+            case 3: MDB(3) break;
+            case 4: MDB(4) break;
+            case 5: MDB(5) break;
+            case 6: MDB(6) break;
+            case 7: MDB(7) break;
+            default: MDB(8) break;
+        }
+#undef MDB
+        DWF_CHECK_LAUNCH();
+    }
+}
+
+template <typename T>
+void multiaxpy_b(dwf_ctx *c, T *w, T *const *V, int k, int base, int stride, double sgn, int64_t n, int nrhs) {
+    dim3 g = grid_b(c, n, nrhs, 16);
+    for (int j0 = 0; j0 < k; j0 += 32) {
+        MArgs<T> a;
+        a.k = std::min(32, k - j0);
+        for (int j = 0; j < a.k; ++j) a.v[j] = V[j0 + j];
+        multiaxpy_b_kernel<T><<<g, BT, 0, c->stream>>>(w, a, c->scal.as<double>(), base + 2 * j0, stride, sgn, n);
+        DWF_CHECK_LAUNCH();
+    }
+}
+
+template <typename T>
+void cg_xr_b(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs) {
+    dim3 g = grid_b(c, n, nrhs, 16);
+    cg_xr_b_kernel<T><<<g, BT, 0, c->stream>>>(x, r, p, w, c->scal.as<double>(), base, stride, izz, iww, n);
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename T>
+void cg_p_b(dwf_ctx *c, T *p, const T *z, int base, int stride, int inew, int iold, int64_t n, int nrhs) {
+    dim3 g = grid_b(c, n, nrhs, 16);
+    cg_p_b_kernel<T><<<g, BT, 0, c->stream>>>(p, z, c->scal.as<double>(), base, stride, inew, iold, n);
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs) {
+    dim3 g = grid_b(c, n, nrhs, 16);
+    axpy_b_kernel<T><<<g, BT, 0, c->stream>>>(y, x, coef, n);
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename T>
+void gcr_wr_b(dwf_ctx *c, T *w, T *res, const double *sc, const double2 *al, int64_t n, int nrhs) {
+    dim3 g = grid_b(c, n, nrhs, 16);
+    gcr_wr_b_kernel<T><<<g, BT, 0, c->stream>>>(w, res, sc, al, n);
+    DWF_CHECK_LAUNCH();
+}
+
+template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const double2 *g, int64_t n, int nrhs) {
+    DWF_REQUIRE(k <= 32, DWF_EINVAL, "combo_b: at most 32 vectors");
+    if (k == 0) return;
+    dim3 gr = grid_b(c, n, nrhs, 16);
+    MArgs<T> a;
+    a.k = k;
+    for (int j = 0; j < k; ++j) a.v[j] = V[j];
+    combo_b_kernel<T><<<gr, BT, 0, c->stream>>>(x, a, g, n);
+    DWF_CHECK_LAUNCH();
+}
+
+#define INSTB(T)                                                                                            \
+    template void norm2_b<T>(dwf_ctx *, BatchScratch &, int, int, const T *, int64_t, int);                  \
+    template void multidot_b<T>(dwf_ctx *, BatchScratch &, int, int, T *const *, int, const T *, int64_t, int); \
+    template void multiaxpy_b<T>(dwf_ctx *, T *, T *const *, int, int, int, double, int64_t, int);            \
+    template void cg_xr_b<T>(dwf_ctx *, T *, T *, const T *, const T *, int, int, int, int, int64_t, int);    \
+    template void cg_p_b<T>(dwf_ctx *, T *, const T *, int, int, int, int, int64_t, int);                     \
+    template void axpy_b<T>(dwf_ctx *, T *, const T *, const double2 *, int64_t, int);                        \
+    template void gcr_wr_b<T>(dwf_ctx *, T *, T *, const double *, const double2 *, int64_t, int);            \
+    template void combo_b<T>(dwf_ctx *, T *, T *const *, int, const double2 *, int64_t, int);
+INSTB(float2)
+INSTB(double2)
+
+}  // namespace dwf

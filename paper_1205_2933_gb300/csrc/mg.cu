@@ -9,6 +9,8 @@
 // the link precision chosen per level; the outer solution and residual, the
 // block Gram-Schmidt and the coarse-operator construction are FP64.
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <cmath>
@@ -24,6 +26,15 @@ const char *last_error() { return g_last_error.c_str(); }
 namespace {
 
 constexpr int SLOT_A = 0;  // scalar slots used by the solvers (double index)
+
+// DWF_VERBOSE=1: per-cycle residual trace of the solvers on stderr
+bool verbose() {
+    static const bool v = [] {
+        const char *e = getenv("DWF_VERBOSE");
+        return e && atoi(e) != 0;
+    }();
+    return v;
+}
 
 template <typename R> DevBuf &Qbuf(Level &L);
 template <> DevBuf &Qbuf<double>(Level &L) { return L.Q64; }
@@ -438,6 +449,7 @@ template <typename R> class Runner {
             st.restarts++;
             caxpy_mixed<double2, T>(c, x, make_double2(1.0, 0.0), eR, N);
             rn = true_residual();
+            if (verbose()) fprintf(stderr, "[dwfmg] cycle %d iters %d |r|/|b| %.3e\n", st.restarts, gi.iters, rn / bn);
         }
         st.iters += iters;
         st.true_res = std::max(st.true_res, rn / bn);
@@ -517,6 +529,322 @@ template <typename R> class Runner {
     }
 };
 
+// Batched solve: all right-hand sides advance together.  Fine-level kernels
+// run over the whole batch (the Dslash with nrhs in its grid, the basis of
+// the transfers read once per 12 right-hand sides); every right-hand side
+// keeps its own GCR coefficients, triangular transform and convergence
+// state, and stops changing once converged.  Coarsest-level solves run per
+// right-hand side through the fused kernel.  FP32 V-cycle, 2 levels, nu_1 = 0.
+template <typename R> class BatchRunner {
+  public:
+    using T = C<R>;
+    dwf_ctx *c;
+    MGState &mg;
+    int nr;
+    Runner<R> one;
+    static constexpr int SB = 1024, SS = 160;  // per-RHS scalar slot blocks: SB + r*SS
+    DevBuf dcoef;                              // per-RHS coefficient arrays (device)
+
+    BatchRunner(dwf_ctx *ctx, MGState &m, int nrhs) : c(ctx), mg(m), nr(nrhs), one(ctx, m) {
+        DWF_REQUIRE(SB + nr * SS <= NSCALAR, DWF_EINVAL, "too many right-hand sides in one batch");
+        mg.bscratch.ensure(nr);
+        dcoef.alloc(sizeof(double2) * (size_t)nr * (MAX_RESTART + 2));
+        dscale.alloc(sizeof(double) * (size_t)nr);
+    }
+
+    int64_t n(int l) const { return mg.lev[l].lg.nelem; }
+
+    T *wsb(int l, int i) {
+        auto &v = mg.wsb[l];
+        if ((int)v.size() <= i) v.resize(i + 1);
+        const size_t bytes = sizeof(T) * (size_t)n(l) * nr;
+        if (v[i].bytes < bytes) v[i].alloc(bytes);
+        return v[i].template as<T>();
+    }
+
+    // the per-RHS scalar blocks SB + r*SS .. + SS, one synchronisation
+    void read_block(std::vector<double> &out) {
+        out.resize((size_t)nr * SS);
+        DWF_CUDA(cudaMemcpyAsync(c->hscal, c->scal.as<double>() + SB, sizeof(double) * (size_t)nr * SS,
+                                 cudaMemcpyDeviceToHost, c->stream));
+        DWF_CUDA(cudaStreamSynchronize(c->stream));
+        std::copy(c->hscal, c->hscal + (size_t)nr * SS, out.begin());
+    }
+
+    // nu CGNR iterations on D x = b for every right-hand side, from x = 0
+    void cgnr_b(T *x, const T *b, int iters) {
+        const int64_t N = n(0), NT = N * nr;
+        T *r = wsb(0, 0), *z = wsb(0, 1), *p = wsb(0, 2), *w = wsb(0, 3);
+        bzero<T>(c, x, NT);
+        bcopy<T, T>(c, r, b, NT);
+        dslash(c, z, r, true, nr);
+        bcopy<T, T>(c, p, z, NT);
+        int izz = 0, inew = 1;
+        const int iww = 2;
+        norm2_b<T>(c, mg.bscratch, SB + izz, SS, z, N, nr);
+        for (int it = 0; it < iters; ++it) {
+            dslash(c, w, p, false, nr);
+            norm2_b<T>(c, mg.bscratch, SB + iww, SS, w, N, nr);
+            cg_xr_b<T>(c, x, r, p, w, SB, SS, izz, iww, N, nr);
+            if (it + 1 == iters) break;
+            dslash(c, z, r, true, nr);
+            norm2_b<T>(c, mg.bscratch, SB + inew, SS, z, N, nr);
+            cg_p_b<T>(c, p, z, SB, SS, inew, izz, N, nr);
+            std::swap(izz, inew);
+        }
+    }
+
+    // Coarsest-level solves of every right-hand side.  One fused solve fills
+    // about a third of the SMs, so NS of them run at a time on side streams
+    // (each with its own scratch), joined back to the context stream.
+    static constexpr int NS = 3;
+    cudaStream_t side[NS] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[NS] = {nullptr, nullptr, nullptr};
+    DevBuf cs_r[NS], cs_Z[NS], cs_W[NS], cs_part[NS];
+
+    void coarse_solves(T *x2, const T *b2, int64_t Nc) {
+        Level &Lc = mg.lev[1];
+        const mg_params &p = mg.p;
+        if (!coarse_gcr_fused_ok(Lc, p.coarse_restart)) {
+            for (int r = 0; r < nr; ++r) one.coarse_solve(1, x2 + (size_t)r * Nc, b2 + (size_t)r * Nc);
+            return;
+        }
+        if (!side[0]) {
+            for (int i = 0; i < NS; ++i) {
+                DWF_CUDA(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking));
+                DWF_CUDA(cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming));
+                cs_r[i].alloc(sizeof(T) * Nc);
+                cs_Z[i].alloc(sizeof(T) * Nc * p.coarse_restart);
+                cs_W[i].alloc(sizeof(T) * Nc * p.coarse_restart);
+                cs_part[i].alloc(coarse_gcr_part_bytes(c));
+            }
+            DWF_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+            if (!Lc.cgIters.p) {
+                Lc.cgIters.alloc(sizeof(int));
+                DWF_CUDA(cudaMemsetAsync(Lc.cgIters.p, 0, sizeof(int), c->stream));
+            }
+        }
+        DWF_CUDA(cudaEventRecord(ev_fork, c->stream));
+        cudaStream_t main = c->stream;
+        for (int i = 0; i < NS; ++i) DWF_CUDA(cudaStreamWaitEvent(side[i], ev_fork, 0));
+        for (int r = 0; r < nr; ++r) {
+            const int i = r % NS;
+            c->stream = side[i];
+            coarse_gcr_fused<R>(c, Lc, x2 + (size_t)r * Nc, b2 + (size_t)r * Nc, cs_r[i].as<T>(), cs_Z[i].as<T>(),
+                                cs_W[i].as<T>(), cs_part[i].as<double2>(), Lc.cgIters.as<int>(), p.coarsest_tol,
+                                p.coarsest_maxiter, p.coarse_restart);
+        }
+        c->stream = main;
+        for (int i = 0; i < NS; ++i) {
+            DWF_CUDA(cudaEventRecord(ev_join[i], side[i]));
+            DWF_CUDA(cudaStreamWaitEvent(main, ev_join[i], 0));
+        }
+    }
+
+    ~BatchRunner() {
+        if (side[0]) cudaStreamSynchronize(c->stream);
+        for (int i = 0; i < NS; ++i) {
+            if (side[i]) cudaStreamDestroy(side[i]);
+            if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
+
+    // one V-cycle for every right-hand side (nu_1 = 0)
+    void vcycle_b(T *x, const T *b) {
+        Level &L = mg.lev[0];
+        const int64_t N = n(0), NT = N * nr, Nc = n(1);
+        T *res = wsb(0, 4), *sm = wsb(0, 5);
+        T *b2 = wsb(1, 8), *x2 = wsb(1, 9);
+        restrict_batch<R>(c, L, b2, b, one.Q(0), nr);
+        coarse_solves(x2, b2, Nc);
+        prolong_batch<R>(c, L, x, x2, one.Q(0), nr, false);
+        if (mg.p.nu_post > 0) {
+            dslash(c, res, x, false, nr);
+            cxpay<T>(c, res, make_double2(-1.0, 0.0), b, NT);  // res = b - A x
+            cgnr_b(sm, res, mg.p.nu_post);
+            caxpy<T>(c, x, make_double2(1.0, 0.0), sm, NT);
+        }
+    }
+
+    // One cycle (at most `restart` iterations) of lockstep flexible GCR on the
+    // fine level for every right-hand side from x = 0, right-preconditioned by
+    // vcycle_b.  tol[r] is relative to |b_r|; a right-hand side stops changing
+    // once its residual estimate meets it (tol[r] >= 1: untouched).  Returns
+    // the summed iterations of the active right-hand sides.
+    long long gcr_b(T *x, const T *b, const std::vector<double> &tol, int restart) {
+        const int64_t N = n(0), NT = N * nr;
+        DWF_REQUIRE(restart >= 1 && restart <= 32, DWF_EINVAL, "batched GCR restart must be in 1..32");
+        T *rr = wsb(0, 10);
+        std::vector<T *> Z(restart), W(restart);
+        for (int i = 0; i < restart; ++i) {
+            Z[i] = wsb(0, 16 + i);
+            W[i] = wsb(0, 16 + restart + i);
+        }
+        bzero<T>(c, x, NT);
+        bcopy<T, T>(c, rr, b, NT);
+        std::vector<double> sv;
+        norm2_b<T>(c, mg.bscratch, SB, SS, b, N, nr);
+        read_block(sv);
+        std::vector<double> bn(nr), rn(nr);
+        std::vector<char> act(nr);
+        for (int r = 0; r < nr; ++r) {
+            bn[r] = std::sqrt(sv[(size_t)r * SS]);
+            rn[r] = bn[r];
+            act[r] = bn[r] > 0.0 && tol[r] < 1.0;
+        }
+        auto any = [&]() { for (int r = 0; r < nr; ++r) if (act[r]) return true; return false; };
+        std::vector<double2> Tm((size_t)nr * restart * restart), alpha((size_t)nr * restart);
+        std::vector<double2> al(nr);
+        std::vector<double> scr(nr);
+        long long active_iters = 0;
+        int k = 0;
+        while (k < restart && any()) {
+            vcycle_b(Z[k], rr);
+            dslash(c, W[k], Z[k], false, nr);
+            for (int r = 0; r < nr; ++r)
+                for (int i = 0; i <= k; ++i) Tm[(size_t)r * restart * restart + i * restart + k] = make_double2(0, 0);
+            for (int pass = 0; pass < 2; ++pass) {
+                multidot_b<T>(c, mg.bscratch, SB, SS, W.data(), k + 1, W[k], N, nr);
+                if (k > 0) multiaxpy_b<T>(c, W[k], W.data(), k, SB, SS, -1.0, N, nr);
+                read_block(sv);
+                bool again = false;
+                for (int r = 0; r < nr; ++r) {
+                    const double *v = sv.data() + (size_t)r * SS;
+                    double removed = 0.0;
+                    for (int i = 0; i < k; ++i) {
+                        Tm[(size_t)r * restart * restart + i * restart + k].x += v[2 * i];
+                        Tm[(size_t)r * restart * restart + i * restart + k].y += v[2 * i + 1];
+                        removed += v[2 * i] * v[2 * i] + v[2 * i + 1] * v[2 * i + 1];
+                    }
+                    if (!std::isfinite(v[2 * k])) throw Error{DWF_ENAN, "NaN or Inf in batched GCR"};
+                    if (act[r] && k > 0 && removed >= 0.75 * v[2 * k]) again = true;
+                }
+                if (!again) break;
+            }
+            // |W_k|^2 and <W_k, r> per right-hand side
+            norm2_b<T>(c, mg.bscratch, SB + 2, SS, W[k], N, nr);
+            T *wk = W[k];
+            multidot_b<T>(c, mg.bscratch, SB + 4, SS, &wk, 1, rr, N, nr);
+            read_block(sv);
+            for (int r = 0; r < nr; ++r) {
+                const double *v = sv.data() + (size_t)r * SS;
+                const double ww = v[2];
+                double2 &Td = Tm[(size_t)r * restart * restart + k * restart + k];
+                const bool ok = ww > 0.0 && std::isfinite(ww);
+                scr[r] = ok ? 1.0 / std::sqrt(ww) : 0.0;
+                if (act[r] && ok) {
+                    const double nw = std::sqrt(ww);
+                    Td = make_double2(nw, 0.0);
+                    al[r] = make_double2(v[4] / nw, v[5] / nw);
+                    const double r2 = rn[r] * rn[r] - (al[r].x * al[r].x + al[r].y * al[r].y);
+                    rn[r] = r2 > 0 ? std::sqrt(r2) : 0.0;
+                    ++active_iters;
+                } else {
+                    Td = make_double2(1.0, 0.0);
+                    al[r] = make_double2(0.0, 0.0);
+                }
+                alpha[(size_t)r * restart + k] = al[r];
+            }
+            DWF_CUDA(cudaMemcpyAsync(dcoef.p, al.data(), sizeof(double2) * nr, cudaMemcpyHostToDevice, c->stream));
+            DWF_CUDA(cudaMemcpyAsync(dscale.p, scr.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, c->stream));
+            gcr_wr_b<T>(c, W[k], rr, dscale.as<double>(), dcoef.as<double2>(), N, nr);
+            for (int r = 0; r < nr; ++r)
+                if (act[r] && rn[r] <= tol[r] * bn[r]) act[r] = 0;
+            ++k;
+        }
+        // x += sum_j gamma_j z_j with gamma = T^-1 alpha for every right-hand side
+        if (k > 0) {
+            std::vector<double2> g((size_t)nr * k);
+            for (int r = 0; r < nr; ++r) {
+                const double2 *Tr = Tm.data() + (size_t)r * restart * restart;
+                const double2 *ar = alpha.data() + (size_t)r * restart;
+                for (int i = k - 1; i >= 0; --i) {
+                    double2 s = ar[i];
+                    for (int j = i + 1; j < k; ++j) {
+                        double2 t = cmul(Tr[i * restart + j], g[(size_t)r * k + j]);
+                        s.x -= t.x;
+                        s.y -= t.y;
+                    }
+                    const double d = Tr[i * restart + i].x;
+                    g[(size_t)r * k + i] = make_double2(s.x / d, s.y / d);
+                }
+            }
+            DWF_CUDA(cudaMemcpyAsync(dcoef.p, g.data(), sizeof(double2) * g.size(), cudaMemcpyHostToDevice, c->stream));
+            combo_b<T>(c, x, Z.data(), k, dcoef.as<double2>(), N, nr);
+        }
+        return active_iters;
+    }
+
+    // outer flexible GCR in FP64 with reliable updates, all right-hand sides together
+    dwf_status solve(double2 *b, double2 *x, double tol, mg_stats &st) {
+        const mg_params &p = mg.p;
+        const int64_t N = n(0), NT = N * nr;
+        double2 *r64 = mg_wsb64(0), *t64 = mg_wsb64(1);
+        std::vector<double> sv;
+        norm2_b<double2>(c, mg.bscratch, SB, SS, b, N, nr);
+        read_block(sv);
+        std::vector<double> bn(nr), rn(nr);
+        for (int r = 0; r < nr; ++r) bn[r] = std::sqrt(sv[(size_t)r * SS]);
+        auto true_residual = [&]() {
+            dslash(c, t64, x, false, nr);
+            bcopy<double2, double2>(c, r64, b, NT);
+            caxpy<double2>(c, r64, make_double2(-1.0, 0.0), t64, NT);
+            norm2_b<double2>(c, mg.bscratch, SB, SS, r64, N, nr);
+            read_block(sv);
+            for (int r = 0; r < nr; ++r) {
+                rn[r] = std::sqrt(sv[(size_t)r * SS]);
+                if (!std::isfinite(rn[r])) throw Error{DWF_ENAN, "NaN or Inf in the residual"};
+            }
+        };
+        true_residual();
+        T *bR = wsb(0, 8), *eR = wsb(0, 9);
+        long long iters = 0;
+        int cycles = 0;
+        const double floor_rel = std::is_same<R, float>::value ? 2e-6 : 0.0;
+        dwf_status status = DWF_OK;
+        auto done = [&]() { for (int r = 0; r < nr; ++r) if (rn[r] > tol * bn[r]) return false; return true; };
+        while (!done()) {
+            if (cycles * p.outer_restart >= p.outer_maxiter) {
+                status = DWF_ENOCONV;
+                break;
+            }
+            std::vector<double> tin(nr);
+            for (int r = 0; r < nr; ++r)
+                tin[r] = (bn[r] == 0.0 || rn[r] <= tol * bn[r]) ? 1.0 : std::max(tol * bn[r] / rn[r], floor_rel);
+            bcopy<T, double2>(c, bR, r64, NT);
+            long long gi = gcr_b(eR, bR, tin, std::min(p.outer_restart, 32));
+            if (gi == 0) {
+                status = DWF_EBREAKDOWN;
+                break;
+            }
+            iters += gi;
+            ++cycles;
+            st.restarts++;
+            caxpy_mixed<double2, T>(c, x, make_double2(1.0, 0.0), eR, NT);
+            true_residual();
+            if (verbose()) {
+                fprintf(stderr, "[dwfmg batch] cycle %d active-iters %lld |r|/|b|:", cycles, gi);
+                for (int r = 0; r < nr; ++r) fprintf(stderr, " %.2e", bn[r] > 0 ? rn[r] / bn[r] : 0.0);
+                fprintf(stderr, "\n");
+            }
+        }
+        st.iters += (int)iters;
+        for (int r = 0; r < nr; ++r) st.true_res = std::max(st.true_res, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
+        return status;
+    }
+
+    double2 *mg_wsb64(int i) {
+        auto &v = mg.wsb64;
+        if ((int)v.size() <= i) v.resize(i + 1);
+        const size_t bytes = sizeof(double2) * (size_t)n(0) * nr;
+        if (v[i].bytes < bytes) v[i].alloc(bytes);
+        return v[i].as<double2>();
+    }
+
+    DevBuf dscale;  // per-RHS real scale factors (device)
+};
+
 template <typename R>
 dwf_status setup_t(dwf_ctx *c, MGState &mg, int levels, const void *start, bool start_on_host) {
     Runner<R> run(c, mg);
@@ -527,6 +855,25 @@ dwf_status setup_t(dwf_ctx *c, MGState &mg, int levels, const void *start, bool 
 
 template <typename R>
 dwf_status solve_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, int nrhs, mg_stats &st) {
+    static const bool batch_on = [] {
+        const char *e = getenv("DWF_BATCH");
+        return !(e && atoi(e) == 0);
+    }();
+    if (std::is_same<R, float>::value && nrhs > 1 && batch_on && mg.nlevels == 2 && mg.p.nu_pre == 0 &&
+        mg.p.outer_restart <= 32) {
+        const int64_t N = mg.lev[0].lg.nelem;
+        dwf_status worst = DWF_OK;
+        long long c0 = 0;
+        for (int r0 = 0; r0 < nrhs; r0 += 32) {
+            const int nb = std::min(32, nrhs - r0);
+            BatchRunner<R> br(c, mg, nb);
+            dwf_status s = br.solve(b + (size_t)r0 * N, x + (size_t)r0 * N, tol, st);
+            if (s != DWF_OK && worst == DWF_OK) worst = s;
+            c0 += br.one.fused_iters(1);
+        }
+        st.coarse_applies[1] += c0;
+        return worst;
+    }
     Runner<R> run(c, mg);
     dwf_status worst = DWF_OK;
     const int64_t N = mg.lev[0].lg.nelem;

@@ -39,12 +39,21 @@ struct Level {
     DevBuf cgZ, cgW, cgPart, cgIters;
 };
 
+// ---- blasb.cu ---- batched vector kernels: nrhs fields of n elements, per-RHS
+// scalars at slot blocks base + r*stride of ctx->scal
+struct BatchScratch {
+    DevBuf part, count;
+    void ensure(int nrhs);
+};
 struct MGState {
     int nlevels = 0;
     mg_params p;
     Level lev[MAX_LEVELS];
     // workspaces (allocated lazily by precision)
     std::vector<DevBuf> ws64[MAX_LEVELS], ws32[MAX_LEVELS];
+    // batched solve: nrhs-wide workspaces and reduction scratch
+    std::vector<DevBuf> wsb[MAX_LEVELS], wsb64;
+    BatchScratch bscratch;
     mg_stats stats;
 };
 
@@ -74,6 +83,10 @@ template <typename R> void prolong_(dwf_ctx *c, const Level &L, C<R> *fout, cons
 void restrict_h(dwf_ctx *c, const Level &L, float2 *cout, const float2 *fin, const __half2 *Q);
 void prolong_h(dwf_ctx *c, const Level &L, float2 *fout, const float2 *cin, const __half2 *Q, bool accumulate);
 void basis_to_half(dwf_ctx *c, __half2 *out, const float2 *in, int64_t n);
+// batched transfers: nrhs fine fields <-> nrhs coarse fields, basis read once per 12 RHS
+template <typename R> void restrict_batch(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const C<R> *Q, int nrhs);
+template <typename R>
+void prolong_batch(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const C<R> *Q, int nrhs, bool accumulate);
 // G[Vc][nv][nv] = block inner products <A_k, B_l> over each block (FP64 accumulate)
 template <typename R> void block_gram(dwf_ctx *c, const Level &L, double2 *G, const C<R> *A, const C<R> *B);
 // In-place block orthonormalisation of the nv fields Q (CholQR2, FP64); returns false on breakdown
@@ -97,6 +110,17 @@ size_t coarse_gcr_part_bytes(dwf_ctx *c);
 template <typename R>
 void coarse_gcr_fused(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, C<R> *r, C<R> *Z, C<R> *W, double2 *part,
                       int *iters, double tol, int maxiter, int restart);
+
+template <typename T> void norm2_b(dwf_ctx *c, BatchScratch &bs, int base, int stride, const T *x, int64_t n, int nrhs);
+template <typename T>
+void multidot_b(dwf_ctx *c, BatchScratch &bs, int base, int stride, T *const *V, int k, const T *w, int64_t n, int nrhs);
+template <typename T> void multiaxpy_b(dwf_ctx *c, T *w, T *const *V, int k, int base, int stride, double sgn, int64_t n, int nrhs);
+template <typename T>
+void cg_xr_b(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
+template <typename T> void cg_p_b(dwf_ctx *c, T *p, const T *z, int base, int stride, int inew, int iold, int64_t n, int nrhs);
+template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs);
+template <typename T> void gcr_wr_b(dwf_ctx *c, T *w, T *res, const double *sc, const double2 *al, int64_t n, int nrhs);
+template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const double2 *g, int64_t n, int nrhs);
 
 // ---- blas2.cu ----  (host scalars; FP64 accumulate inside reductions)
 template <typename T> void caxpy(dwf_ctx *c, T *y, double2 a, const T *x, int64_t n);       // y += a x

@@ -314,11 +314,117 @@ void prolong_h(dwf_ctx *c, const Level &L, float2 *fout, const float2 *cin, cons
 }
 
 namespace {
+// Batched restriction: c_r(xc, k) = sum_e conj(Q_k(e)) f_r(e) for NB right-
+// hand sides r0 .. r0+NB-1 (masked beyond nrhs), one CTA per coarse site.
+// Warp w owns basis rows k = w*KG .. w*KG+KG-1 and all NB right-hand sides
+// (KG*NB accumulators per lane); lanes stream over the block's elements, so
+// every basis value is read once and each field value is read by the 8
+// warps of the CTA (L1).  Lane partial sums are reduced with shuffles.
+template <typename R, int NV, int NB>
+__global__ void __launch_bounds__(TT) restrict_b_kernel(C<R> *__restrict__ cout, const C<R> *__restrict__ f,
+                                                        const C<R> *__restrict__ Q, BlockMap m, int nrhs, int r0,
+                                                        int64_t cstride) {
+    constexpr int NW = TT / 32;
+    constexpr int KG = (NV + NW - 1) / NW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k0 = warp * KG;
+    const int64_t xc = blockIdx.x;
+    const int64_t ne = m.bsites * m.run;
+    C<R> acc[KG][NB];
+#pragma unroll
+    for (int a = 0; a < KG; ++a)
+#pragma unroll
+        for (int r = 0; r < NB; ++r) acc[a][r] = mk<R>(0, 0);
+    const int nrb = nrhs - r0 < NB ? nrhs - r0 : NB;
+    for (int64_t e = lane; e < ne; e += 32) {
+        const int64_t ad = block_elem_addr(m, xc, e);
+        C<R> fv[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) fv[r] = r < nrb ? f[(int64_t)(r0 + r) * m.nelem + ad] : mk<R>(0, 0);
+#pragma unroll
+        for (int a = 0; a < KG; ++a) {
+            if (k0 + a < NV) {
+                const C<R> q = Q[(k0 + a) * m.nelem + ad];
+#pragma unroll
+                for (int r = 0; r < NB; ++r) cfmac(acc[a][r], q, fv[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < KG; ++a)
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            C<R> v = acc[a][r];
+            for (int o = 16; o > 0; o >>= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+            }
+            if (lane == 0 && k0 + a < NV && r < nrb) cout[(int64_t)(r0 + r) * cstride + xc * NV + k0 + a] = v;
+        }
+}
+
+// Batched prolongation: f_r(e) (+)= sum_k Q_k(e) c_r(xc, k) for all nrhs
+// right-hand sides; each basis value is loaded once for all of them.
+template <typename R, int NV>
+__global__ void __launch_bounds__(TT) prolong_b_kernel(C<R> *__restrict__ f, const C<R> *__restrict__ cin,
+                                                       const C<R> *__restrict__ Q, BlockMap m, int nrhs,
+                                                       int64_t cstride, int accumulate) {
+    extern __shared__ unsigned char cs_raw[];
+    C<R> *cs = reinterpret_cast<C<R> *>(cs_raw);  // [nrhs][NV]
+    const int64_t xc = blockIdx.x;
+    for (int i = threadIdx.x; i < nrhs * NV; i += TT) cs[i] = cin[(int64_t)(i / NV) * cstride + xc * NV + i % NV];
+    __syncthreads();
+    const int64_t ne = m.bsites * m.run;
+    for (int64_t e = threadIdx.x; e < ne; e += TT) {
+        const int64_t a = block_elem_addr(m, xc, e);
+        C<R> q[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) q[k] = Q[k * m.nelem + a];
+        for (int r = 0; r < nrhs; ++r) {
+            C<R> v = accumulate ? f[(int64_t)r * m.nelem + a] : mk<R>(0, 0);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) cfma(v, q[k], cs[r * NV + k]);
+            f[(int64_t)r * m.nelem + a] = v;
+        }
+    }
+}
+
 __global__ void to_half_kernel(__half2 *__restrict__ out, const float2 *__restrict__ in, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = __floats2half2_rn(in[i].x, in[i].y);
 }
 }  // namespace
+
+template <typename R>
+void restrict_batch(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const C<R> *Q, int nrhs) {
+    BlockMap m = make_map(L);
+    ProfScope ps(c, K_RESTRICT);
+    const int64_t cstride = ncoarse(m) * L.nv;
+    for (int r0 = 0; r0 < nrhs; r0 += 12) {
+#define RB(NV) restrict_b_kernel<R, NV, 12><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(cout, fin, Q, m, nrhs, r0, cstride)
+        NV_DISPATCH(L.nv, RB);
+#undef RB
+        DWF_CHECK_LAUNCH();
+    }
+}
+
+template <typename R>
+void prolong_batch(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const C<R> *Q, int nrhs, bool acc) {
+    BlockMap m = make_map(L);
+    ProfScope ps(c, K_PROLONG);
+    const int64_t cstride = ncoarse(m) * L.nv;
+    const size_t smem = sizeof(C<R>) * (size_t)nrhs * L.nv;
+    DWF_REQUIRE(smem <= 46 * 1024, DWF_EINVAL, "too many right-hand sides for the batched prolongation");
+#define PB(NV) prolong_b_kernel<R, NV><<<(unsigned)ncoarse(m), TT, smem, c->stream>>>(fout, cin, Q, m, nrhs, cstride, acc ? 1 : 0)
+    NV_DISPATCH(L.nv, PB);
+#undef PB
+    DWF_CHECK_LAUNCH();
+}
+
+template void restrict_batch<float>(dwf_ctx *, const Level &, float2 *, const float2 *, const float2 *, int);
+template void restrict_batch<double>(dwf_ctx *, const Level &, double2 *, const double2 *, const double2 *, int);
+template void prolong_batch<float>(dwf_ctx *, const Level &, float2 *, const float2 *, const float2 *, int, bool);
+template void prolong_batch<double>(dwf_ctx *, const Level &, double2 *, const double2 *, const double2 *, int, bool);
 
 void basis_to_half(dwf_ctx *c, __half2 *out, const float2 *in, int64_t n) {
     unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
