@@ -226,6 +226,15 @@ dwf_status mg_coarse_solve_static(dwf_ctx *ctx, int level, void *x_dev, const vo
  * precision; x and b are FP64.  Synchronous. */
 dwf_status mg_vcycle(dwf_ctx *ctx, void *x_dev, const void *b_dev);
 
+/* The V-cycle of mg_vcycle (Sec. 2) for nrhs right-hand sides stored one
+ * after another (nrhs fine FP64 fields each for x and b).  With an FP32
+ * V-cycle on two levels and nu_1 = 0 the right-hand sides go through the
+ * fine level together (one Dslash launch, one read of the transfer basis
+ * per 12 of them) and their coarsest solves run concurrently; otherwise
+ * they run one after another.  Each x_r equals what mg_vcycle gives for
+ * b_r up to rounding order.  x and b must not overlap.  Synchronous. */
+dwf_status mg_vcycle_batch(dwf_ctx *ctx, void *x_dev, const void *b_dev, int nrhs);
+
 /* ---- Measurement -------------------------------------------------------
  * An optional profiler brackets every launch of the timed kernel classes
  * with CUDA events on the context's stream.  dwf_profile(ctx, 1) clears the

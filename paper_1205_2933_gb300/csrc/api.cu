@@ -237,7 +237,15 @@ dwf_status mg_coarse_solve_static(dwf_ctx *c, int level, void *x, const void *b)
 
 dwf_status mg_vcycle(dwf_ctx *c, void *x, const void *b) {
     if (!c || !x || !b || x == b) return DWF_EINVAL;
-    return guarded(c, [&]() -> dwf_status { dwf::mg_vcycle_impl(c, (double2 *)x, (const double2 *)b); return DWF_OK; });
+    return guarded(c, [&]() -> dwf_status { dwf::mg_vcycle_impl(c, (double2 *)x, (const double2 *)b, 1); return DWF_OK; });
+}
+
+dwf_status mg_vcycle_batch(dwf_ctx *c, void *x, const void *b, int nrhs) {
+    if (!c || !x || !b || x == b || nrhs < 1) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        dwf::mg_vcycle_impl(c, (double2 *)x, (const double2 *)b, nrhs);
+        return DWF_OK;
+    });
 }
 
 const char *dwf_last_error(void) { return dwf::last_error(); }
@@ -273,4 +281,68 @@ dwf_status dwf_profile_read(dwf_ctx *c, int kernel_class, long long *launches, d
 
 unsigned long long dwf_launch_count(void) { return dwf::launch_count(); }
 
+// ---- learned near-null proposal (include/dwfnet.h) ----
+
+dwf_status net_create(dwf_ctx *c, const dwf_net_shape *shape, dwf_net **out) {
+    if (!c || !shape || !out) return DWF_EINVAL;
+    *out = nullptr;
+    return guarded(c, [&]() -> dwf_status {
+        *out = dwf::net_create_impl(c, *shape);
+        return DWF_OK;
+    });
+}
+
+dwf_status net_num_params(const dwf_net *net, long long *count) {
+    if (!net || !count) return DWF_EINVAL;
+    *count = dwf::net_nparams(net);
+    return DWF_OK;
+}
+
+dwf_status net_set_params(dwf_net *net, const void *params) {
+    if (!net || !params) return DWF_EINVAL;
+    return guarded(nullptr, [&]() -> dwf_status {
+        dwf::net_set_params_impl(net, params, is_device_ptr(params));
+        return DWF_OK;
+    });
+}
+
+dwf_status net_get_params(dwf_net *net, void *params) {
+    if (!net || !params) return DWF_EINVAL;
+    return guarded(nullptr, [&]() -> dwf_status {
+        dwf::net_get_params_impl(net, params, is_device_ptr(params));
+        return DWF_OK;
+    });
+}
+
+dwf_status net_forward(dwf_net *net, dwf_ctx *c, const void *input, unsigned int seed, void *out) {
+    if (!net || !c || !out) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        dwf::net_forward_impl(net, c, input, input && is_device_ptr(input), seed, (double2 *)out);
+        return DWF_OK;
+    });
+}
+
+dwf_status net_loss_grad(dwf_net *net, dwf_ctx *c, const void *input, unsigned int seed, const void *targets, int nt,
+                         const int block[4], double *loss, void *grad) {
+    if (!net || !c || !targets || !block || !loss || nt < 1) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        *loss = dwf::net_loss_grad_impl(net, c, input, input && is_device_ptr(input), seed, (const double2 *)targets,
+                                        nt, block, grad, grad && is_device_ptr(grad));
+        return DWF_OK;
+    });
+}
+
+dwf_status net_adam(dwf_net *net, double lr, double beta1, double beta2, double eps) {
+    if (!net) return DWF_EINVAL;
+    return guarded(nullptr, [&]() -> dwf_status {
+        dwf::net_adam_impl(net, lr, beta1, beta2, eps);
+        return DWF_OK;
+    });
+}
+
+void net_destroy(dwf_net *net) {
+    if (net) dwf::net_free(net);
+}
+
 }  // extern "C"
+

@@ -32,8 +32,9 @@ __device__ __forceinline__ double2 bsum(double2 v, double2 *sh) {
     return v;
 }
 
-// K complex reductions per right-hand side: out[base + r*stride + 2j (+1)]
-template <int K>
+// K complex reductions per right-hand side: out[base + r*stride + 2j (+1)];
+// a real result (CPLX = false, K = 1) writes the single slot base + r*stride
+template <int K, bool CPLX = true>
 __device__ void finish_b(const double2 (&mine)[K], double2 *part, unsigned *count, double *s, int base, int stride) {
     __shared__ double2 sh[32];
     __shared__ bool last;
@@ -61,7 +62,7 @@ __device__ void finish_b(const double2 (&mine)[K], double2 *part, unsigned *coun
         v = bsum(v, sh);
         if (threadIdx.x == 0) {
             s[base + r * stride + 2 * j] = v.x;
-            s[base + r * stride + 2 * j + 1] = v.y;
+            if (CPLX) s[base + r * stride + 2 * j + 1] = v.y;
         }
     }
     if (threadIdx.x == 0) count[r] = 0u;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(BT) norm2_b_kernel(const T *__restrict__ x, in
         a += u.x * u.x + u.y * u.y;
     }
     double2 m[1] = {make_double2((double)a, 0.0)};
-    finish_b<1>(m, part, count, s, base, stride);
+    finish_b<1, false>(m, part, count, s, base, stride);
 }
 
 // s[base + r*stride + 2j (+1)] = <V_j,r, w_r>, j < K (w read once)

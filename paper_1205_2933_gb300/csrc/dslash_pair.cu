@@ -163,15 +163,20 @@ __device__ __forceinline__ void hop2(CP acc[12], const float2 *__restrict__ row,
 }
 
 // CTA = spb whole 4D sites x LS/2 threads; LS/2 divides 32 so that the
-// threads of a site share a warp.
+// threads of a site share a warp.  A site's 72 staged link elements are
+// LSTRIDE = 73 float4 apart: the sites of one warp then start 4 banks apart
+// and their broadcast reads of the same element need one shared-memory
+// wavefront instead of one per site.
+constexpr int LSTRIDE = 73;
+
 template <bool DAG, int LS, int MINB>
 __global__ void __launch_bounds__(128, MINB)
 dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, const float2 *__restrict__ U, Geom g,
                    float diag, float mf, int spb, int64_t field) {
     constexpr int TPS = LS / 2;  // threads per site
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *sL = reinterpret_cast<float4 *>(smem_raw);                 // [spb][8][9]
-    int *sN = reinterpret_cast<int *>(sL + (size_t)spb * 72);           // [spb][8]
+    float4 *sL = reinterpret_cast<float4 *>(smem_raw);                 // [spb][LSTRIDE]
+    int *sN = reinterpret_cast<int *>(sL + (size_t)spb * LSTRIDE);      // [spb][8]
     const int V = (int)g.V;
     const int site0 = blockIdx.x * spb;
     const size_t rhs_off = (size_t)blockIdx.y * (size_t)field;
@@ -203,7 +208,7 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
 #pragma unroll
             for (int e = 0; e < 9; ++e) {
                 const float re = coef * m[e].x, im = coef * m[e].y;
-                sL[(ls * 8 + k) * 9 + e] = make_float4(re, re, im, im);
+                sL[ls * LSTRIDE + k * 9 + e] = make_float4(re, re, im, im);
             }
             sN[ls * 8 + k] = nb;
         }
@@ -250,7 +255,7 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
         acc[dn_lo + q].im = add2(acc[dn_lo + q].im, pk(c_dn0 * pw, -sd.y));
     }
     if (!active) return;
-    const float4 *sLs = sL + ls * 72;
+    const float4 *sLs = sL + ls * LSTRIDE;
     const int *sNs = sN + ls * 8;
     const float fs = DAG ? 1.f : -1.f;  // sig of the forward hops
     hop2<0, false, LS>(acc, in + (size_t)sNs[0] * row + s0, sLs + 0 * 9, fs);
@@ -274,7 +279,7 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
     const Geom &g = c->g;
     constexpr int TPS = LS / 2;
     int spb = 128 / TPS;
-    const size_t per_site = 72 * sizeof(float4) + 8 * sizeof(int);
+    const size_t per_site = LSTRIDE * sizeof(float4) + 8 * sizeof(int);
     const int max_spb = (int)((46 * 1024) / per_site);
     if (spb > max_spb) spb = max_spb;
     const int threads = spb * TPS;

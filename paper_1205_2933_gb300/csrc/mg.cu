@@ -777,43 +777,79 @@ template <typename R> class BatchRunner {
     }
 
     // outer flexible GCR in FP64 with reliable updates, all right-hand sides together
+    // Right-hand sides that have converged leave the batch: each outer cycle
+    // gathers the unconverged residuals into the first slots and runs the
+    // lockstep GCR on that smaller batch.
     dwf_status solve(double2 *b, double2 *x, double tol, mg_stats &st) {
         const mg_params &p = mg.p;
-        const int64_t N = n(0), NT = N * nr;
+        const int nfull = nr;
+        const int64_t N = n(0), NT = N * nfull;
         double2 *r64 = mg_wsb64(0), *t64 = mg_wsb64(1);
         std::vector<double> sv;
-        norm2_b<double2>(c, mg.bscratch, SB, SS, b, N, nr);
+        norm2_b<double2>(c, mg.bscratch, SB, SS, b, N, nfull);
         read_block(sv);
-        std::vector<double> bn(nr), rn(nr);
-        for (int r = 0; r < nr; ++r) bn[r] = std::sqrt(sv[(size_t)r * SS]);
+        std::vector<double> bn(nfull), rn(nfull);
+        for (int r = 0; r < nfull; ++r) bn[r] = std::sqrt(sv[(size_t)r * SS]);
+        std::vector<int> idx;  // unconverged right-hand sides
         auto true_residual = [&]() {
-            dslash(c, t64, x, false, nr);
-            bcopy<double2, double2>(c, r64, b, NT);
-            caxpy<double2>(c, r64, make_double2(-1.0, 0.0), t64, NT);
-            norm2_b<double2>(c, mg.bscratch, SB, SS, r64, N, nr);
+            const int na = (int)idx.size();
+            if (na == nfull) {
+                dslash(c, t64, x, false, nfull);
+                bcopy<double2, double2>(c, r64, b, NT);
+                caxpy<double2>(c, r64, make_double2(-1.0, 0.0), t64, NT);
+                norm2_b<double2>(c, mg.bscratch, SB, SS, r64, N, nfull);
+            } else {
+                for (int r : idx) {
+                    const size_t o = (size_t)r * N;
+                    dslash(c, t64 + o, x + o, false, 1);
+                    bcopy<double2, double2>(c, r64 + o, b + o, N);
+                    caxpy<double2>(c, r64 + o, make_double2(-1.0, 0.0), t64 + o, N);
+                    norm2_b<double2>(c, mg.bscratch, SB + r * SS, SS, r64 + o, N, 1);
+                }
+            }
             read_block(sv);
-            for (int r = 0; r < nr; ++r) {
+            for (int r : idx) {
                 rn[r] = std::sqrt(sv[(size_t)r * SS]);
                 if (!std::isfinite(rn[r])) throw Error{DWF_ENAN, "NaN or Inf in the residual"};
             }
         };
-        true_residual();
+        for (int r = 0; r < nfull; ++r) {
+            if (bn[r] == 0.0) bzero<double2>(c, x + (size_t)r * N, N);  // x = 0 solves D x = 0 exactly
+            else idx.push_back(r);
+        }
+        for (int r = 0; r < nfull; ++r) rn[r] = 0.0;
+        if (!idx.empty()) true_residual();
         T *bR = wsb(0, 8), *eR = wsb(0, 9);
         long long iters = 0;
         int cycles = 0;
         const double floor_rel = std::is_same<R, float>::value ? 2e-6 : 0.0;
         dwf_status status = DWF_OK;
-        auto done = [&]() { for (int r = 0; r < nr; ++r) if (rn[r] > tol * bn[r]) return false; return true; };
-        while (!done()) {
+        while (true) {
+            idx.clear();
+            for (int r = 0; r < nfull; ++r)
+                if (rn[r] > tol * bn[r]) idx.push_back(r);
+            const int na = (int)idx.size();
+            if (na == 0) break;
             if (cycles * p.outer_restart >= p.outer_maxiter) {
                 status = DWF_ENOCONV;
                 break;
             }
-            std::vector<double> tin(nr);
-            for (int r = 0; r < nr; ++r)
-                tin[r] = (bn[r] == 0.0 || rn[r] <= tol * bn[r]) ? 1.0 : std::max(tol * bn[r] / rn[r], floor_rel);
-            bcopy<T, double2>(c, bR, r64, NT);
-            long long gi = gcr_b(eR, bR, tin, std::min(p.outer_restart, 32));
+            std::vector<double> tin(na);
+            for (int k = 0; k < na; ++k) {
+                const int r = idx[k];
+                tin[k] = std::max(tol * bn[r] / rn[r], floor_rel);
+                if (na < nfull) bcopy<T, double2>(c, bR + (size_t)k * N, r64 + (size_t)r * N, N);
+            }
+            if (na == nfull) bcopy<T, double2>(c, bR, r64, NT);
+            nr = na;
+            long long gi = 0;
+            try {
+                gi = gcr_b(eR, bR, tin, std::min(p.outer_restart, 32));
+            } catch (...) {
+                nr = nfull;
+                throw;
+            }
+            nr = nfull;
             if (gi == 0) {
                 status = DWF_EBREAKDOWN;
                 break;
@@ -821,16 +857,19 @@ template <typename R> class BatchRunner {
             iters += gi;
             ++cycles;
             st.restarts++;
-            caxpy_mixed<double2, T>(c, x, make_double2(1.0, 0.0), eR, NT);
+            if (na == nfull) caxpy_mixed<double2, T>(c, x, make_double2(1.0, 0.0), eR, NT);
+            else
+                for (int k = 0; k < na; ++k)
+                    caxpy_mixed<double2, T>(c, x + (size_t)idx[k] * N, make_double2(1.0, 0.0), eR + (size_t)k * N, N);
             true_residual();
             if (verbose()) {
-                fprintf(stderr, "[dwfmg batch] cycle %d active-iters %lld |r|/|b|:", cycles, gi);
-                for (int r = 0; r < nr; ++r) fprintf(stderr, " %.2e", bn[r] > 0 ? rn[r] / bn[r] : 0.0);
+                fprintf(stderr, "[dwfmg batch] cycle %d batch %d iters %lld |r|/|b|:", cycles, na, gi);
+                for (int r = 0; r < nfull; ++r) fprintf(stderr, " %.2e", bn[r] > 0 ? rn[r] / bn[r] : 0.0);
                 fprintf(stderr, "\n");
             }
         }
         st.iters += (int)iters;
-        for (int r = 0; r < nr; ++r) st.true_res = std::max(st.true_res, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
+        for (int r = 0; r < nfull; ++r) st.true_res = std::max(st.true_res, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
         return status;
     }
 
@@ -853,19 +892,44 @@ dwf_status setup_t(dwf_ctx *c, MGState &mg, int levels, const void *start, bool 
     return DWF_OK;
 }
 
-template <typename R>
-dwf_status solve_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, int nrhs, mg_stats &st) {
+// The batched path covers FP32 V-cycles on two levels with nu_1 = 0;
+// DWF_BATCH=0 in the environment turns it off.
+template <typename R> bool batch_eligible(const MGState &mg, int nrhs) {
     static const bool batch_on = [] {
         const char *e = getenv("DWF_BATCH");
         return !(e && atoi(e) == 0);
     }();
-    if (std::is_same<R, float>::value && nrhs > 1 && batch_on && mg.nlevels == 2 && mg.p.nu_pre == 0 &&
-        mg.p.outer_restart <= 32) {
+    return std::is_same<R, float>::value && nrhs > 1 && batch_on && mg.nlevels == 2 && mg.p.nu_pre == 0 &&
+           mg.p.outer_restart <= 32;
+}
+
+// Right-hand sides per batch: at most 32, and no more than the free device
+// memory holds (9 + 2 * restart fine fields in precision R and two FP64
+// fields per right-hand side, counting the batch workspaces already held).
+// 1 means: solve one at a time.
+template <typename R> int batch_width(const MGState &mg, int nrhs, bool solve) {
+    const int64_t N = mg.lev[0].lg.nelem;
+    const int restart = std::min(mg.p.outer_restart, 32);
+    const double per = (double)N * ((solve ? 9 + 2 * restart : 8) * sizeof(C<R>) + (solve ? 2 * sizeof(double2) : 0));
+    double held = 0;
+    for (const DevBuf &d : mg.wsb[0]) held += (double)d.bytes;
+    for (const DevBuf &d : mg.wsb64) held += (double)d.bytes;
+    size_t fr = 0, tot = 0;
+    DWF_CUDA(cudaMemGetInfo(&fr, &tot));
+    int nb = std::min(32, nrhs);
+    while (nb > 1 && nb * per - held > 0.9 * (double)fr) --nb;
+    return nb;
+}
+
+template <typename R>
+dwf_status solve_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, int nrhs, mg_stats &st) {
+    const int width = batch_eligible<R>(mg, nrhs) ? batch_width<R>(mg, nrhs, true) : 1;
+    if (width > 1) {
         const int64_t N = mg.lev[0].lg.nelem;
         dwf_status worst = DWF_OK;
         long long c0 = 0;
-        for (int r0 = 0; r0 < nrhs; r0 += 32) {
-            const int nb = std::min(32, nrhs - r0);
+        for (int r0 = 0; r0 < nrhs; r0 += width) {
+            const int nb = std::min(width, nrhs - r0);
             BatchRunner<R> br(c, mg, nb);
             dwf_status s = br.solve(b + (size_t)r0 * N, x + (size_t)r0 * N, tol, st);
             if (s != DWF_OK && worst == DWF_OK) worst = s;
@@ -1072,13 +1136,27 @@ template <typename R> void coarse_solve_t(dwf_ctx *c, MGState &mg, int level, vo
     DWF_CUDA(cudaMemcpyAsync(x, xl, sizeof(T) * N, cudaMemcpyDeviceToDevice, c->stream));
     DWF_CUDA(cudaStreamSynchronize(c->stream));
 }
-template <typename R> void vcycle_t(dwf_ctx *c, MGState &mg, double2 *x, const double2 *b) {
-    Runner<R> run(c, mg);
+template <typename R> void vcycle_t(dwf_ctx *c, MGState &mg, double2 *x, const double2 *b, int nrhs) {
     const int64_t N = mg.lev[0].lg.nelem;
-    C<R> *bR = run.ws(0, 8), *xR = run.ws(0, 9);
-    bcopy<C<R>, double2>(c, bR, b, N);
-    run.vcycle(0, xR, bR);
-    bcopy<double2, C<R>>(c, x, xR, N);
+    const int width = batch_eligible<R>(mg, nrhs) ? batch_width<R>(mg, nrhs, false) : 1;
+    if (width > 1) {
+        for (int r0 = 0; r0 < nrhs; r0 += width) {
+            const int nb = std::min(width, nrhs - r0);
+            BatchRunner<R> br(c, mg, nb);
+            C<R> *bR = br.wsb(0, 8), *xR = br.wsb(0, 9);
+            bcopy<C<R>, double2>(c, bR, b + (size_t)r0 * N, N * nb);
+            br.vcycle_b(xR, bR);
+            bcopy<double2, C<R>>(c, x + (size_t)r0 * N, xR, N * nb);
+        }
+    } else {
+        Runner<R> run(c, mg);
+        C<R> *bR = run.ws(0, 8), *xR = run.ws(0, 9);
+        for (int r = 0; r < nrhs; ++r) {
+            bcopy<C<R>, double2>(c, bR, b + (size_t)r * N, N);
+            run.vcycle(0, xR, bR);
+            bcopy<double2, C<R>>(c, x + (size_t)r * N, xR, N);
+        }
+    }
     DWF_CUDA(cudaStreamSynchronize(c->stream));
 }
 }  // namespace
@@ -1090,10 +1168,10 @@ void mg_coarse_solve_impl(dwf_ctx *c, int level, void *x, const void *b) {
     else coarse_solve_t<double>(c, mg, level, x, b);
 }
 
-void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b) {
+void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b, int nrhs) {
     MGState &mg = need_mg(c, 0, 0, 1);
-    if (mg.p.smoother_prec == DWF_F32) vcycle_t<float>(c, mg, x, b);
-    else vcycle_t<double>(c, mg, x, b);
+    if (mg.p.smoother_prec == DWF_F32) vcycle_t<float>(c, mg, x, b, nrhs);
+    else vcycle_t<double>(c, mg, x, b, nrhs);
 }
 
 dwf_status cg_solve_impl(dwf_ctx *c, const void *b, void *x, double tol, int maxiter, int nrhs, dwf_prec prec,

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "dwf_internal.cuh"
+#include "dwfnet.h"
 
 namespace dwf {
 
@@ -71,7 +72,7 @@ void mg_get_coarse_links_impl(dwf_ctx *c, int level, double2 *out);
 void mg_restrict_impl(dwf_ctx *c, int level, double2 *cout, const double2 *fin);
 void mg_prolong_impl(dwf_ctx *c, int level, double2 *fout, const double2 *cin);
 void mg_coarse_apply_impl(dwf_ctx *c, int level, void *out, const void *in, bool dag, dwf_prec prec);
-void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b);
+void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b, int nrhs);
 void mg_coarse_solve_impl(dwf_ctx *c, int level, void *x, const void *b);
 void mg_coarse_solve_static_impl(dwf_ctx *c, int level, void *x, const void *b);
 
@@ -139,5 +140,16 @@ template <typename T> void gcr_step(dwf_ctx *c, T *x, T *r, T *z, T *w, int iww,
 // x = a * x + b * y (real a, complex b) fused for two pairs: used by GCR updates
 template <typename T> void gauss_fill(dwf_ctx *c, double2 *out, int nfields, int64_t nelem, int Ls, int64_t V,
                                       bool canonical_fine, uint32_t seed, uint32_t stream);
+
+// ---- net.cu ---- learned near-null proposal (include/dwfnet.h)
+dwf_net *net_create_impl(dwf_ctx *c, const dwf_net_shape &s);
+void net_set_params_impl(dwf_net *net, const void *p, bool dev);
+void net_get_params_impl(dwf_net *net, void *p, bool dev);
+void net_forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed, double2 *out);
+double net_loss_grad_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed,
+                          const double2 *targets, int nt, const int block[4], void *grad, bool grad_dev);
+void net_adam_impl(dwf_net *net, double lr, double b1, double b2, double eps);
+long long net_nparams(const dwf_net *net);
+void net_free(dwf_net *net);
 
 }  // namespace dwf

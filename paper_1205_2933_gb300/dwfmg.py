@@ -1,4 +1,4 @@
-"""Python binding of the dwfmg C ABI (include/dwfmg.h).
+"""Python binding of the dwfmg C ABI (include/dwfmg.h, include/dwfnet.h).
 
 Argument marshalling only: every computation runs in the CUDA library
 libdwfmg.so.  The functions keep the C names; arrays are torch tensors
@@ -59,6 +59,11 @@ class mg_stats(ctypes.Structure):
                 "true_res": self.true_res, "seconds": self.seconds}
 
 
+class dwf_net_shape(ctypes.Structure):
+    _fields_ = [("c_in", ctypes.c_int), ("hidden", ctypes.c_int), ("layers", ctypes.c_int),
+                ("nout", ctypes.c_int), ("Ls", ctypes.c_int)]
+
+
 class DWFError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -94,6 +99,7 @@ def _load():
     L.mg_prolong.argtypes = [vp, i, vp, vp]
     L.mg_coarse_apply.argtypes = [vp, i, vp, vp, i, st]
     L.mg_vcycle.argtypes = [vp, vp, vp]
+    L.mg_vcycle_batch.argtypes = [vp, vp, vp, i]
     L.mg_coarse_solve.argtypes = [vp, i, vp, vp]
     L.mg_coarse_solve.restype = st
     L.mg_coarse_solve_static.argtypes = [vp, i, vp, vp]
@@ -104,9 +110,21 @@ def _load():
     L.dwf_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
     L.dwf_launch_count.argtypes = []
     L.dwf_launch_count.restype = ctypes.c_ulonglong
+    L.net_create.argtypes = [vp, ctypes.POINTER(dwf_net_shape), ctypes.POINTER(vp)]
+    L.net_num_params.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.net_set_params.argtypes = [vp, vp]
+    L.net_get_params.argtypes = [vp, vp]
+    L.net_forward.argtypes = [vp, vp, vp, ctypes.c_uint, vp]
+    L.net_loss_grad.argtypes = [vp, vp, vp, ctypes.c_uint, vp, i, ip, ctypes.POINTER(ctypes.c_double), vp]
+    L.net_adam.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.net_destroy.argtypes = [vp]
+    L.net_destroy.restype = None
+    for name in ("net_create", "net_num_params", "net_set_params", "net_get_params", "net_forward",
+                 "net_loss_grad", "net_adam"):
+        getattr(L, name).restype = st
     for name in ("dwf_profile", "dwf_profile_read", "dwf_create", "dwf_apply", "dwf_pack", "dwf_unpack", "mg_setup", "mg_solve", "mg_level_info",
                  "mg_get_vectors", "mg_get_coarse_links", "mg_restrict", "mg_prolong", "mg_coarse_apply",
-                 "mg_vcycle"):
+                 "mg_vcycle", "mg_vcycle_batch"):
         getattr(L, name).restype = st
     return L
 
@@ -239,6 +257,10 @@ def mg_vcycle(ctx, x, b):
     return _check(_lib.mg_vcycle(ctx, _ptr(x), _ptr(b)), "mg_vcycle")
 
 
+def mg_vcycle_batch(ctx, x, b, nrhs):
+    return _check(_lib.mg_vcycle_batch(ctx, _ptr(x), _ptr(b), int(nrhs)), "mg_vcycle_batch")
+
+
 K_DSLASH_F64, K_DSLASH_F32, K_RESTRICT, K_PROLONG, K_COARSE = 0, 1, 2, 3, 4
 
 
@@ -285,3 +307,47 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ---- learned near-null proposal (include/dwfnet.h) ----
+
+def net_create(ctx, c_in, hidden, layers, nout, Ls):
+    h = ctypes.c_void_p()
+    sh = dwf_net_shape(int(c_in), int(hidden), int(layers), int(nout), int(Ls))
+    _check(_lib.net_create(ctx, ctypes.byref(sh), ctypes.byref(h)), "net_create")
+    return h
+
+
+def net_num_params(net):
+    n = ctypes.c_longlong()
+    _check(_lib.net_num_params(net, ctypes.byref(n)), "net_num_params")
+    return n.value
+
+
+def net_set_params(net, params):
+    return _check(_lib.net_set_params(net, _ptr(params)), "net_set_params")
+
+
+def net_get_params(net, params):
+    return _check(_lib.net_get_params(net, _ptr(params)), "net_get_params")
+
+
+def net_forward(net, ctx, out, input=None, seed=0):
+    return _check(_lib.net_forward(net, ctx, _ptr(input), int(seed), _ptr(out)), "net_forward")
+
+
+def net_loss_grad(net, ctx, targets, nt, block, input=None, seed=0, grad=None):
+    b = (ctypes.c_int * 4)(*[int(x) for x in block])
+    loss = ctypes.c_double()
+    _check(_lib.net_loss_grad(net, ctx, _ptr(input), int(seed), _ptr(targets), int(nt), b, ctypes.byref(loss),
+                              _ptr(grad)), "net_loss_grad")
+    return loss.value
+
+
+def net_adam(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    return _check(_lib.net_adam(net, float(lr), float(beta1), float(beta2), float(eps)), "net_adam")
+
+
+def net_destroy(net):
+    _lib.net_destroy(net)
+

@@ -1,5 +1,6 @@
 """CPU checks of the C-ABI boundary: the library builds, loads, and exports
-every function include/dwfmg.h declares (no compute calls without a GPU)."""
+every function include/dwfmg.h and include/dwfnet.h declare (no compute calls
+without a GPU)."""
 import ctypes
 import os
 import re
@@ -11,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "dwfmg.h")).read()
+    text = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("dwfmg.h", "dwfnet.h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?(?:dwf_status|void|unsigned long long|const char\s*\*|char\s*\*)\s*\*?\s*(\w+)\s*\(",
                        text, flags=re.M)
@@ -27,7 +28,8 @@ def libpath():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("dwf_create", "dwf_apply", "mg_setup", "mg_solve", "dwf_pack", "dwf_unpack",
-                     "dwf_strerror", "dwf_destroy", "mg_default_params"):
+                     "dwf_strerror", "dwf_destroy", "mg_default_params", "net_create", "net_forward",
+                     "net_loss_grad", "net_adam", "mg_vcycle_batch"):
         assert required in names
 
 
@@ -51,6 +53,8 @@ def test_library_loads_and_host_only_calls(libpath):
     d = (ctypes.c_int * 4)(4, 4, 4, 4)
     assert G.lib().dwf_create(ctypes.byref(h), d, 0, 1.8, 0.1, None, 1, None) == G.DWF_EINVAL
     assert G.lib().dwf_apply(None, None, None, 0, 0, 1) == G.DWF_EINVAL
+    assert G.lib().net_create(None, None, None) == G.DWF_EINVAL
+    assert G.lib().net_adam(None, 1e-3, 0.9, 0.999, 1e-8) == G.DWF_EINVAL
 
 
 def test_no_cpu_fallback_in_product_path():

@@ -188,6 +188,33 @@ def test_vcycle_parity(G):
     c.close()
 
 
+@pytest.mark.parametrize("cfg", [SMALL, RAGGED], ids=["4^4xLs8", "ragged"])
+def test_vcycle_batch_parity(G, cfg):
+    """The batched FP32 V-cycle (three right-hand sides together) against the
+    oracle's V-cycle of each and against the one-at-a-time GPU V-cycle.  A
+    fixed number of coarsest GCR iterations (tolerance 0) keeps both sides on
+    the same Krylov step count, so the comparison is one of rounding only."""
+    c = Case(G, **cfg, setup_iters0=10, setup_sweeps=0, smoother_prec=G.DWF_F32,
+             coarse_prec=[G.DWF_F32], coarsest_tol=0.0, coarsest_maxiter=8, nu_post=4)
+    from gpu_util import to_internal, to_canonical, rel_norm
+    nr = 3
+    bs = [I.gaussian_source(c.dims, c.Ls, 40 + r) for r in range(nr)]
+    bt = torch.cat([to_internal(c.ctx, b) for b in bs])
+    xb = torch.empty_like(bt)
+    G.mg_vcycle_batch(c.ctx.h, xb, bt, nr)
+    n = c.ctx.field_elems
+    for r in range(nr):
+        x1 = torch.empty(n, dtype=torch.complex128, device="cuda")
+        G.mg_vcycle(c.ctx.h, x1, bt[r * n:(r + 1) * n].contiguous())
+        e1 = (xb[r * n:(r + 1) * n] - x1).norm().item() / x1.norm().item()
+        assert e1 < 1e-4, (r, e1)
+        got = to_canonical(c.ctx, xb[r * n:(r + 1) * n].contiguous(), bs[r].shape)
+        ref = c.mg.vcycle(0, bs[r].reshape(c.op.shape)).reshape(bs[r].shape)
+        eo = rel_norm(got, ref)
+        assert eo < 1e-4, (r, eo)
+    c.close()
+
+
 def test_vcycle_galerkin_orthogonality(G):
     """nu1 = nu3 = 0 and a tight coarse solve: R (b - D x) = 0 on the GPU."""
     c = Case(G, **SMALL, setup_iters0=10, setup_sweeps=0, nu_post=0, coarsest_tol=1e-12,
@@ -334,5 +361,24 @@ def test_batched_solve_matches_oracle(G, nrhs):
     assert st.true_res <= 1e-10
     x = to_canonical(c.ctx, xt, bs.shape, nrhs=nrhs)
     for i in (0, nrhs - 1):
+        assert rel_norm(x[i], _oracle_solution(c, bs[i])) < 1e-8
+    c.close()
+
+
+def test_batched_solve_zero_member_and_guess(G):
+    """A zero right-hand side inside a batch gets x = 0 whatever the initial
+    guess; the others start from the guess and still reach the oracle's
+    solutions (members leave the batch as they converge)."""
+    c = Case(G, **SMALL, setup_sweeps=0, smoother_prec=G.DWF_F32, coarse_prec=[G.DWF_BF16])
+    from gpu_util import to_internal, to_canonical, rel_norm
+    bs = np.stack([I.gaussian_source(c.dims, c.Ls, 70 + i) for i in range(3)])
+    bs[1] = 0.0
+    bt = to_internal(c.ctx, bs, nrhs=3)
+    xt = torch.full_like(bt, 0.25)
+    st = G.mg_solve(c.ctx.h, bt, xt, 1e-10, nrhs=3)
+    assert st.true_res <= 1e-10
+    x = to_canonical(c.ctx, xt, bs.shape, nrhs=3)
+    assert np.abs(x[1]).max() == 0.0
+    for i in (0, 2):
         assert rel_norm(x[i], _oracle_solution(c, bs[i])) < 1e-8
     c.close()

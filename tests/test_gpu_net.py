@@ -1,0 +1,139 @@
+"""GPU parity of the learned near-null proposal (include/dwfnet.h) against the
+FP64 network oracle (oracle/net.py) on identical seeded inputs: forward
+outputs, the block-projection loss and every parameter gradient; plus gauge
+covariance on the GPU and a few Adam steps lowering the loss."""
+import numpy as np
+import pytest
+
+from oracle import net as N
+import paper_1205_2933_gb300.inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+DIMS = (4, 4, 4, 4)
+LS = 8
+BLOCK = (2, 2, 2, 2)
+SHAPE = N.NetShape(c_in=2, hidden=4, layers=2, nout=3, Ls=LS)
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1205_2933_gb300 import dwfmg
+    return dwfmg
+
+
+def _params(shape, seed):
+    parts = []
+    for k, sh in enumerate(N.param_shapes(shape)):
+        fan_in = int(np.prod(sh[2:])) if k < shape.layers else int(np.prod(sh[3:]))
+        parts.append(I.gauss_complex(sh, seed + k, I.STREAM_NETWORK) / np.sqrt(fan_in))
+    return parts
+
+
+def _input(shape, dims, seed):
+    X, Y, Z, T = dims
+    return I.gauss_complex((shape.c_in, 4, T, Z, Y, X, 3), seed, I.STREAM_NETWORK)
+
+
+class NetCase:
+    def __init__(self, G, U, shape=SHAPE, pseed=10):
+        from gpu_util import ctx_for
+        self.G, self.U, self.shape = G, U, shape
+        self.ctx = ctx_for(U, DIMS, shape.Ls, 1.8, 0.1)
+        self.net = G.net_create(self.ctx.h, shape.c_in, shape.hidden, shape.layers, shape.nout, shape.Ls)
+        self.p = _params(shape, pseed)
+        flat = N.flatten(self.p)
+        assert G.net_num_params(self.net) == flat.size
+        G.net_set_params(self.net, np.ascontiguousarray(flat))
+
+    def forward(self, h0=None, seed=0):
+        out = torch.empty(self.shape.nout * self.ctx.field_elems, dtype=torch.complex128, device="cuda")
+        inp = None if h0 is None else np.ascontiguousarray(h0)
+        self.G.net_forward(self.net, self.ctx.h, out, input=inp, seed=seed)
+        torch.cuda.synchronize()
+        X, Y, Z, T = DIMS
+        return out.cpu().numpy().reshape(self.shape.nout, self.shape.Ls, T, Z, Y, X, 12)
+
+    def close(self):
+        self.G.net_destroy(self.net)
+        self.ctx.close()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_forward_matches_oracle(G):
+    U = I.epsilon_links(DIMS, 0.4, 3)
+    c = NetCase(G, U)
+    h0 = _input(SHAPE, DIMS, 20)
+    got = c.forward(h0)
+    ref, _ = N.forward(SHAPE, c.p, U, h0, DIMS)
+    assert _rel(got, ref) < 1e-5
+    # the device Philox input equals the host generator's field
+    got2 = c.forward(None, seed=20)
+    assert _rel(got2, got) < 1e-6
+    # parameters round-trip through the device copy (FP32 storage)
+    back = np.empty(G.net_num_params(c.net), dtype=np.complex128)
+    G.net_get_params(c.net, back)
+    flat = N.flatten(c.p)
+    assert np.abs(back - flat).max() < 1e-6 * np.abs(flat).max()
+    c.close()
+
+
+def test_forward_gauge_covariance(G):
+    U = I.epsilon_links(DIMS, 0.5, 4)
+    g = I.random_gauge_transform(DIMS, 5)
+    h0 = _input(SHAPE, DIMS, 21)
+    c1 = NetCase(G, U)
+    v = c1.forward(h0)
+    c1.close()
+    c2 = NetCase(G, N.gauge_transform_links(g, U))
+    vg = c2.forward(N.gauge_transform_field(g, h0))
+    c2.close()
+    v6 = v.reshape(v.shape[:6] + (4, 3))
+    expect = np.einsum("tzyxab,jstzyxcb->jstzyxca", g, v6).reshape(v.shape)
+    assert _rel(vg, expect) < 1e-5
+
+
+def test_loss_and_gradient_match_oracle(G):
+    from gpu_util import to_internal
+    U = I.epsilon_links(DIMS, 0.4, 6)
+    c = NetCase(G, U, pseed=30)
+    h0 = _input(SHAPE, DIMS, 31)
+    X, Y, Z, T = DIMS
+    nt = 4
+    q = I.gauss_complex((nt, LS, T, Z, Y, X, 12), 32, I.STREAM_NETWORK)
+    qt = to_internal(c.ctx, q, nrhs=nt)
+    grad = np.empty(G.net_num_params(c.net), dtype=np.complex128)
+    L = G.net_loss_grad(c.net, c.ctx.h, qt, nt, BLOCK, input=np.ascontiguousarray(h0), grad=grad)
+    Lo, go = N.loss_and_grad(SHAPE, c.p, U, h0, q, DIMS, BLOCK)
+    assert abs(L - Lo) < 1e-5 * Lo
+    parts = N.unflatten(SHAPE, grad)
+    for k, (a, b) in enumerate(zip(parts, go)):
+        assert _rel(a, b) < 1e-4, (k, _rel(a, b))
+    c.close()
+
+
+def test_adam_lowers_the_loss_and_breakdown(G):
+    from gpu_util import to_internal
+    U = I.epsilon_links(DIMS, 0.4, 7)
+    c = NetCase(G, U, pseed=40)
+    X, Y, Z, T = DIMS
+    nt = 6
+    q = I.gauss_complex((nt, LS, T, Z, Y, X, 12), 41, I.STREAM_NETWORK)
+    qt = to_internal(c.ctx, q, nrhs=nt)
+    losses = []
+    for _ in range(30):
+        losses.append(G.net_loss_grad(c.net, c.ctx.h, qt, nt, BLOCK, seed=42))
+        G.net_adam(c.net, 3e-3)
+    assert losses[-1] < 0.9 * losses[0], losses
+    # a network with zero parameters proposes zero vectors: Gram-Schmidt breaks down
+    G.net_set_params(c.net, np.zeros(G.net_num_params(c.net), dtype=np.complex128))
+    with pytest.raises(G.DWFError) as e:
+        G.net_loss_grad(c.net, c.ctx.h, qt, nt, BLOCK, seed=42)
+    assert e.value.status == G.DWF_EBREAKDOWN
+    with pytest.raises(G.DWFError):
+        G.net_adam(c.net, 1e-3)   # no gradient since the parameters were set
+    c.close()
