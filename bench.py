@@ -47,6 +47,10 @@ BLOCK = (4, 4, 4, 4)
 NRHS = 12
 TOL = 1e-10
 FINE_BYTES_F32 = 204   # algorithmic bytes per 5D site of the FP32 Dslash
+# dram__bytes_read.sum + dram__bytes_write.sum of one one-field launch of the
+# current FP32 Dslash kernel from an ncu capture (profiles/); None until the
+# kernel as it stands has been captured
+DSLASH_TRAFFIC_PER_FIELD = None
 FINE_BYTES_F64 = 408
 
 
@@ -290,9 +294,10 @@ def main():
     launches = G.dwf_launch_count() - launches0
     ms_total = t0.elapsed_time(t1)
     clk = clocks.stop()
-    prof = {name: G.dwf_profile_read(ctx.h, k) for name, k in
-            (("dslash_f32", G.K_DSLASH_F32), ("dslash_f64", G.K_DSLASH_F64), ("restrict", G.K_RESTRICT),
-             ("prolong", G.K_PROLONG), ("coarse", G.K_COARSE))}
+    classes = (("dslash_f32", G.K_DSLASH_F32), ("dslash_f64", G.K_DSLASH_F64), ("restrict", G.K_RESTRICT),
+               ("prolong", G.K_PROLONG), ("coarse", G.K_COARSE))
+    prof = {name: G.dwf_profile_read(ctx.h, k) for name, k in classes}
+    units = {name: G.dwf_profile_units(ctx.h, k) for name, k in classes}
     G.dwf_profile(ctx.h, False)
     if dist:
         t = torch.tensor([ms_total], device=dev)
@@ -303,16 +308,19 @@ def main():
 
     # roofline of the dominant kernel: the FP32 fine Dslash
     n32, ms32 = prof["dslash_f32"]
+    u32 = units["dslash_f32"]
     V5 = ctx.V * LS
     peak, peak_kind = measured_peaks()
     roof = None
     if n32:
-        avg = ms32 / n32
-        achieved = FINE_BYTES_F32 * V5 / (avg * 1e-3) / 1e9
+        # launches cover 1 (setup, single solves) or nrhs (batched solve) fields:
+        # algorithmic bytes of all of them over their summed device time
+        achieved = FINE_BYTES_F32 * V5 * u32 / (ms32 * 1e-3) / 1e9
         roof = {"kernel": "dslash_f32", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "avg_launch_us": avg * 1e3, "launches": n32,
-                "bytes_per_launch": FINE_BYTES_F32 * V5}
+                "frac": achieved / peak, "traffic": DSLASH_TRAFFIC_PER_FIELD, "peak_kind": peak_kind,
+                "avg_launch_us": ms32 / n32 * 1e3, "launches": n32, "fields": u32,
+                "bytes_per_launch": FINE_BYTES_F32 * V5 * u32 / n32,
+                "traffic_note": "ncu dram bytes per field application (one-field launch)"}
 
     applies_per_solve = None
     if stats:
@@ -325,7 +333,7 @@ def main():
             "dtype": "f32+bf16 (fp64 outer)", "data": "synthetic (seeded heatbath links, Gaussian sources)",
             "config": workload_config(nrhs), "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
             "solve_stats": stats[-1] if stats else None,
-            "kernel_time_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()}}
+            "kernel_time_ms": {k: {"launches": v[0], "fields": units[k], "ms": v[1]} for k, v in prof.items()}}
 
     if args.plain and rank == 0:
         line["plain_fp64"] = run_plain(G, torch, ctx, b, nrhs)

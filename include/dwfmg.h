@@ -244,6 +244,10 @@ dwf_status mg_vcycle_batch(dwf_ctx *ctx, void *x_dev, const void *b_dev, int nrh
  * D in FP32, 2 = restriction, 3 = prolongation, 4 = coarse stencil. */
 dwf_status dwf_profile(dwf_ctx *ctx, int enable);
 dwf_status dwf_profile_read(dwf_ctx *ctx, int kernel_class, long long *launches, double *total_ms);
+/* The number of fields (right-hand sides) the recorded launches of one class
+ * processed: a batched launch over nrhs fields counts nrhs (classes 0, 1: fine
+ * D applications; 2, 3: batched transfers count their right-hand sides). */
+dwf_status dwf_profile_units(dwf_ctx *ctx, int kernel_class, long long *units);
 
 /* Number of kernels this library has launched in the process so far. */
 unsigned long long dwf_launch_count(void);

@@ -92,6 +92,20 @@ dwf_status net_adam(dwf_net *net, double lr, double beta1, double beta2, double 
 
 void net_destroy(dwf_net *net);
 
+/* The learned setup: mg_setup (dwfmg.h) started from the network's proposal
+ * for the links of ctx (net_forward with input NULL and this seed), which
+ * opt->setup_iters0 relaxation iterations then refine.  nout of the network
+ * must be nvec[0]/2 (opt->split = 1) or nvec[0].
+ * Fallback to the plain adaptive setup: when probe_max_iters > 0, a probe
+ * solve (a Gaussian source from Philox-4x32-10 with key (seed, 3), x = 0)
+ * runs to the relative residual probe_tol; if it needs more than
+ * probe_max_iters outer iterations or fails, the setup is redone from random
+ * vectors with setup_iters0 = fallback_iters0, and *used_fallback (if not
+ * NULL) is set to 1 (else 0).  Synchronous. */
+dwf_status mg_setup_learned(dwf_ctx *ctx, dwf_net *net, unsigned int seed, int levels, const int *nvec,
+                            const int (*block)[4], const mg_params *opt, int fallback_iters0, double probe_tol,
+                            int probe_max_iters, int *used_fallback);
+
 #ifdef __cplusplus
 }
 #endif

@@ -279,6 +279,15 @@ dwf_status dwf_profile_read(dwf_ctx *c, int kernel_class, long long *launches, d
     });
 }
 
+dwf_status dwf_profile_units(dwf_ctx *c, int kernel_class, long long *units) {
+    if (!c || !units || kernel_class < 0 || kernel_class >= dwf::K_NCLASS) return DWF_EINVAL;
+    long long u = 0;
+    for (auto &r : c->prof_rec)
+        if (r.cls == kernel_class) u += r.units;
+    *units = u;
+    return DWF_OK;
+}
+
 unsigned long long dwf_launch_count(void) { return dwf::launch_count(); }
 
 // ---- learned near-null proposal (include/dwfnet.h) ----
@@ -344,5 +353,43 @@ void net_destroy(dwf_net *net) {
     if (net) dwf::net_free(net);
 }
 
-}  // extern "C"
+dwf_status mg_setup_learned(dwf_ctx *c, dwf_net *net, unsigned int seed, int levels, const int *nvec,
+                            const int (*block)[4], const mg_params *opt, int fallback_iters0, double probe_tol,
+                            int probe_max_iters, int *used_fallback) {
+    if (!c || !net || !nvec || !block || levels < 2) return DWF_EINVAL;
+    if (used_fallback) *used_fallback = 0;
+    mg_params p;
+    if (opt) p = *opt;
+    else mg_default_params(&p);
+    const int nout = dwf::net_nout(net);
+    if (nout != (p.split ? nvec[0] / 2 : nvec[0])) return DWF_EINVAL;
+    dwf::DevBuf start;
+    dwf_status s = guarded(c, [&]() -> dwf_status {
+        start.alloc(sizeof(double2) * (size_t)nout * c->g.V * 12 * c->g.Ls);
+        dwf::net_forward_impl(net, c, nullptr, false, seed, start.as<double2>());
+        return DWF_OK;
+    });
+    if (s != DWF_OK) return s;
+    s = mg_setup(c, levels, nvec, block, &p, start.p);
+    start.release();
+    if (s != DWF_OK || probe_max_iters <= 0) return s;
+    const int64_t n = c->g.V * 12 * c->g.Ls;
+    dwf::DevBuf b, x;
+    s = guarded(c, [&]() -> dwf_status {
+        b.alloc(sizeof(double2) * n);
+        x.alloc(sizeof(double2) * n);
+        dwf::gauss_fill<double2>(c, b.as<double2>(), 1, n, c->g.Ls, c->g.V, false, seed, 3u);
+        dwf::bzero<double2>(c, x.as<double2>(), n);
+        return DWF_OK;
+    });
+    if (s != DWF_OK) return s;
+    mg_stats st;
+    dwf_status ps = mg_solve(c, b.p, x.p, probe_tol, 1, &st);
+    if (ps == DWF_OK && st.iters <= probe_max_iters) return DWF_OK;
+    if (ps != DWF_OK && ps != DWF_ENOCONV && ps != DWF_EBREAKDOWN) return ps;
+    if (used_fallback) *used_fallback = 1;
+    p.setup_iters0 = fallback_iters0;
+    return mg_setup(c, levels, nvec, block, &p, nullptr);
+}
 
+}  // extern "C"

@@ -208,7 +208,7 @@ static cudaEvent_t take_event(dwf_ctx *c) {
     return e;
 }
 
-ProfScope::ProfScope(dwf_ctx *ctx, int k) : c(ctx), cls(k) {
+ProfScope::ProfScope(dwf_ctx *ctx, int k, int nunits) : c(ctx), cls(k), units(nunits) {
     if (!c->prof) return;
     a = take_event(c);
     b = take_event(c);
@@ -217,7 +217,7 @@ ProfScope::ProfScope(dwf_ctx *ctx, int k) : c(ctx), cls(k) {
 
 ProfScope::~ProfScope() {
     if (!a) return;
-    if (cudaEventRecord(b, c->stream) == cudaSuccess) c->prof_rec.push_back(ProfRecord{cls, a, b});
+    if (cudaEventRecord(b, c->stream) == cudaSuccess) c->prof_rec.push_back(ProfRecord{cls, a, b, units});
 }
 
 void prof_reset(dwf_ctx *c) {

@@ -206,7 +206,7 @@ void launch(dwf_ctx *c, C<R> *out, const C<R> *in, const C<R> *U, bool dag, int 
 }  // namespace
 
 void dslash(dwf_ctx *c, double2 *out, const double2 *in, bool dag, int nrhs) {
-    ProfScope ps(c, K_DSLASH_F64);
+    ProfScope ps(c, K_DSLASH_F64, nrhs);
     launch<double>(c, out, in, c->U64.as<double2>(), dag, nrhs);
     c->applies64 += nrhs;
 }
@@ -215,7 +215,7 @@ bool dslash_pair_supported(int Ls);
 void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb);
 
 void dslash(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs) {
-    ProfScope ps(c, K_DSLASH_F32);
+    ProfScope ps(c, K_DSLASH_F32, nrhs);
     // two slices per thread with packed FP32x2 arithmetic where Ls allows;
     // DWF_DSLASH_PAIR=0 selects the one-slice kernel
     static const int pair_minb = [] {

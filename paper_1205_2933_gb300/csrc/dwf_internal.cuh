@@ -142,6 +142,7 @@ enum KernelClass { K_DSLASH_F64 = 0, K_DSLASH_F32 = 1, K_RESTRICT = 2, K_PROLONG
 struct ProfRecord {
     int cls;
     cudaEvent_t a, b;
+    int units;  // fields (right-hand sides) the bracketed launch processed
 };
 
 }  // namespace dwf
@@ -174,9 +175,9 @@ namespace dwf {
 // Brackets one kernel launch with profiling events when the profiler is on.
 struct ProfScope {
     dwf_ctx *c;
-    int cls;
+    int cls, units;
     cudaEvent_t a = nullptr, b = nullptr;
-    ProfScope(dwf_ctx *ctx, int k);
+    ProfScope(dwf_ctx *ctx, int k, int nunits = 1);
     ~ProfScope();
 };
 void prof_reset(dwf_ctx *c);

@@ -150,6 +150,7 @@ double net_loss_grad_impl(dwf_net *net, dwf_ctx *c, const void *input, bool inpu
                           const double2 *targets, int nt, const int block[4], void *grad, bool grad_dev);
 void net_adam_impl(dwf_net *net, double lr, double b1, double b2, double eps);
 long long net_nparams(const dwf_net *net);
+int net_nout(const dwf_net *net);
 void net_free(dwf_net *net);
 
 }  // namespace dwf

@@ -806,6 +806,7 @@ void net_adam_impl(dwf_net *net, double lr, double b1, double b2, double eps) {
 }
 
 long long net_nparams(const dwf_net *net) { return net->nparams; }
+int net_nout(const dwf_net *net) { return net->sh.nout; }
 void net_free(dwf_net *net) { delete net; }
 
 }  // namespace dwf

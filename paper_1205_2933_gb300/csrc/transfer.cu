@@ -398,7 +398,7 @@ __global__ void to_half_kernel(__half2 *__restrict__ out, const float2 *__restri
 template <typename R>
 void restrict_batch(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, const C<R> *Q, int nrhs) {
     BlockMap m = make_map(L);
-    ProfScope ps(c, K_RESTRICT);
+    ProfScope ps(c, K_RESTRICT, nrhs);
     const int64_t cstride = ncoarse(m) * L.nv;
     for (int r0 = 0; r0 < nrhs; r0 += 12) {
 #define RB(NV) restrict_b_kernel<R, NV, 12><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(cout, fin, Q, m, nrhs, r0, cstride)
@@ -411,7 +411,7 @@ void restrict_batch(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, con
 template <typename R>
 void prolong_batch(dwf_ctx *c, const Level &L, C<R> *fout, const C<R> *cin, const C<R> *Q, int nrhs, bool acc) {
     BlockMap m = make_map(L);
-    ProfScope ps(c, K_PROLONG);
+    ProfScope ps(c, K_PROLONG, nrhs);
     const int64_t cstride = ncoarse(m) * L.nv;
     const size_t smem = sizeof(C<R>) * (size_t)nrhs * L.nv;
     DWF_REQUIRE(smem <= 46 * 1024, DWF_EINVAL, "too many right-hand sides for the batched prolongation");

@@ -108,6 +108,8 @@ def _load():
     L.dwf_cg_solve.restype = st
     L.dwf_profile.argtypes = [vp, i]
     L.dwf_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+    L.dwf_profile_units.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong)]
+    L.dwf_profile_units.restype = st
     L.dwf_launch_count.argtypes = []
     L.dwf_launch_count.restype = ctypes.c_ulonglong
     L.net_create.argtypes = [vp, ctypes.POINTER(dwf_net_shape), ctypes.POINTER(vp)]
@@ -119,6 +121,9 @@ def _load():
     L.net_adam.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.net_destroy.argtypes = [vp]
     L.net_destroy.restype = None
+    L.mg_setup_learned.argtypes = [vp, vp, ctypes.c_uint, i, ip, ip, ctypes.POINTER(mg_params), i, ctypes.c_double, i,
+                                   ip]
+    L.mg_setup_learned.restype = st
     for name in ("net_create", "net_num_params", "net_set_params", "net_get_params", "net_forward",
                  "net_loss_grad", "net_adam"):
         getattr(L, name).restype = st
@@ -276,6 +281,13 @@ def dwf_profile_read(ctx, kernel_class):
     return n.value, ms.value
 
 
+def dwf_profile_units(ctx, kernel_class):
+    """Fields processed by the recorded launches of one class (a batched launch counts its nrhs)."""
+    n = ctypes.c_longlong()
+    _check(_lib.dwf_profile_units(ctx, int(kernel_class), ctypes.byref(n)), "dwf_profile_units")
+    return n.value
+
+
 def dwf_launch_count():
     return int(_lib.dwf_launch_count())
 
@@ -350,4 +362,16 @@ def net_adam(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def net_destroy(net):
     _lib.net_destroy(net)
+
+
+def mg_setup_learned(ctx, net, seed, levels, nvec, block, params=None, fallback_iters0=1000, probe_tol=1e-4,
+                     probe_max_iters=0):
+    """mg_setup from the network's proposal; returns True when the plain setup was used as fallback."""
+    nv = (ctypes.c_int * (levels - 1))(*[int(v) for v in nvec])
+    bl = (ctypes.c_int * (4 * (levels - 1)))(*[int(b) for blk in block for b in blk])
+    p = ctypes.byref(params) if params is not None else None
+    used = ctypes.c_int(0)
+    _check(_lib.mg_setup_learned(ctx, net, int(seed), int(levels), nv, bl, p, int(fallback_iters0),
+                                 float(probe_tol), int(probe_max_iters), ctypes.byref(used)), "mg_setup_learned")
+    return bool(used.value)
 

