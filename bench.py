@@ -215,13 +215,16 @@ def profile_modes(args):
         torch.cuda.synchronize()
         print("dslash-only ok")
     else:
-        b = torch.empty(ctx.field_elems, dtype=torch.complex128, device="cuda")
-        G.dwf_pack(ctx.h, b, canon, G.DWF_F64, 1)
+        # one solve of args.nrhs right-hand sides (batched when nrhs > 1)
+        U, bs = gen_inputs(args.nrhs)
+        canon = torch.from_numpy(bs).cuda()
+        b = torch.empty(ctx.field_elems * args.nrhs, dtype=torch.complex128, device="cuda")
+        G.dwf_pack(ctx.h, b, canon, G.DWF_F64, args.nrhs)
         G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], mixed_params(G))
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        st = G.mg_solve(ctx.h, b, x, TOL, 1)
+        st = G.mg_solve(ctx.h, b, x, TOL, args.nrhs)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         print("profile-solve ok", st.iters, st.true_res)

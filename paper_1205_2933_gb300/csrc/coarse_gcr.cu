@@ -81,6 +81,9 @@ __device__ void apply_owned(const Args<R, LT> &a, C<R> *out, const C<R> *in, int
             xv[d] = on ? in[o * NV + lane] : mk<R>(0, 0);
         }
         const LT *Ys = a.Y + site * 9 * NV * NV;
+        // unrolled so that the link loads of several row pairs are in flight
+        // together (the loop is bound by L2 latency, not bandwidth)
+#pragma unroll 4
         for (int k = 0; k < NV; k += 2) {
             R r0 = 0, i0 = 0, r1 = 0, i1 = 0;
             if (on) {

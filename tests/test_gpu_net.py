@@ -166,3 +166,25 @@ def test_learned_setup_and_fallback(G):
         G.mg_setup_learned(ctx.h, net, 3, 2, [6], [(2, 2, 2, 2)], p)
     G.net_destroy(net)
     ctx.close()
+
+
+def test_trained_weights_beat_untrained(G):
+    """The committed network (trained on heatbath lattices 1000-1031 at 8^4,
+    Ls = 16) against its own initialisation on a held-out lattice (seed 1035):
+    the trained proposal is closer to the adaptive setup's subspace."""
+    import pathlib
+    from paper_1205_2933_gb300 import learned as Lm
+    path = pathlib.Path(Lm.__file__).parent / "weights" / "near_null_8x8x8x8_Ls16.npz"
+    shape, params, meta = Lm.load(path)
+    assert shape == Lm.SHAPE
+    ctx = Lm.lattice((8, 8, 8, 8), shape["Ls"], 1035)
+    nvec, block = 2 * shape["nout"], (4, 4, 4, 4)
+    q = Lm.adaptive_targets(ctx, nvec, block, Lm.solve_params())
+    trained = Lm.make_net(ctx, shape, params)
+    untrained = Lm.make_net(ctx, shape, Lm.init_params(shape, 77))
+    lt = np.mean([G.net_loss_grad(trained, ctx.h, q, nvec, block, seed=s) for s in (1, 2)])
+    lu = np.mean([G.net_loss_grad(untrained, ctx.h, q, nvec, block, seed=s) for s in (1, 2)])
+    assert lt < lu - 0.02, (lt, lu)
+    G.net_destroy(trained)
+    G.net_destroy(untrained)
+    ctx.close()
