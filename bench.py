@@ -50,7 +50,7 @@ FINE_BYTES_F32 = 204   # algorithmic bytes per 5D site of the FP32 Dslash
 # dram__bytes_read.sum + dram__bytes_write.sum of one one-field launch of the
 # current FP32 Dslash kernel from an ncu capture (profiles/); None until the
 # kernel as it stands has been captured
-DSLASH_TRAFFIC_PER_FIELD = None
+DSLASH_TRAFFIC_PER_FIELD = 411171840  # 239.68 MB read + 171.49 MB written (profiles/dslash_f32_pair_16x16x16x32_Ls16.md)
 FINE_BYTES_F64 = 408
 
 

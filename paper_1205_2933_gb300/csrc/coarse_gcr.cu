@@ -202,22 +202,40 @@ __global__ void __launch_bounds__(CT) coarse_gcr_kernel(Args<R, LT> a) {
                 for (int i = 0; i < k; ++i) v[i] = make_double2(0, 0);
                 for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) {
                     C<R> w = Wk[e];
-                    for (int i = 0; i < k; ++i) {
-                        C<R> u = a.W[(size_t)i * N + e];
-                        v[i].x += (double)u.x * w.x + (double)u.y * w.y;
-                        v[i].y += (double)u.x * w.y - (double)u.y * w.x;
+                    // loads issued eight at a time before the products (the loop is latency-bound)
+                    for (int i0 = 0; i0 < k; i0 += 8) {
+                        C<R> u[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (i0 + j < k) u[j] = a.W[(size_t)(i0 + j) * N + e];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (i0 + j < k) {
+                                v[i0 + j].x += (double)u[j].x * w.x + (double)u[j].y * w.y;
+                                v[i0 + j].y += (double)u[j].x * w.y - (double)u[j].y * w.x;
+                            }
                     }
                 }
                 reduce(v, k, P[pass]);
                 for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) {
                     C<R> w = Wk[e], z = Zk[e];
-                    for (int i = 0; i < k; ++i) {
-                        const R br = (R)tot[i].x, bi = (R)tot[i].y;
-                        C<R> wi = a.W[(size_t)i * N + e], zi = a.Z[(size_t)i * N + e];
-                        w.x -= br * wi.x - bi * wi.y;
-                        w.y -= br * wi.y + bi * wi.x;
-                        z.x -= br * zi.x - bi * zi.y;
-                        z.y -= br * zi.y + bi * zi.x;
+                    for (int i0 = 0; i0 < k; i0 += 8) {
+                        C<R> wi[8], zi[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (i0 + j < k) {
+                                wi[j] = a.W[(size_t)(i0 + j) * N + e];
+                                zi[j] = a.Z[(size_t)(i0 + j) * N + e];
+                            }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (i0 + j < k) {
+                                const R br = (R)tot[i0 + j].x, bi = (R)tot[i0 + j].y;
+                                w.x -= br * wi[j].x - bi * wi[j].y;
+                                w.y -= br * wi[j].y + bi * wi[j].x;
+                                z.x -= br * zi[j].x - bi * zi[j].y;
+                                z.y -= br * zi[j].y + bi * zi[j].x;
+                            }
                     }
                     Wk[e] = w;
                     Zk[e] = z;

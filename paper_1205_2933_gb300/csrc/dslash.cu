@@ -212,24 +212,40 @@ void dslash(dwf_ctx *c, double2 *out, const double2 *in, bool dag, int nrhs) {
 }
 
 bool dslash_pair_supported(int Ls);
-void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb);
+void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot,
+                     int nstride);
 
-void dslash(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs) {
-    ProfScope ps(c, K_DSLASH_F32, nrhs);
-    // two slices per thread with packed FP32x2 arithmetic where Ls allows;
-    // DWF_DSLASH_PAIR=0 selects the one-slice kernel
-    static const int pair_minb = [] {
+namespace {
+// two slices per thread with packed FP32x2 arithmetic where Ls allows;
+// DWF_DSLASH_PAIR=0 selects the one-slice kernel
+int pair_minb() {
+    static const int v = [] {
         const char *e = getenv("DWF_DSLASH_PAIR");
         if (e && atoi(e) == 0) return 0;
         const char *m = getenv("DWF_DSLASH_PAIR_MINB");
         return (m && atoi(m) == 5) ? 5 : 4;
     }();
-    if (pair_minb && dslash_pair_supported(c->g.Ls)) {
-        dslash_pair_f32(c, out, in, dag, nrhs, pair_minb);
+    return v;
+}
+}  // namespace
+
+void dslash(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs) {
+    ProfScope ps(c, K_DSLASH_F32, nrhs);
+    if (pair_minb() && dslash_pair_supported(c->g.Ls)) {
+        dslash_pair_f32(c, out, in, dag, nrhs, pair_minb(), nullptr, 0);
         c->applies32 += nrhs;
         return;
     }
     launch<float>(c, out, in, c->U32.as<float2>(), dag, nrhs);
+    c->applies32 += nrhs;
+}
+
+bool dslash_norm_fused(dwf_ctx *c) { return pair_minb() && dslash_pair_supported(c->g.Ls); }
+
+void dslash_norm(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int slot, int stride) {
+    DWF_REQUIRE(dslash_norm_fused(c), DWF_EINVAL, "fused Dslash norm needs the paired kernel");
+    ProfScope ps(c, K_DSLASH_F32, nrhs);
+    dslash_pair_f32(c, out, in, dag, nrhs, pair_minb(), c->scal.as<double>() + slot, stride);
     c->applies32 += nrhs;
 }
 

@@ -13,6 +13,7 @@
 // into (re, re, im, im) so that one 16-byte shared load gives both packed
 // operands.  The fifth-dimension neighbours come from the thread's own pair
 // and from the neighbouring lane (warp shuffles).
+#include <algorithm>
 #include <cstdint>
 
 #include "dwf_internal.cuh"
@@ -169,10 +170,15 @@ __device__ __forceinline__ void hop2(CP acc[12], const float2 *__restrict__ row,
 // wavefront instead of one per site.
 constexpr int LSTRIDE = 73;
 
-template <bool DAG, int LS, int MINB>
+// NORM: also |out_r|^2 of every right-hand side r = blockIdx.y into
+// nslot[r * nstride]: one partial per CTA (FP32 per thread, FP64 across the
+// CTA), and the last CTA of each right-hand side (atomic ticket) adds the
+// partials in a fixed order.
+template <bool DAG, int LS, int MINB, bool NORM>
 __global__ void __launch_bounds__(128, MINB)
 dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, const float2 *__restrict__ U, Geom g,
-                   float diag, float mf, int spb, int64_t field) {
+                   float diag, float mf, int spb, int64_t field, double *__restrict__ npart,
+                   unsigned *__restrict__ ncount, double *__restrict__ nslot, int nstride) {
     constexpr int TPS = LS / 2;  // threads per site
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *sL = reinterpret_cast<float4 *>(smem_raw);                 // [spb][LSTRIDE]
@@ -254,43 +260,102 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
         acc[dn_lo + q].re = add2(acc[dn_lo + q].re, pk(c_dn0 * pz, -sd.x));
         acc[dn_lo + q].im = add2(acc[dn_lo + q].im, pk(c_dn0 * pw, -sd.y));
     }
-    if (!active) return;
-    const float4 *sLs = sL + ls * LSTRIDE;
-    const int *sNs = sN + ls * 8;
-    const float fs = DAG ? 1.f : -1.f;  // sig of the forward hops
-    hop2<0, false, LS>(acc, in + (size_t)sNs[0] * row + s0, sLs + 0 * 9, fs);
-    hop2<0, true, LS>(acc, in + (size_t)sNs[4] * row + s0, sLs + 4 * 9, -fs);
-    hop2<1, false, LS>(acc, in + (size_t)sNs[1] * row + s0, sLs + 1 * 9, fs);
-    hop2<1, true, LS>(acc, in + (size_t)sNs[5] * row + s0, sLs + 5 * 9, -fs);
-    hop2<2, false, LS>(acc, in + (size_t)sNs[2] * row + s0, sLs + 2 * 9, fs);
-    hop2<2, true, LS>(acc, in + (size_t)sNs[6] * row + s0, sLs + 6 * 9, -fs);
-    hop2<3, false, LS>(acc, in + (size_t)sNs[3] * row + s0, sLs + 3 * 9, fs);
-    hop2<3, true, LS>(acc, in + (size_t)sNs[7] * row + s0, sLs + 7 * 9, -fs);
-    float2 *o = out + (size_t)site * row + s0;
+    if (!NORM && !active) return;
+    float nrm = 0.f;
+    if (!NORM || active) {
+        const float4 *sLs = sL + ls * LSTRIDE;
+        const int *sNs = sN + ls * 8;
+        const float fs = DAG ? 1.f : -1.f;  // sig of the forward hops
+        hop2<0, false, LS>(acc, in + (size_t)sNs[0] * row + s0, sLs + 0 * 9, fs);
+        hop2<0, true, LS>(acc, in + (size_t)sNs[4] * row + s0, sLs + 4 * 9, -fs);
+        hop2<1, false, LS>(acc, in + (size_t)sNs[1] * row + s0, sLs + 1 * 9, fs);
+        hop2<1, true, LS>(acc, in + (size_t)sNs[5] * row + s0, sLs + 5 * 9, -fs);
+        hop2<2, false, LS>(acc, in + (size_t)sNs[2] * row + s0, sLs + 2 * 9, fs);
+        hop2<2, true, LS>(acc, in + (size_t)sNs[6] * row + s0, sLs + 6 * 9, -fs);
+        hop2<3, false, LS>(acc, in + (size_t)sNs[3] * row + s0, sLs + 3 * 9, fs);
+        hop2<3, true, LS>(acc, in + (size_t)sNs[7] * row + s0, sLs + 7 * 9, -fs);
+        float2 *o = out + (size_t)site * row + s0;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const float2 re = unpk(acc[k].re), im = unpk(acc[k].im);
-        *reinterpret_cast<float4 *>(o + k * LS) = make_float4(re.x, im.x, re.y, im.y);
+        for (int k = 0; k < 12; ++k) {
+            const float2 re = unpk(acc[k].re), im = unpk(acc[k].im);
+            *reinterpret_cast<float4 *>(o + k * LS) = make_float4(re.x, im.x, re.y, im.y);
+            if (NORM) nrm += re.x * re.x + im.x * im.x + re.y * re.y + im.y * im.y;
+        }
+    }
+    if (NORM) {
+        __shared__ double wsum[4];
+        __shared__ bool last;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+        const int warp = threadIdx.x >> 5;
+        if (lane == 0) wsum[warp] = (double)nrm;
+        __syncthreads();
+        const int nw = (blockDim.x + 31) >> 5;
+        double *pr = npart + (size_t)blockIdx.y * gridDim.x;
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int w = 0; w < nw; ++w) t += wsum[w];
+            pr[blockIdx.x] = t;
+            __threadfence();
+            const unsigned ticket = atomicAdd(ncount + blockIdx.y, 1u);
+            last = (ticket == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            double t = 0;
+            for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += ((volatile double *)pr)[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) wsum[warp] = t;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double u = 0;
+                for (int w = 0; w < nw; ++w) u += wsum[w];
+                nslot[(size_t)blockIdx.y * nstride] = u;
+                ncount[blockIdx.y] = 0u;
+            }
+        }
     }
 }
 
 template <int LS>
-void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb) {
+void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot, int nstride) {
     const Geom &g = c->g;
     constexpr int TPS = LS / 2;
     int spb = 128 / TPS;
     const size_t per_site = LSTRIDE * sizeof(float4) + 8 * sizeof(int);
     const int max_spb = (int)((46 * 1024) / per_site);
     if (spb > max_spb) spb = max_spb;
+    // whole warps: the s-neighbour shuffles and the norm reduction use full masks
+    if (TPS < 32) spb = std::max(32 / TPS, spb / (32 / TPS) * (32 / TPS));
     const int threads = spb * TPS;
     dim3 grid((unsigned)((g.V + spb - 1) / spb), (unsigned)nrhs);
     size_t smem = (size_t)spb * per_site;
     int64_t field = g.V * g.Ls * 12;
     float diag = (float)(5.0 - c->M5), mf = (float)c->mf;
     const float2 *U = c->U32.as<float2>();
-#define PL(D, M) dslash_pair_kernel<D, LS, M><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, spb, field)
-    if (dag) { if (minb == 4) PL(true, 4); else PL(true, 5); }
-    else { if (minb == 4) PL(false, 4); else PL(false, 5); }
+    double *npart = nullptr;
+    unsigned *ncount = nullptr;
+    if (nslot) {
+        const size_t pb = sizeof(double) * (size_t)grid.x * nrhs;
+        if (c->dn_part.bytes < pb) c->dn_part.alloc(pb);
+        if (c->dn_count.bytes < sizeof(unsigned) * (size_t)nrhs) {
+            c->dn_count.alloc(sizeof(unsigned) * (size_t)std::max(nrhs, 32));
+            DWF_CUDA(cudaMemsetAsync(c->dn_count.p, 0, c->dn_count.bytes, c->stream));
+        }
+        npart = c->dn_part.as<double>();
+        ncount = c->dn_count.as<unsigned>();
+    }
+#define PL(D, M, NRM) dslash_pair_kernel<D, LS, M, NRM><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, spb, \
+                                                                                              field, npart, ncount, nslot, nstride)
+    if (nslot) {
+        if (dag) { if (minb == 4) PL(true, 4, true); else PL(true, 5, true); }
+        else { if (minb == 4) PL(false, 4, true); else PL(false, 5, true); }
+    } else {
+        if (dag) { if (minb == 4) PL(true, 4, false); else PL(true, 5, false); }
+        else { if (minb == 4) PL(false, 4, false); else PL(false, 5, false); }
+    }
 #undef PL
     DWF_CHECK_LAUNCH();
 }
@@ -300,13 +365,14 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
 // true when the paired FP32 kernel handles this fifth extent
 bool dslash_pair_supported(int Ls) { return Ls == 4 || Ls == 8 || Ls == 16 || Ls == 32 || Ls == 64; }
 
-void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb) {
+void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot,
+                     int nstride) {
     switch (c->g.Ls) {
-        case 4: launch_ls<4>(c, out, in, dag, nrhs, minb); break;
-        case 8: launch_ls<8>(c, out, in, dag, nrhs, minb); break;
-        case 16: launch_ls<16>(c, out, in, dag, nrhs, minb); break;
-        case 32: launch_ls<32>(c, out, in, dag, nrhs, minb); break;
-        case 64: launch_ls<64>(c, out, in, dag, nrhs, minb); break;
+        case 4: launch_ls<4>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
+        case 8: launch_ls<8>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
+        case 16: launch_ls<16>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
+        case 32: launch_ls<32>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
+        case 64: launch_ls<64>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
         default: throw Error{DWF_EINVAL, "paired Dslash needs Ls in {4, 8, 16, 32, 64}"};
     }
 }

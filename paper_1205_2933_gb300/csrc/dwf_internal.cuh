@@ -162,6 +162,8 @@ struct dwf_ctx {
     double *hscal = nullptr;
     // reduction partial sums + completion counter
     dwf::DevBuf red_part, red_count;
+    // partial sums and counters of the Dslash's fused output norms
+    dwf::DevBuf dn_part, dn_count;
     dwf::MGState *mg = nullptr;
     long long applies64 = 0, applies32 = 0;
     // event profiler
@@ -192,6 +194,10 @@ void pack_links(dwf_ctx *c, const double2 *U);  // fills U32 from U64
 // out = D in (or D^+) on nrhs fields, precision by pointer type
 void dslash(dwf_ctx *c, double2 *out, const double2 *in, bool dag, int nrhs);
 void dslash(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs);
+// FP32 D (or D^+) that also writes |out_r|^2 to the double slot slot + r*stride
+// (available when dslash_norm_fused(c))
+bool dslash_norm_fused(dwf_ctx *c);
+void dslash_norm(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int slot, int stride);
 
 // ---- blas.cu ---- (n = number of complex elements; slots index ctx->scal)
 template <typename T> void bzero(dwf_ctx *c, T *x, int64_t n);

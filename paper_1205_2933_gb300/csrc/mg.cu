@@ -119,17 +119,27 @@ template <typename R> class Runner {
             bnorm2<T>(c, S_RR, r, N);
             r0 = std::sqrt(read_scalar(c, S_RR));
         }
+        // on the fine level the FP32 Dslash produces the norms of its outputs
+        bool fused = false;
+        if constexpr (std::is_same<R, float>::value) fused = (l == 0) && dslash_norm_fused(c);
+        auto anorm = [&](T *out, const T *in, bool dag, int slot) {
+            if constexpr (std::is_same<R, float>::value)
+                if (fused) {
+                    dslash_norm(c, out, in, dag, 1, slot, 0);
+                    return;
+                }
+            apply(l, out, in, dag);
+            bnorm2<T>(c, slot, out, N);
+        };
         for (int it = 0; it < iters; ++it) {
-            apply(l, w, p, false);
-            bnorm2<T>(c, S_WW, w, N);
+            anorm(w, p, false, S_WW);
             cg_xr<T>(c, x, r, p, w, izz, S_WW, N);
             if (it + 1 == iters) break;
             if (rtol > 0.0 && (it + 1) % 8 == 0) {
                 bnorm2<T>(c, S_RR, r, N);
                 if (std::sqrt(read_scalar(c, S_RR)) <= rtol * r0) break;
             }
-            apply(l, z, r, true);
-            bnorm2<T>(c, inew, z, N);
+            anorm(z, r, true, inew);
             cg_p<T>(c, p, z, inew, izz, N);
             std::swap(izz, inew);
         }
@@ -582,13 +592,20 @@ template <typename R> class BatchRunner {
         int izz = 0, inew = 1;
         const int iww = 2;
         norm2_b<T>(c, mg.bscratch, SB + izz, SS, z, N, nr);
+        // the FP32 Dslash can produce the norms of its outputs in its epilogue
+        bool fused = false;
+        if constexpr (std::is_same<R, float>::value) fused = dslash_norm_fused(c);
+        auto dnorm = [&](T *out, const T *in, bool dag, int slot) {
+            if constexpr (std::is_same<R, float>::value)
+                if (fused) return dslash_norm(c, out, in, dag, nr, SB + slot, SS);
+            dslash(c, out, in, dag, nr);
+            norm2_b<T>(c, mg.bscratch, SB + slot, SS, out, N, nr);
+        };
         for (int it = 0; it < iters; ++it) {
-            dslash(c, w, p, false, nr);
-            norm2_b<T>(c, mg.bscratch, SB + iww, SS, w, N, nr);
+            dnorm(w, p, false, iww);
             cg_xr_b<T>(c, x, r, p, w, SB, SS, izz, iww, N, nr);
             if (it + 1 == iters) break;
-            dslash(c, z, r, true, nr);
-            norm2_b<T>(c, mg.bscratch, SB + inew, SS, z, N, nr);
+            dnorm(z, r, true, inew);
             cg_p_b<T>(c, p, z, SB, SS, inew, izz, N, nr);
             std::swap(izz, inew);
         }
@@ -602,9 +619,37 @@ template <typename R> class BatchRunner {
     cudaEvent_t ev_fork = nullptr, ev_join[NS] = {nullptr, nullptr, nullptr};
     DevBuf cs_r[NS], cs_Z[NS], cs_W[NS], cs_part[NS];
 
+    DevBuf cb_r, cb_Z, cb_W, cb_part;  // scratch of the batched coarsest solver
+
     void coarse_solves(T *x2, const T *b2, int64_t Nc) {
         Level &Lc = mg.lev[1];
         const mg_params &p = mg.p;
+        static const bool batched = [] {
+            const char *e = getenv("DWF_COARSE_BATCH");
+            return !(e && atoi(e) == 0);
+        }();
+        if (batched && coarse_gcr_batch_ok(Lc, p.coarse_restart, std::min(nr, 16))) {
+            // all right-hand sides through one cooperative launch (16 at a time)
+            const int w = std::min(nr, 16);
+            const size_t vb = sizeof(T) * (size_t)Nc * w;
+            if (cb_r.bytes < vb) {
+                cb_r.alloc(vb);
+                cb_Z.alloc(vb * p.coarse_restart);
+                cb_W.alloc(vb * p.coarse_restart);
+            }
+            if (!cb_part.p) cb_part.alloc(coarse_gcr_batch_part_bytes(c));
+            if (!Lc.cgIters.p) {
+                Lc.cgIters.alloc(sizeof(int));
+                DWF_CUDA(cudaMemsetAsync(Lc.cgIters.p, 0, sizeof(int), c->stream));
+            }
+            for (int r0 = 0; r0 < nr; r0 += w) {
+                const int nb = std::min(w, nr - r0);
+                coarse_gcr_fused_batch<R>(c, Lc, x2 + (size_t)r0 * Nc, b2 + (size_t)r0 * Nc, nb, cb_r.as<T>(),
+                                          cb_Z.as<T>(), cb_W.as<T>(), cb_part.as<double2>(), Lc.cgIters.as<int>(),
+                                          p.coarsest_tol, p.coarsest_maxiter, p.coarse_restart);
+            }
+            return;
+        }
         if (!coarse_gcr_fused_ok(Lc, p.coarse_restart)) {
             for (int r = 0; r < nr; ++r) one.coarse_solve(1, x2 + (size_t)r * Nc, b2 + (size_t)r * Nc);
             return;

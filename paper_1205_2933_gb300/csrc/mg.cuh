@@ -107,6 +107,12 @@ void convert_coarse_links(dwf_ctx *c, Level &L);
 
 // ---- coarse_gcr.cu ----  fused coarsest-level GCR (one cooperative launch)
 bool coarse_gcr_fused_ok(const Level &L, int restart);
+// ---- coarse_gcr_batch.cu ---- the same solve for nb <= 16 right-hand sides in lockstep
+bool coarse_gcr_batch_ok(const Level &L, int restart, int nb);
+size_t coarse_gcr_batch_part_bytes(dwf_ctx *c);
+template <typename R>
+void coarse_gcr_fused_batch(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, int nb, C<R> *r, C<R> *Z, C<R> *W,
+                            double2 *part, int *iters, double tol, int maxiter, int restart);
 size_t coarse_gcr_part_bytes(dwf_ctx *c);
 template <typename R>
 void coarse_gcr_fused(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, C<R> *r, C<R> *Z, C<R> *W, double2 *part,

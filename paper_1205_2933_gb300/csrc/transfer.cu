@@ -38,6 +38,21 @@ __device__ __forceinline__ int64_t block_elem_addr(const BlockMap &m, int64_t xc
     return site * m.run + rem;
 }
 
+// element address of the first element of the i-th finer site of block xc
+__device__ __forceinline__ int64_t block_site_addr(const BlockMap &m, int64_t xc, int64_t i) {
+    int c[4], o[4];
+    int64_t t = xc;
+    c[0] = (int)(t % m.Lc[0]); t /= m.Lc[0];
+    c[1] = (int)(t % m.Lc[1]); t /= m.Lc[1];
+    c[2] = (int)(t % m.Lc[2]); c[3] = (int)(t / m.Lc[2]);
+    o[0] = (int)(i % m.b[0]); i /= m.b[0];
+    o[1] = (int)(i % m.b[1]); i /= m.b[1];
+    o[2] = (int)(i % m.b[2]); o[3] = (int)(i / m.b[2]);
+    int64_t site = (((int64_t)(c[3] * m.b[3] + o[3]) * m.L[2] + (c[2] * m.b[2] + o[2])) * m.L[1] +
+                    (c[1] * m.b[1] + o[1])) * m.L[0] + (c[0] * m.b[0] + o[0]);
+    return site * m.run;
+}
+
 BlockMap make_map(const Level &L) {
     BlockMap m;
     for (int i = 0; i < 4; ++i) {
@@ -321,7 +336,7 @@ namespace {
 // every basis value is read once and each field value is read by the 8
 // warps of the CTA (L1).  Lane partial sums are reduced with shuffles.
 template <typename R, int NV, int NB>
-__global__ void __launch_bounds__(TT) restrict_b_kernel(C<R> *__restrict__ cout, const C<R> *__restrict__ f,
+__global__ void __launch_bounds__(TT, 2) restrict_b_kernel(C<R> *__restrict__ cout, const C<R> *__restrict__ f,
                                                         const C<R> *__restrict__ Q, BlockMap m, int nrhs, int r0,
                                                         int64_t cstride) {
     constexpr int NW = TT / 32;
@@ -329,24 +344,29 @@ __global__ void __launch_bounds__(TT) restrict_b_kernel(C<R> *__restrict__ cout,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = warp * KG;
     const int64_t xc = blockIdx.x;
-    const int64_t ne = m.bsites * m.run;
     C<R> acc[KG][NB];
 #pragma unroll
     for (int a = 0; a < KG; ++a)
 #pragma unroll
         for (int r = 0; r < NB; ++r) acc[a][r] = mk<R>(0, 0);
     const int nrb = nrhs - r0 < NB ? nrhs - r0 : NB;
-    for (int64_t e = lane; e < ne; e += 32) {
-        const int64_t ad = block_elem_addr(m, xc, e);
-        C<R> fv[NB];
+    // walk the block site by site (one address computation per site); the
+    // lanes stream over the site's contiguous run of components x s
+    for (int64_t i = 0; i < m.bsites; ++i) {
+        const int64_t sa = block_site_addr(m, xc, i);
+#pragma unroll 1
+        for (int j = lane; j < m.run; j += 32) {
+            const int64_t ad = sa + j;
+            C<R> fv[NB];
 #pragma unroll
-        for (int r = 0; r < NB; ++r) fv[r] = r < nrb ? f[(int64_t)(r0 + r) * m.nelem + ad] : mk<R>(0, 0);
+            for (int r = 0; r < NB; ++r) fv[r] = r < nrb ? f[(int64_t)(r0 + r) * m.nelem + ad] : mk<R>(0, 0);
 #pragma unroll
-        for (int a = 0; a < KG; ++a) {
-            if (k0 + a < NV) {
-                const C<R> q = Q[(k0 + a) * m.nelem + ad];
+            for (int a = 0; a < KG; ++a) {
+                if (k0 + a < NV) {
+                    const C<R> q = Q[(k0 + a) * m.nelem + ad];
 #pragma unroll
-                for (int r = 0; r < NB; ++r) cfmac(acc[a][r], q, fv[r]);
+                    for (int r = 0; r < NB; ++r) cfmac(acc[a][r], q, fv[r]);
+                }
             }
         }
     }
