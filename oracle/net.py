@@ -45,6 +45,11 @@ Shapes
   Hd     (nout, Ls, 4, C, 4)
   v      (nout, Ls, T, Z, Y, X, 12)     fine fields in the oracle layout
 
+Refinement mode (forward_refine): the network maps each given fine field
+v_b (its fifth dimension folded into c_in = Ls channels) to
+v_b + head(h_L) (nout = 1, a skip connection), for improving vectors that
+a short relaxation produced.
+
 Parity pins (tests/test_oracle_net.py): adjointness of the transports
 (T_{+mu}^+ = T_{-mu}), gauge covariance of the forward pass and gauge
 invariance of the loss, central finite differences of every parameter
@@ -268,6 +273,44 @@ def loss_and_grad(s: NetShape, params, U, h0, targets, dims, block):
     v, cache = forward(s, params, U, h0, dims)
     L, gv = projection_loss(v, targets, dims, block, grad=True)
     return L, backward(s, params, U, cache, gv, dims)
+
+
+# ---------------------------------------------------------------------------
+# refinement mode: the network improves given vectors instead of drawing them
+# ---------------------------------------------------------------------------
+
+def fields_to_input(v, dims):
+    """Fine fields (B, Ls, T, Z, Y, X, 12) -> B network inputs with the fifth
+    dimension as channels: (B, Ls, 4, T, Z, Y, X, 3)."""
+    X, Y, Z, T = dims
+    B, Ls = v.shape[0], v.shape[1]
+    v8 = v.reshape(B, Ls, T, Z, Y, X, 4, 3)
+    return np.ascontiguousarray(np.transpose(v8, (0, 1, 6, 2, 3, 4, 5, 7)))
+
+
+def forward_refine(s: NetShape, params, U, v, dims):
+    """out_b = v_b + net(v_b): c_in = Ls channels (one per s), nout = 1, and
+    a skip connection, so that zero head weights give out = v exactly."""
+    assert s.c_in == s.Ls and s.nout == 1
+    h0s = fields_to_input(v, dims)
+    outs, caches = [], []
+    for b in range(v.shape[0]):
+        o, cache = forward(s, params, U, h0s[b], dims)
+        outs.append(v[b] + o[0])
+        caches.append(cache)
+    return np.array(outs), caches
+
+
+def loss_and_grad_refine(s: NetShape, params, U, v, targets, dims, block):
+    """Projection loss of the refined fields and the parameter gradients
+    (summed over the batch; the skip connection holds no parameters)."""
+    out, caches = forward_refine(s, params, U, v, dims)
+    L, gout = projection_loss(out, targets, dims, block, grad=True)
+    grads = None
+    for b, cache in enumerate(caches):
+        gb = backward(s, params, U, cache, gout[b:b + 1], dims)
+        grads = gb if grads is None else [x + y for x, y in zip(grads, gb)]
+    return L, grads
 
 
 def gauge_transform_field(g, h):

@@ -148,3 +148,47 @@ def test_finite_differences_input_gate_path():
     eps = 1e-6
     fd = (f(a + eps * d) - f(a - eps * d)) / (2 * eps)
     assert abs(fd - 2 * np.real(_vdot(g, d))) < 1e-6 * abs(fd)
+
+
+RSHAPE = N.NetShape(c_in=4, hidden=3, layers=2, nout=1, Ls=4)
+
+
+def test_refine_identity_and_covariance():
+    """Zero head weights give back the input fields exactly; the refined fields
+    transform like fermions under a gauge transform of links and inputs."""
+    U = I.epsilon_links(DIMS, 0.4, 80)
+    X, Y, Z, T = DIMS
+    v = _targets(2, DIMS, RSHAPE.Ls, 81)
+    p = _params(RSHAPE, 82)
+    p0 = [x.copy() for x in p]
+    p0[-1][:] = 0
+    out, _ = N.forward_refine(RSHAPE, p0, U, v, DIMS)
+    assert np.array_equal(out, v)
+    g = I.random_gauge_transform(DIMS, 83)
+    def gf(f):
+        f6 = f.reshape(f.shape[:6] + (4, 3))
+        return np.einsum("tzyxab,jstzyxcb->jstzyxca", g, f6).reshape(f.shape)
+    out, _ = N.forward_refine(RSHAPE, p, U, v, DIMS)
+    outg, _ = N.forward_refine(RSHAPE, p, N.gauge_transform_links(g, U), gf(v), DIMS)
+    assert np.abs(outg - gf(out)).max() < 1e-12 * np.abs(out).max()
+
+
+@pytest.mark.parametrize("group", [0, 2])
+def test_refine_finite_differences(group):
+    U = I.epsilon_links(DIMS, 0.4, 90)
+    p = _params(RSHAPE, 91)
+    v = _targets(2, DIMS, RSHAPE.Ls, 92)
+    q = _targets(3, DIMS, RSHAPE.Ls, 93)
+    L, grads = N.loss_and_grad_refine(RSHAPE, p, U, v, q, DIMS, BLOCK)
+    dirn = I.gauss_complex(p[group].shape, 94 + group, I.STREAM_NETWORK)
+    eps = 1e-5
+
+    def loss_at(e):
+        pp = [x.copy() for x in p]
+        pp[group] = p[group] + e * dirn
+        out, _ = N.forward_refine(RSHAPE, pp, U, v, DIMS)
+        return N.projection_loss(out, q, DIMS, BLOCK)
+
+    fd = (loss_at(eps) - loss_at(-eps)) / (2 * eps)
+    an = 2.0 * np.real(_vdot(grads[group], dirn))
+    assert abs(fd - an) < 1e-6 * max(abs(an), 1e-3), (fd, an)
