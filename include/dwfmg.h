@@ -226,6 +226,12 @@ dwf_status mg_coarse_solve_static(dwf_ctx *ctx, int level, void *x_dev, const vo
  * precision; x and b are FP64.  Synchronous. */
 dwf_status mg_vcycle(dwf_ctx *ctx, void *x_dev, const void *b_dev);
 
+/* The adaptive vectors a finished setup built level `level` from (Nvec/2
+ * with split, else Nvec fields of that level), globally orthonormal, before
+ * the Gamma split and block orthonormalisation: complex128, internal
+ * layout, device.  Synchronous. */
+dwf_status mg_get_adaptive_vectors(dwf_ctx *ctx, int level, void *out_dev);
+
 /* The V-cycle of mg_vcycle (Sec. 2) for nrhs right-hand sides stored one
  * after another (nrhs fine FP64 fields each for x and b).  With an FP32
  * V-cycle on two levels and nu_1 = 0 the right-hand sides go through the

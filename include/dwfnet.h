@@ -92,10 +92,25 @@ dwf_status net_adam(dwf_net *net, double lr, double beta1, double beta2, double 
 
 void net_destroy(dwf_net *net);
 
-/* The learned setup: mg_setup (dwfmg.h) started from the network's proposal
- * for the links of ctx (net_forward with input NULL and this seed), which
- * opt->setup_iters0 relaxation iterations then refine.  nout of the network
- * must be nvec[0]/2 (opt->split = 1) or nvec[0].
+/* Refinement mode: a network with c_in = Ls and nout = 1 improves given
+ * fields instead of drawing them.  Field v_b enters with its fifth dimension
+ * as the c_in channels (h_0[s][spin](x, colour) = v_b(x, s, spin, colour)) and
+ * leaves as v_b + head(h_L) (a skip connection: zero head weights return the
+ * input).  in_dev: nfields complex128 fine fields, internal layout, device
+ * (e.g. mg_get_adaptive_vectors after a short setup); out_dev: nfields
+ * complex128 fields, canonical layout, device. */
+dwf_status net_refine(dwf_net *net, dwf_ctx *ctx, const void *in_dev, int nfields, void *out_dev);
+
+/* The projection loss of net_refine's outputs (as net_loss_grad). */
+dwf_status net_refine_loss_grad(dwf_net *net, dwf_ctx *ctx, const void *in_dev, int nfields, const void *targets_dev,
+                                int nt, const int block[4], double *loss, void *grad);
+
+/* The learned setup: mg_setup (dwfmg.h) started from the network's vectors,
+ * which opt->setup_iters0 relaxation iterations then refine.  A proposal
+ * network (nout = nvec[0]/2 with opt->split = 1, else nvec[0]) draws them
+ * (net_forward with input NULL and this seed); a refinement network
+ * (net_refine) improves the vectors of a first setup that relaxes random
+ * vectors for pre_iters0 iterations.
  * Fallback to the plain adaptive setup: when probe_max_iters > 0, a probe
  * solve (a Gaussian source from Philox-4x32-10 with key (seed, 3), x = 0)
  * runs to the relative residual probe_tol; if it needs more than
@@ -103,8 +118,8 @@ void net_destroy(dwf_net *net);
  * vectors with setup_iters0 = fallback_iters0, and *used_fallback (if not
  * NULL) is set to 1 (else 0).  Synchronous. */
 dwf_status mg_setup_learned(dwf_ctx *ctx, dwf_net *net, unsigned int seed, int levels, const int *nvec,
-                            const int (*block)[4], const mg_params *opt, int fallback_iters0, double probe_tol,
-                            int probe_max_iters, int *used_fallback);
+                            const int (*block)[4], const mg_params *opt, int pre_iters0, int fallback_iters0,
+                            double probe_tol, int probe_max_iters, int *used_fallback);
 
 #ifdef __cplusplus
 }

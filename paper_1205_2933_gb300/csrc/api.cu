@@ -240,6 +240,14 @@ dwf_status mg_vcycle(dwf_ctx *c, void *x, const void *b) {
     return guarded(c, [&]() -> dwf_status { dwf::mg_vcycle_impl(c, (double2 *)x, (const double2 *)b, 1); return DWF_OK; });
 }
 
+dwf_status mg_get_adaptive_vectors(dwf_ctx *c, int level, void *out_dev) {
+    if (!c || !out_dev || level < 0) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        dwf::mg_get_adaptive_impl(c, level, (double2 *)out_dev);
+        return DWF_OK;
+    });
+}
+
 dwf_status mg_vcycle_batch(dwf_ctx *c, void *x, const void *b, int nrhs) {
     if (!c || !x || !b || x == b || nrhs < 1) return DWF_EINVAL;
     return guarded(c, [&]() -> dwf_status {
@@ -353,22 +361,58 @@ void net_destroy(dwf_net *net) {
     if (net) dwf::net_free(net);
 }
 
+dwf_status net_refine(dwf_net *net, dwf_ctx *c, const void *in_dev, int nfields, void *out_dev) {
+    if (!net || !c || !in_dev || !out_dev || nfields < 1) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        dwf::net_refine_impl(net, c, (const double2 *)in_dev, nfields, (double2 *)out_dev);
+        return DWF_OK;
+    });
+}
+
+dwf_status net_refine_loss_grad(dwf_net *net, dwf_ctx *c, const void *in_dev, int nfields, const void *targets,
+                                int nt, const int block[4], double *loss, void *grad) {
+    if (!net || !c || !in_dev || !targets || !block || !loss || nfields < 1 || nt < 1) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        *loss = dwf::net_refine_loss_grad_impl(net, c, (const double2 *)in_dev, nfields, (const double2 *)targets, nt,
+                                               block, grad, grad && is_device_ptr(grad));
+        return DWF_OK;
+    });
+}
+
 dwf_status mg_setup_learned(dwf_ctx *c, dwf_net *net, unsigned int seed, int levels, const int *nvec,
-                            const int (*block)[4], const mg_params *opt, int fallback_iters0, double probe_tol,
-                            int probe_max_iters, int *used_fallback) {
-    if (!c || !net || !nvec || !block || levels < 2) return DWF_EINVAL;
+                            const int (*block)[4], const mg_params *opt, int pre_iters0, int fallback_iters0,
+                            double probe_tol, int probe_max_iters, int *used_fallback) {
+    if (!c || !net || !nvec || !block || levels < 2 || pre_iters0 < 0) return DWF_EINVAL;
     if (used_fallback) *used_fallback = 0;
     mg_params p;
     if (opt) p = *opt;
     else mg_default_params(&p);
-    const int nout = dwf::net_nout(net);
-    if (nout != (p.split ? nvec[0] / 2 : nvec[0])) return DWF_EINVAL;
-    dwf::DevBuf start;
-    dwf_status s = guarded(c, [&]() -> dwf_status {
-        start.alloc(sizeof(double2) * (size_t)nout * c->g.V * 12 * c->g.Ls);
-        dwf::net_forward_impl(net, c, nullptr, false, seed, start.as<double2>());
+    const int nad = p.split ? nvec[0] / 2 : nvec[0];
+    const bool refiner = dwf::net_is_refiner(net);
+    if (!refiner && dwf::net_nout(net) != nad) return DWF_EINVAL;
+    dwf::DevBuf start, pre;
+    dwf_status s = DWF_OK;
+    if (refiner) {
+        // a short relaxation from random vectors, then the network refines them
+        mg_params p0 = p;
+        p0.setup_iters0 = pre_iters0;
+        p0.setup_sweeps = 0;
+        s = mg_setup(c, levels, nvec, block, &p0, nullptr);
+        if (s != DWF_OK) return s;
+    }
+    s = guarded(c, [&]() -> dwf_status {
+        const size_t fb = sizeof(double2) * (size_t)nad * c->g.V * 12 * c->g.Ls;
+        start.alloc(fb);
+        if (refiner) {
+            pre.alloc(fb);
+            dwf::mg_get_adaptive_impl(c, 0, pre.as<double2>());
+            dwf::net_refine_impl(net, c, pre.as<double2>(), nad, start.as<double2>());
+        } else {
+            dwf::net_forward_impl(net, c, nullptr, false, seed, start.as<double2>());
+        }
         return DWF_OK;
     });
+    pre.release();
     if (s != DWF_OK) return s;
     s = mg_setup(c, levels, nvec, block, &p, start.p);
     start.release();

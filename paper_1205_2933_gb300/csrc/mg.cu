@@ -1213,6 +1213,14 @@ void mg_coarse_solve_impl(dwf_ctx *c, int level, void *x, const void *b) {
     else coarse_solve_t<double>(c, mg, level, x, b);
 }
 
+void mg_get_adaptive_impl(dwf_ctx *c, int level, double2 *out) {
+    MGState &mg = need_mg(c, level, 0, mg_nlevels_minus1(c));
+    const Level &L = mg.lev[level];
+    DWF_CUDA(cudaMemcpyAsync(out, L.vec64.p, sizeof(double2) * (size_t)L.lg.nelem * L.nadapt, cudaMemcpyDeviceToDevice,
+                             c->stream));
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
 void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b, int nrhs) {
     MGState &mg = need_mg(c, 0, 0, 1);
     if (mg.p.smoother_prec == DWF_F32) vcycle_t<float>(c, mg, x, b, nrhs);

@@ -73,6 +73,7 @@ void mg_restrict_impl(dwf_ctx *c, int level, double2 *cout, const double2 *fin);
 void mg_prolong_impl(dwf_ctx *c, int level, double2 *fout, const double2 *cin);
 void mg_coarse_apply_impl(dwf_ctx *c, int level, void *out, const void *in, bool dag, dwf_prec prec);
 void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b, int nrhs);
+void mg_get_adaptive_impl(dwf_ctx *c, int level, double2 *out);
 void mg_coarse_solve_impl(dwf_ctx *c, int level, void *x, const void *b);
 void mg_coarse_solve_static_impl(dwf_ctx *c, int level, void *x, const void *b);
 
@@ -155,6 +156,10 @@ void net_forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_de
 double net_loss_grad_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed,
                           const double2 *targets, int nt, const int block[4], void *grad, bool grad_dev);
 void net_adam_impl(dwf_net *net, double lr, double b1, double b2, double eps);
+void net_refine_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B, double2 *out);
+double net_refine_loss_grad_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B, const double2 *targets, int nt,
+                                 const int block[4], void *grad, bool grad_dev);
+bool net_is_refiner(const dwf_net *net);
 long long net_nparams(const dwf_net *net);
 int net_nout(const dwf_net *net);
 void net_free(dwf_net *net);

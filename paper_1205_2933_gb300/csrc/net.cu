@@ -27,8 +27,10 @@ struct dwf_net {
     dwf::DevBuf P, G, M1, M2;  // parameters, gradient, Adam moments (FP32 complex)
     int adam_t = 0;
     bool have_grad = false;
-    // workspaces for one lattice volume
+    // workspaces for one lattice volume and batch (B fields side by side in
+    // the columns: column (b*V + site)*3 + colour)
     int64_t V = -1;
+    int B = 0;
     std::vector<dwf::DevBuf> h, a, S;
     dwf::DevBuf vh, v, F, R, gvh, gh, ga, yt, gws, gpart, gram, Y, info, lpart, lval, in64;
 };
@@ -137,16 +139,16 @@ __device__ __forceinline__ int64_t shifted(const Geom &g, const int co[4], int m
 }
 
 __global__ void transport_kernel(float2 *__restrict__ S, const float2 *__restrict__ h, const double2 *__restrict__ U,
-                                 Geom g, int nrow) {
-    const int64_t V = g.V, plane = (int64_t)nrow * V * 3;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrow * V;
+                                 Geom g, int nrow, int B) {
+    const int64_t V = g.V, cols = (int64_t)B * V * 3, plane = (int64_t)nrow * cols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nrow * B * V;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t / V);
-        const int64_t x = t - (int64_t)i * V;
+        const int64_t i = t / (B * V), xb = t - i * B * V;
+        const int64_t b = xb / V, x = xb - b * V;
         int co[4];
         site_coords(g, x, co);
-        const float2 *hi = h + (int64_t)i * V * 3;
-        float2 *So = S + (int64_t)i * V * 3 + x * 3;
+        const float2 *hi = h + i * cols + b * V * 3;
+        float2 *So = S + i * cols + xb * 3;
 #pragma unroll
         for (int c = 0; c < 3; ++c) So[c] = hi[x * 3 + c];
         for (int mu = 0; mu < 4; ++mu) {
@@ -155,14 +157,14 @@ __global__ void transport_kernel(float2 *__restrict__ S, const float2 *__restric
             const double2 *um = U + (xm * 4 + mu) * 9; // U_mu(x - mu)
             float2 hp[3], hm[3];
 #pragma unroll
-            for (int b = 0; b < 3; ++b) { hp[b] = hi[xp * 3 + b]; hm[b] = hi[xm * 3 + b]; }
+            for (int bb = 0; bb < 3; ++bb) { hp[bb] = hi[xp * 3 + bb]; hm[bb] = hi[xm * 3 + bb]; }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float2 sp = make_float2(0.f, 0.f), sm = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    cfma(sp, cvt<float2, double2>(u[a * 3 + b]), hp[b]);    // U(x)[a][b] h(x+mu)[b]
-                    cfmac(sm, cvt<float2, double2>(um[b * 3 + a]), hm[b]);  // conj(U(x-mu)[b][a]) h(x-mu)[b]
+                for (int bb = 0; bb < 3; ++bb) {
+                    cfma(sp, cvt<float2, double2>(u[a * 3 + bb]), hp[bb]);    // U(x)[a][b] h(x+mu)[b]
+                    cfmac(sm, cvt<float2, double2>(um[bb * 3 + a]), hm[bb]);  // conj(U(x-mu)[b][a]) h(x-mu)[b]
                 }
                 So[(1 + 2 * mu) * plane + a] = sp;
                 So[(2 + 2 * mu) * plane + a] = sm;
@@ -174,15 +176,15 @@ __global__ void transport_kernel(float2 *__restrict__ S, const float2 *__restric
 // gh[i][x] = sum_d (T_d^+ Y_d)(x):  T_{+mu}^+ y(x) = U_mu(x-mu)^+ y(x-mu),
 // T_{-mu}^+ y(x) = U_mu(x) y(x+mu)
 __global__ void transport_adj_kernel(float2 *__restrict__ gh, const float2 *__restrict__ Y,
-                                     const double2 *__restrict__ U, Geom g, int nrow) {
-    const int64_t V = g.V, plane = (int64_t)nrow * V * 3;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrow * V;
+                                     const double2 *__restrict__ U, Geom g, int nrow, int B) {
+    const int64_t V = g.V, cols = (int64_t)B * V * 3, plane = (int64_t)nrow * cols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nrow * B * V;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t / V);
-        const int64_t x = t - (int64_t)i * V;
+        const int64_t i = t / (B * V), xb = t - i * B * V;
+        const int64_t b = xb / V, x = xb - b * V;
         int co[4];
         site_coords(g, x, co);
-        const float2 *Yi = Y + (int64_t)i * V * 3;
+        const float2 *Yi = Y + i * cols + b * V * 3;
         float2 acc[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[c] = Yi[x * 3 + c];
@@ -194,13 +196,13 @@ __global__ void transport_adj_kernel(float2 *__restrict__ gh, const float2 *__re
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    cfmac(acc[a], cvt<float2, double2>(um[b * 3 + a]), Yp[xm * 3 + b]);
-                    cfma(acc[a], cvt<float2, double2>(u[a * 3 + b]), Ym[xp * 3 + b]);
+                for (int bb = 0; bb < 3; ++bb) {
+                    cfmac(acc[a], cvt<float2, double2>(um[bb * 3 + a]), Yp[xm * 3 + bb]);
+                    cfma(acc[a], cvt<float2, double2>(u[a * 3 + bb]), Ym[xp * 3 + bb]);
                 }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) gh[(int64_t)i * V * 3 + x * 3 + c] = acc[c];
+        for (int c = 0; c < 3; ++c) gh[i * cols + xb * 3 + c] = acc[c];
     }
 }
 
@@ -240,18 +242,42 @@ __global__ void gate_bwd_kernel(float2 *__restrict__ ga, const float2 *__restric
 // ---------------------------------------------------------------------------
 // head layout [(j*Ls + s)*4 + spin][x*3 + c]  <->  internal fine fields
 // ---------------------------------------------------------------------------
-// dir = 0: v <- vh;  dir = 1: vh <- v
+// Output field f = j*B + b (output j of batch member b):
+// dir = 0: v_f <- vh;  dir = 1: vh <- v_f
 __global__ void head_to_internal_kernel(float2 *__restrict__ v, float2 *__restrict__ vh, int nout, int Ls,
-                                        int64_t V, int dir) {
-    const int64_t nelem = V * 12 * Ls, total = nelem * nout;
+                                        int64_t V, int B, int dir) {
+    const int64_t nelem = V * 12 * Ls, total = nelem * nout * B, cols = (int64_t)B * V * 3;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = t / nelem, e = t - j * nelem;
+        const int64_t f = t / nelem, e = t - f * nelem;
+        const int64_t j = f / B, b = f - j * B;
         const int s = (int)(e % Ls);
         const int64_t sc = e / Ls, x = sc / 12;
         const int comp = (int)(sc - x * 12);
-        const int64_t hidx = ((j * Ls + s) * 4 + comp / 3) * (V * 3) + x * 3 + comp % 3;
+        const int64_t hidx = ((j * Ls + s) * 4 + comp / 3) * cols + (b * V + x) * 3 + comp % 3;
         if (dir == 0) v[t] = vh[hidx];
         else vh[hidx] = v[t];
+    }
+}
+
+// refinement input: h0[(s*4 + spin)][(b*V + x)*3 + c] = v_b[(x*12 + spin*3 + c)*Ls + s]
+__global__ void fields_to_input_kernel(float2 *__restrict__ h0, const double2 *__restrict__ v, int Ls, int64_t V,
+                                       int B) {
+    const int64_t nelem = V * 12 * Ls, cols = (int64_t)B * V * 3;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nelem * B; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = t / nelem, e = t - b * nelem;
+        const int s = (int)(e % Ls);
+        const int64_t sc = e / Ls, x = sc / 12;
+        const int comp = (int)(sc - x * 12);
+        h0[((int64_t)s * 4 + comp / 3) * cols + (b * V + x) * 3 + comp % 3] = cvt<float2, double2>(v[t]);
+    }
+}
+
+// out += in (FP32 += FP64): the skip connection of the refinement
+__global__ void add_skip_kernel(float2 *__restrict__ out, const double2 *__restrict__ in, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 a = out[i];
+        const double2 b = in[i];
+        out[i] = make_float2((float)((double)a.x + b.x), (float)((double)a.y + b.y));
     }
 }
 
@@ -559,13 +585,13 @@ void gemm(dwf_net *net, dwf_ctx *c, float2 *C, const float2 *A, const float2 *B,
     DWF_CHECK_LAUNCH();
 }
 
-void ensure_ws(dwf_net *net, dwf_ctx *c) {
+void ensure_ws(dwf_net *net, dwf_ctx *c, int B) {
     DWF_REQUIRE(c->g.Ls == net->sh.Ls, DWF_EINVAL, "the network's Ls differs from the context's");
     int dev = 0;
     DWF_CUDA(cudaGetDevice(&dev));
     DWF_REQUIRE(dev == net->device, DWF_EINVAL, "the network lives on another device");
-    if (net->V == c->g.V) return;
-    const int64_t V3 = c->g.V * 3;
+    if (net->V == c->g.V && net->B == B) return;
+    const int64_t X3 = c->g.V * 3 * B;
     const int L = net->sh.layers, C4 = 4 * net->sh.hidden;
     net->h.clear();
     net->a.clear();
@@ -573,23 +599,51 @@ void ensure_ws(dwf_net *net, dwf_ctx *c) {
     net->h.resize(L + 1);
     net->a.resize(L);
     net->S.resize(L);
-    for (int l = 0; l <= L; ++l) net->h[l].alloc(sizeof(float2) * (l == 0 ? cin4(net, 0) : C4) * V3);
+    for (int l = 0; l <= L; ++l) net->h[l].alloc(sizeof(float2) * (l == 0 ? cin4(net, 0) : C4) * X3);
     for (int l = 0; l < L; ++l) {
-        net->a[l].alloc(sizeof(float2) * C4 * V3);
-        net->S[l].alloc(sizeof(float2) * 9 * cin4(net, l) * V3);
+        net->a[l].alloc(sizeof(float2) * C4 * X3);
+        net->S[l].alloc(sizeof(float2) * 9 * cin4(net, l) * X3);
     }
     const int64_t nhead = (int64_t)net->sh.nout * net->sh.Ls * 4;
-    net->vh.alloc(sizeof(float2) * nhead * V3);
-    net->v.alloc(sizeof(float2) * nhead * V3);  // nout internal fields
+    net->vh.alloc(sizeof(float2) * nhead * X3);
+    net->v.alloc(sizeof(float2) * nhead * X3);  // nout * B internal fields
     net->V = c->g.V;
+    net->B = B;
     net->F.release();
     net->R.release();
+    net->gh.release();
+    net->ga.release();
+    net->yt.release();
 }
 
-void forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed) {
-    ensure_ws(net, c);
-    const int64_t V = c->g.V, V3 = V * 3;
+// layers and head on h[0] (already filled) for the current batch
+void forward_core(dwf_net *net, dwf_ctx *c) {
+    const int64_t V = c->g.V, X3 = V * 3 * net->B;
     const int L = net->sh.layers, C4 = 4 * net->sh.hidden;
+    const double2 *U = c->U64.as<double2>();
+    for (int l = 0; l < L; ++l) {
+        const int ci = cin4(net, l);
+        transport_kernel<<<grid1(c, ci * V * net->B), NT, 0, c->stream>>>(net->S[l].as<float2>(),
+                                                                          net->h[l].as<float2>(), U, c->g, ci, net->B);
+        DWF_CHECK_LAUNCH();
+        const float2 *W = net->P.as<float2>() + net->off[l];
+        gemm(net, c, net->a[l].as<float2>(), W, net->S[l].as<float2>(), C4, (int)X3, 9 * ci, 9 * ci, X3, 0, 0);
+        gate_kernel<<<grid1(c, C4 * V * net->B), NT, 0, c->stream>>>(net->h[l + 1].as<float2>(), net->a[l].as<float2>(),
+                                                                       (int64_t)C4 * V * net->B);
+        DWF_CHECK_LAUNCH();
+    }
+    const int nhead = net->sh.nout * net->sh.Ls * 4;
+    gemm(net, c, net->vh.as<float2>(), net->P.as<float2>() + net->off[L], net->h[L].as<float2>(), nhead, (int)X3, C4,
+         C4, X3, 0, 0);
+    head_to_internal_kernel<<<grid1(c, (int64_t)nhead * X3), NT, 0, c->stream>>>(
+        net->v.as<float2>(), net->vh.as<float2>(), net->sh.nout, net->sh.Ls, V, net->B, 0);
+    DWF_CHECK_LAUNCH();
+}
+
+// the proposal from seeded (or given) noise
+void forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed) {
+    ensure_ws(net, c, 1);
+    const int64_t V = c->g.V, V3 = V * 3;
     const int64_t nin = (int64_t)cin4(net, 0) * V3;
     float2 *h0 = net->h[0].as<float2>();
     if (input) {
@@ -605,29 +659,26 @@ void forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, u
         gauss_fill<double2>(c, net->in64.as<double2>(), 1, nin, 1, V, false, seed, STREAM_NETWORK);
         bcopy<float2, double2>(c, h0, net->in64.as<double2>(), nin);
     }
-    const double2 *U = c->U64.as<double2>();
-    for (int l = 0; l < L; ++l) {
-        const int ci = cin4(net, l);
-        transport_kernel<<<grid1(c, ci * V), NT, 0, c->stream>>>(net->S[l].as<float2>(), net->h[l].as<float2>(), U,
-                                                                 c->g, ci);
-        DWF_CHECK_LAUNCH();
-        const float2 *W = net->P.as<float2>() + net->off[l];
-        gemm(net, c, net->a[l].as<float2>(), W, net->S[l].as<float2>(), C4, (int)V3, 9 * ci, 9 * ci, V3, 0, 0);
-        gate_kernel<<<grid1(c, C4 * V), NT, 0, c->stream>>>(net->h[l + 1].as<float2>(), net->a[l].as<float2>(),
-                                                             (int64_t)C4 * V);
-        DWF_CHECK_LAUNCH();
-    }
-    const int nhead = net->sh.nout * net->sh.Ls * 4;
-    gemm(net, c, net->vh.as<float2>(), net->P.as<float2>() + net->off[L], net->h[L].as<float2>(), nhead, (int)V3, C4,
-         C4, V3, 0, 0);
-    head_to_internal_kernel<<<grid1(c, (int64_t)nhead * V3), NT, 0, c->stream>>>(
-        net->v.as<float2>(), net->vh.as<float2>(), net->sh.nout, net->sh.Ls, V, 0);
+    forward_core(net, c);
+}
+
+// the refinement of B given internal FP64 fields: out_b = v_b + net(v_b)
+void refine_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B) {
+    DWF_REQUIRE(net->sh.c_in == net->sh.Ls && net->sh.nout == 1, DWF_EINVAL,
+                "a refinement network needs c_in = Ls and nout = 1");
+    DWF_REQUIRE(B >= 1, DWF_EINVAL, "no fields to refine");
+    ensure_ws(net, c, B);
+    const int64_t nelem = c->g.V * 12 * c->g.Ls;
+    fields_to_input_kernel<<<grid1(c, nelem * B), NT, 0, c->stream>>>(net->h[0].as<float2>(), fields, c->g.Ls, c->g.V, B);
+    DWF_CHECK_LAUNCH();
+    forward_core(net, c);
+    add_skip_kernel<<<grid1(c, nelem * B), NT, 0, c->stream>>>(net->v.as<float2>(), fields, nelem * B);
     DWF_CHECK_LAUNCH();
 }
 
 double loss_grad_impl(dwf_net *net, dwf_ctx *c, const double2 *targets, int nt, const int block[4]) {
-    const int64_t V = c->g.V, V3 = V * 3;
-    const int Ls = net->sh.Ls, nout = net->sh.nout, nh = 2 * nout, nf = nh + nt;
+    const int64_t V = c->g.V, X3 = V * 3 * net->B;
+    const int Ls = net->sh.Ls, nout = net->sh.nout * net->B, nh = 2 * nout, nf = nh + nt;
     const int64_t nelem = V * 12 * Ls;
     DWF_REQUIRE(nh <= MAXH, DWF_EINVAL, "at most 24 network outputs");
     DWF_REQUIRE(nt >= 1 && nt <= MAXT && nf <= MAXF, DWF_EINVAL, "target count out of range (outputs*2 + targets <= 64)");
@@ -686,31 +737,32 @@ double loss_grad_impl(dwf_net *net, dwf_ctx *c, const double2 *targets, int nt, 
     float2 *gv = net->v.as<float2>();  // the outputs are no longer needed
     split_adj_kernel<<<grid1(c, nelem * nout), NT, 0, c->stream>>>(gv, F, nout, Ls, nelem);
     DWF_CHECK_LAUNCH();
-    const int nhead = nout * Ls * 4, C4 = 4 * net->sh.hidden, L = net->sh.layers;
+    const int nhead = net->sh.nout * Ls * 4, C4 = 4 * net->sh.hidden, L = net->sh.layers;
     float2 *gvh = net->vh.as<float2>();
-    head_to_internal_kernel<<<grid1(c, (int64_t)nhead * V3), NT, 0, c->stream>>>(gv, gvh, nout, Ls, V, 1);
+    head_to_internal_kernel<<<grid1(c, (int64_t)nhead * X3), NT, 0, c->stream>>>(gv, gvh, net->sh.nout, Ls, V, net->B,
+                                                                                  1);
     DWF_CHECK_LAUNCH();
     float2 *Gr = net->G.as<float2>();
     // head: dHd = gvh h_L^+,  dh_L = Hd^+ gvh
-    gemm(net, c, Gr + net->off[L], gvh, net->h[L].as<float2>(), nhead, C4, (int)V3, V3, V3, 0, 1);
-    if (net->gh.bytes < sizeof(float2) * (size_t)C4 * V3) net->gh.alloc(sizeof(float2) * (size_t)C4 * V3);
-    if (net->ga.bytes < sizeof(float2) * (size_t)C4 * V3) net->ga.alloc(sizeof(float2) * (size_t)C4 * V3);
-    gemm(net, c, net->gh.as<float2>(), net->P.as<float2>() + net->off[L], gvh, C4, (int)V3, nhead, C4, V3, 1, 0);
+    gemm(net, c, Gr + net->off[L], gvh, net->h[L].as<float2>(), nhead, C4, (int)X3, X3, X3, 0, 1);
+    if (net->gh.bytes < sizeof(float2) * (size_t)C4 * X3) net->gh.alloc(sizeof(float2) * (size_t)C4 * X3);
+    if (net->ga.bytes < sizeof(float2) * (size_t)C4 * X3) net->ga.alloc(sizeof(float2) * (size_t)C4 * X3);
+    gemm(net, c, net->gh.as<float2>(), net->P.as<float2>() + net->off[L], gvh, C4, (int)X3, nhead, C4, X3, 1, 0);
     for (int l = L - 1; l >= 0; --l) {
         const int ci = cin4(net, l);
-        gate_bwd_kernel<<<grid1(c, (int64_t)C4 * V), NT, 0, c->stream>>>(net->ga.as<float2>(), net->a[l].as<float2>(),
-                                                                         net->gh.as<float2>(), (int64_t)C4 * V);
+        gate_bwd_kernel<<<grid1(c, (int64_t)C4 * V * net->B), NT, 0, c->stream>>>(
+            net->ga.as<float2>(), net->a[l].as<float2>(), net->gh.as<float2>(), (int64_t)C4 * V * net->B);
         DWF_CHECK_LAUNCH();
         // dW_l = ga S_l^+
-        gemm(net, c, Gr + net->off[l], net->ga.as<float2>(), net->S[l].as<float2>(), C4, 9 * ci, (int)V3, V3, V3, 0, 1);
+        gemm(net, c, Gr + net->off[l], net->ga.as<float2>(), net->S[l].as<float2>(), C4, 9 * ci, (int)X3, X3, X3, 0, 1);
         if (l == 0) break;
         // dh_l = sum_d T_d^+ (W_l[d]^+ ga)
-        const size_t yt = sizeof(float2) * (size_t)9 * ci * V3;
+        const size_t yt = sizeof(float2) * (size_t)9 * ci * X3;
         if (net->yt.bytes < yt) net->yt.alloc(yt);
-        gemm(net, c, net->yt.as<float2>(), net->P.as<float2>() + net->off[l], net->ga.as<float2>(), 9 * ci, (int)V3, C4,
-             9 * ci, V3, 1, 0);
-        transport_adj_kernel<<<grid1(c, (int64_t)ci * V), NT, 0, c->stream>>>(net->gh.as<float2>(), net->yt.as<float2>(),
-                                                                              c->U64.as<double2>(), c->g, ci);
+        gemm(net, c, net->yt.as<float2>(), net->P.as<float2>() + net->off[l], net->ga.as<float2>(), 9 * ci, (int)X3, C4,
+             9 * ci, X3, 1, 0);
+        transport_adj_kernel<<<grid1(c, (int64_t)ci * V * net->B), NT, 0, c->stream>>>(
+            net->gh.as<float2>(), net->yt.as<float2>(), c->U64.as<double2>(), c->g, ci, net->B);
         DWF_CHECK_LAUNCH();
     }
     double loss = 0;
@@ -783,6 +835,22 @@ void net_forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_de
     unpack(c, out, net->v.p, DWF_F32, net->sh.nout);
     DWF_CUDA(cudaStreamSynchronize(c->stream));
 }
+
+void net_refine_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B, double2 *out) {
+    refine_impl(net, c, fields, B);
+    unpack(c, out, net->v.p, DWF_F32, B);
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+double net_refine_loss_grad_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B, const double2 *targets, int nt,
+                                 const int block[4], void *grad, bool grad_dev) {
+    refine_impl(net, c, fields, B);
+    const double L = loss_grad_impl(net, c, targets, nt, block);
+    if (grad) net_copy_out(net, net->G, grad, grad_dev);
+    return L;
+}
+
+bool net_is_refiner(const dwf_net *net) { return net->sh.c_in == net->sh.Ls && net->sh.nout == 1; }
 
 double net_loss_grad_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed,
                           const double2 *targets, int nt, const int block[4], void *grad, bool grad_dev) {

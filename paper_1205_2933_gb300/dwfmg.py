@@ -121,9 +121,15 @@ def _load():
     L.net_adam.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.net_destroy.argtypes = [vp]
     L.net_destroy.restype = None
-    L.mg_setup_learned.argtypes = [vp, vp, ctypes.c_uint, i, ip, ip, ctypes.POINTER(mg_params), i, ctypes.c_double, i,
-                                   ip]
+    L.mg_setup_learned.argtypes = [vp, vp, ctypes.c_uint, i, ip, ip, ctypes.POINTER(mg_params), i, i, ctypes.c_double,
+                                   i, ip]
     L.mg_setup_learned.restype = st
+    L.net_refine.argtypes = [vp, vp, vp, i, vp]
+    L.net_refine.restype = st
+    L.net_refine_loss_grad.argtypes = [vp, vp, vp, i, vp, i, ip, ctypes.POINTER(ctypes.c_double), vp]
+    L.net_refine_loss_grad.restype = st
+    L.mg_get_adaptive_vectors.argtypes = [vp, i, vp]
+    L.mg_get_adaptive_vectors.restype = st
     for name in ("net_create", "net_num_params", "net_set_params", "net_get_params", "net_forward",
                  "net_loss_grad", "net_adam"):
         getattr(L, name).restype = st
@@ -364,14 +370,29 @@ def net_destroy(net):
     _lib.net_destroy(net)
 
 
-def mg_setup_learned(ctx, net, seed, levels, nvec, block, params=None, fallback_iters0=1000, probe_tol=1e-4,
-                     probe_max_iters=0):
-    """mg_setup from the network's proposal; returns True when the plain setup was used as fallback."""
+def mg_setup_learned(ctx, net, seed, levels, nvec, block, params=None, pre_iters0=0, fallback_iters0=1000,
+                     probe_tol=1e-4, probe_max_iters=0):
+    """mg_setup from the network's vectors; returns True when the plain setup was used as fallback."""
     nv = (ctypes.c_int * (levels - 1))(*[int(v) for v in nvec])
     bl = (ctypes.c_int * (4 * (levels - 1)))(*[int(b) for blk in block for b in blk])
     p = ctypes.byref(params) if params is not None else None
     used = ctypes.c_int(0)
-    _check(_lib.mg_setup_learned(ctx, net, int(seed), int(levels), nv, bl, p, int(fallback_iters0),
+    _check(_lib.mg_setup_learned(ctx, net, int(seed), int(levels), nv, bl, p, int(pre_iters0), int(fallback_iters0),
                                  float(probe_tol), int(probe_max_iters), ctypes.byref(used)), "mg_setup_learned")
     return bool(used.value)
 
+
+def net_refine(net, ctx, fields, nfields, out):
+    return _check(_lib.net_refine(net, ctx, _ptr(fields), int(nfields), _ptr(out)), "net_refine")
+
+
+def net_refine_loss_grad(net, ctx, fields, nfields, targets, nt, block, grad=None):
+    b = (ctypes.c_int * 4)(*[int(x) for x in block])
+    loss = ctypes.c_double()
+    _check(_lib.net_refine_loss_grad(net, ctx, _ptr(fields), int(nfields), _ptr(targets), int(nt), b,
+                                     ctypes.byref(loss), _ptr(grad)), "net_refine_loss_grad")
+    return loss.value
+
+
+def mg_get_adaptive_vectors(ctx, level, out):
+    return _check(_lib.mg_get_adaptive_vectors(ctx, int(level), _ptr(out)), "mg_get_adaptive_vectors")

@@ -23,7 +23,8 @@ import numpy as np
 from . import dwfmg as G
 from . import inputs as I
 
-SHAPE = dict(c_in=4, hidden=16, layers=3, nout=12, Ls=16)
+SHAPE = dict(c_in=4, hidden=16, layers=3, nout=12, Ls=16)            # proposal from noise
+REFINE_SHAPE = dict(c_in=16, hidden=16, layers=3, nout=1, Ls=16)     # refinement of relaxed vectors
 
 
 def param_shapes(c_in, hidden, layers, nout, Ls):
@@ -36,12 +37,15 @@ def param_shapes(c_in, hidden, layers, nout, Ls):
     return out
 
 
-def init_params(shape: dict, seed: int) -> np.ndarray:
-    """Gaussian weights scaled by 1/sqrt(fan-in) (complex), seeded."""
+def init_params(shape: dict, seed: int, head_scale: float = 1.0) -> np.ndarray:
+    """Gaussian weights scaled by 1/sqrt(fan-in) (complex), seeded; the head
+    additionally by head_scale (small for a refinement network, which then
+    starts near the identity through its skip connection)."""
     parts = []
     for k, sh in enumerate(param_shapes(**shape)):
         fan_in = int(np.prod(sh[2:])) if k < shape["layers"] else int(np.prod(sh[3:]))
-        parts.append(I.gauss_complex(sh, seed + k, I.STREAM_NETWORK).ravel() / np.sqrt(2.0 * fan_in))
+        w = I.gauss_complex(sh, seed + k, I.STREAM_NETWORK).ravel() / np.sqrt(2.0 * fan_in)
+        parts.append(w * (head_scale if k == shape["layers"] else 1.0))
     return np.concatenate(parts)
 
 
@@ -85,6 +89,35 @@ def lattice(dims, Ls, seed, beta=6.0, sweeps=200, M5=1.8, mf=0.001):
     return G.Context(dims, Ls, M5, mf, torch.from_numpy(U).cuda())
 
 
+def relaxed_vectors(ctx, nvec, block, pre_iters, seed):
+    """The adaptive vectors after a short relaxation (pre_iters CGNR iterations
+    from seeded random vectors): the refinement network's input."""
+    import torch
+    p = solve_params(pre_iters)
+    p.seed = seed
+    G.mg_setup(ctx.h, 2, [nvec], [block], p)
+    v = torch.empty(nvec // 2 * ctx.field_elems, dtype=torch.complex128, device="cuda")
+    G.mg_get_adaptive_vectors(ctx.h, 0, v)
+    return v
+
+
+def train_refine(net, data, nvec, block, epochs, lr, seed=0, log=None):
+    """Adam on the projection loss of refined vectors: data holds (context,
+    relaxed vectors, targets)."""
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        tot = 0.0
+        for i in rng.permutation(len(data)):
+            ctx, v, q = data[i]
+            tot += G.net_refine_loss_grad(net, ctx.h, v, nvec // 2, q, nvec, block)
+            G.net_adam(net, lr)
+        hist.append(tot / len(data))
+        if log:
+            log(f"epoch {ep} loss {hist[-1]:.5f}")
+    return hist
+
+
 def train(net, data, nvec, block, epochs, lr, seed=0, log=None):
     """Adam on the projection loss over (context, targets) pairs; a fresh
     seeded network input every step.  Returns the mean loss of each epoch."""
@@ -117,19 +150,21 @@ def solve_iterations(ctx, src_seed, tol=1e-10):
     return {"iters": st.iters, "true_res": st.true_res, "status": st.status, "seconds": time.perf_counter() - t0}
 
 
-def compare_setups(ctx, net, nvec, block, refine_iters, seed, src_seed, full_iters=1000):
+def compare_setups(ctx, net, nvec, block, refine_iters, seed, src_seed, full_iters=1000, pre_iters=0):
     """Setup time and solve iterations of (a) the plain adaptive setup, (b)
-    random vectors + refine_iters relaxation iterations, (c) the network's
-    proposal + the same refinement."""
+    random vectors + pre_iters + refine_iters relaxation iterations, (c) the
+    network's vectors (a refinement network: after pre_iters relaxation
+    iterations) + refine_iters relaxation iterations."""
     import torch
     out = {}
     for name in ("adaptive", "random", "learned"):
-        p = solve_params(full_iters if name == "adaptive" else refine_iters)
+        p = solve_params(full_iters if name == "adaptive" else
+                         (refine_iters + pre_iters if name == "random" else refine_iters))
         p.seed = seed
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if name == "learned":
-            G.mg_setup_learned(ctx.h, net, seed, 2, [nvec], [block], p)
+            G.mg_setup_learned(ctx.h, net, seed, 2, [nvec], [block], p, pre_iters0=pre_iters)
         else:
             G.mg_setup(ctx.h, 2, [nvec], [block], p)
         torch.cuda.synchronize()
@@ -153,7 +188,11 @@ def main(argv=None):
     ap.add_argument("--refine", type=int, nargs="+", default=[0, 25, 100])
     ap.add_argument("--eval-dims", type=int, nargs=4, default=None)
     ap.add_argument("--eval-seeds", type=int, nargs="*", default=[])
+    ap.add_argument("--mode", choices=["proposal", "refine"], default="proposal")
+    ap.add_argument("--pre", type=int, default=50, help="relaxation iterations before a refinement")
     args = ap.parse_args(argv)
+    if args.mode == "refine":
+        return main_refine(args)
     import torch
     nvec, block, Ls = 2 * SHAPE["nout"], (4, 4, 4, 4), SHAPE["Ls"]
     log = lambda m: print(f"[learned] {m}", flush=True)
@@ -199,6 +238,63 @@ def main(argv=None):
             json.dump(report, f, indent=1)
     G.net_destroy(net)
     for c, _ in train_data + held:
+        c.close()
+
+
+def main_refine(args):
+    """Train and judge a refinement network: inputs are the adaptive vectors
+    after args.pre relaxation iterations, targets the full setup's basis."""
+    import torch
+    shape = REFINE_SHAPE
+    nvec, block, Ls = 24, (4, 4, 4, 4), shape["Ls"]
+    log = lambda m: print(f"[learned] {m}", flush=True)
+    t0 = time.time()
+    train_data, held = [], []
+    for k in range(args.train + args.heldout):
+        ctx = lattice(tuple(args.dims), Ls, args.seed0 + k)
+        q = adaptive_targets(ctx, nvec, block, solve_params())
+        v = relaxed_vectors(ctx, nvec, block, args.pre, seed=3 + k)
+        (train_data if k < args.train else held).append((ctx, v, q))
+    log(f"targets and relaxed inputs for {len(train_data)} + {len(held)} lattices in {time.time() - t0:.1f}s")
+    params = init_params(shape, 78, head_scale=0.01)
+    net = make_net(train_data[0][0], shape, params)
+    ident = make_net(train_data[0][0], shape, init_params(shape, 78, head_scale=0.0))
+    base_loss = [G.net_refine_loss_grad(ident, c.h, v, nvec // 2, q, nvec, block) for c, v, q in held]
+    init_loss = [G.net_refine_loss_grad(net, c.h, v, nvec // 2, q, nvec, block) for c, v, q in held]
+    t1 = time.time()
+    hist = train_refine(net, train_data, nvec, block, args.epochs, args.lr, log=log)
+    train_s = time.time() - t1
+    held_loss = [G.net_refine_loss_grad(net, c.h, v, nvec // 2, q, nvec, block) for c, v, q in held]
+    log(f"held-out loss: relaxed vectors {np.mean(base_loss):.4f}, initial net {np.mean(init_loss):.4f}, "
+        f"trained net {np.mean(held_loss):.4f} ({train_s:.1f}s)")
+    trained = np.empty(G.net_num_params(net), dtype=np.complex128)
+    G.net_get_params(net, trained)
+    report = {"mode": "refine", "shape": shape, "dims": args.dims, "pre_iters": args.pre, "train": args.train,
+              "heldout": args.heldout, "epochs": args.epochs, "lr": args.lr, "train_seconds": train_s,
+              "loss_history": hist, "heldout_loss_relaxed": base_loss, "heldout_loss_initial": init_loss,
+              "heldout_loss_trained": held_loss, "compare": []}
+    for k, (ctx, _, _) in enumerate(held):
+        for it in args.refine:
+            r = compare_setups(ctx, net, nvec, block, it, seed=11 + k, src_seed=500 + k, pre_iters=args.pre)
+            report["compare"].append({"lattice": args.seed0 + args.train + k, "refine": it, **r})
+            log(f"held-out {k} pre {args.pre} refine {it}: " + ", ".join(f"{n} {v['iters']} it" for n, v in r.items()))
+    if args.eval_dims:
+        for s_ in args.eval_seeds:
+            ctx = lattice(tuple(args.eval_dims), Ls, s_)
+            for it in args.refine:
+                r = compare_setups(ctx, net, nvec, block, it, seed=31, src_seed=101, pre_iters=args.pre)
+                report["compare"].append({"lattice": s_, "dims": args.eval_dims, "refine": it, **r})
+                log(f"eval {args.eval_dims} seed {s_} pre {args.pre} refine {it}: " +
+                    ", ".join(f"{n} {v['iters']} it {v['setup_s']:.2f}s" for n, v in r.items()))
+            ctx.close()
+    save(args.out, shape, trained, {"mode": "refine", "dims": args.dims, "pre_iters": args.pre,
+                                    "train_seeds": [args.seed0, args.seed0 + args.train - 1], "epochs": args.epochs})
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump(report, f, indent=1)
+    G.net_destroy(net)
+    G.net_destroy(ident)
+    for c, _, _ in train_data + held:
         c.close()
 
 

@@ -188,3 +188,65 @@ def test_trained_weights_beat_untrained(G):
     G.net_destroy(trained)
     G.net_destroy(untrained)
     ctx.close()
+
+
+RSHAPE = N.NetShape(c_in=LS, hidden=4, layers=2, nout=1, Ls=LS)
+
+
+def test_refine_matches_oracle(G):
+    """Refinement mode: the refined fields, the projection loss and every
+    gradient against the oracle's forward_refine / loss_and_grad_refine."""
+    from gpu_util import to_internal, ctx_for
+    U = I.epsilon_links(DIMS, 0.4, 12)
+    ctx = ctx_for(U, DIMS, LS, 1.8, 0.1)
+    net = G.net_create(ctx.h, RSHAPE.c_in, RSHAPE.hidden, RSHAPE.layers, RSHAPE.nout, RSHAPE.Ls)
+    p = _params(RSHAPE, 60)
+    G.net_set_params(net, np.ascontiguousarray(N.flatten(p)))
+    X, Y, Z, T = DIMS
+    B, nt = 3, 4
+    v = I.gauss_complex((B, LS, T, Z, Y, X, 12), 61, I.STREAM_NETWORK)
+    vt = to_internal(ctx, v, nrhs=B)
+    out = torch.empty(B * ctx.field_elems, dtype=torch.complex128, device="cuda")
+    G.net_refine(net, ctx.h, vt, B, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(v.shape)
+    ref, _ = N.forward_refine(RSHAPE, p, U, v, DIMS)
+    assert _rel(got, ref) < 1e-5
+    q = I.gauss_complex((nt, LS, T, Z, Y, X, 12), 62, I.STREAM_NETWORK)
+    qt = to_internal(ctx, q, nrhs=nt)
+    grad = np.empty(G.net_num_params(net), dtype=np.complex128)
+    L = G.net_refine_loss_grad(net, ctx.h, vt, B, qt, nt, BLOCK, grad=grad)
+    Lo, go = N.loss_and_grad_refine(RSHAPE, p, U, v, q, DIMS, BLOCK)
+    assert abs(L - Lo) < 1e-5 * Lo
+    for k, (a, b) in enumerate(zip(N.unflatten(RSHAPE, grad), go)):
+        assert _rel(a, b) < 1e-4, (k, _rel(a, b))
+    G.net_destroy(net)
+    ctx.close()
+
+
+def test_adaptive_vectors_and_refined_setup(G):
+    """mg_get_adaptive_vectors returns the setup's globally orthonormal
+    vectors; the learned setup with a refinement network (short relaxation,
+    refinement, short relaxation) gives a converging solve."""
+    from gpu_util import ctx_for, to_internal
+    U = I.epsilon_links(DIMS, 0.3, 13)
+    ctx = ctx_for(U, DIMS, LS, 1.8, 0.1)
+    p = G.mg_default_params()
+    p.setup_iters0 = 20
+    G.mg_setup(ctx.h, 2, [8], [(2, 2, 2, 2)], p)
+    a = torch.empty(4 * ctx.field_elems, dtype=torch.complex128, device="cuda")
+    G.mg_get_adaptive_vectors(ctx.h, 0, a)
+    A = a.reshape(4, -1)
+    gram = (A.conj() @ A.T).cpu().numpy()
+    assert np.abs(gram - np.eye(4)).max() < 1e-10
+    net = G.net_create(ctx.h, RSHAPE.c_in, RSHAPE.hidden, RSHAPE.layers, RSHAPE.nout, RSHAPE.Ls)
+    pr = _params(RSHAPE, 70)
+    pr[-1] *= 0.05
+    G.net_set_params(net, np.ascontiguousarray(N.flatten(pr)))
+    p.setup_iters0 = 10
+    assert not G.mg_setup_learned(ctx.h, net, 3, 2, [8], [(2, 2, 2, 2)], p, pre_iters0=10)
+    b = to_internal(ctx, I.gaussian_source(DIMS, LS, 71))
+    x = torch.zeros_like(b)
+    assert G.mg_solve(ctx.h, b, x, 1e-10).true_res <= 1e-10
+    G.net_destroy(net)
+    ctx.close()
