@@ -46,9 +46,10 @@ Shapes
   v      (nout, Ls, T, Z, Y, X, 12)     fine fields in the oracle layout
 
 Refinement mode (forward_refine): the network maps each given fine field
-v_b (its fifth dimension folded into c_in = Ls channels) to
-v_b + head(h_L) (nout = 1, a skip connection), for improving vectors that
-a short relaxation produced.
+v_b (its fifth dimension folded into c_in = Ls channels, scaled by
+alpha = sqrt(Ls V 12) so that a unit-norm field has entries of order one)
+to v_b + head(h_L) / alpha (nout = 1, a skip connection), for improving
+vectors that a short relaxation produced.
 
 Parity pins (tests/test_oracle_net.py): adjointness of the transports
 (T_{+mu}^+ = T_{-mu}), gauge covariance of the forward pass and gauge
@@ -288,15 +289,23 @@ def fields_to_input(v, dims):
     return np.ascontiguousarray(np.transpose(v8, (0, 1, 6, 2, 3, 4, 5, 7)))
 
 
+def refine_scale(s: NetShape, dims):
+    """alpha = sqrt(Ls * V * 12): a unit-norm field times alpha has entries of
+    order one, the range in which the gate t/(1+t) is neither dead nor linear."""
+    return float(np.sqrt(s.Ls * int(np.prod(dims)) * 12))
+
+
 def forward_refine(s: NetShape, params, U, v, dims):
-    """out_b = v_b + net(v_b): c_in = Ls channels (one per s), nout = 1, and
-    a skip connection, so that zero head weights give out = v exactly."""
+    """out_b = v_b + net(alpha v_b) / alpha: c_in = Ls channels (one per s),
+    nout = 1, and a skip connection, so that zero head weights give out = v
+    exactly."""
     assert s.c_in == s.Ls and s.nout == 1
-    h0s = fields_to_input(v, dims)
+    alpha = refine_scale(s, dims)
+    h0s = fields_to_input(v, dims) * alpha
     outs, caches = [], []
     for b in range(v.shape[0]):
         o, cache = forward(s, params, U, h0s[b], dims)
-        outs.append(v[b] + o[0])
+        outs.append(v[b] + o[0] / alpha)
         caches.append(cache)
     return np.array(outs), caches
 
@@ -306,9 +315,10 @@ def loss_and_grad_refine(s: NetShape, params, U, v, targets, dims, block):
     (summed over the batch; the skip connection holds no parameters)."""
     out, caches = forward_refine(s, params, U, v, dims)
     L, gout = projection_loss(out, targets, dims, block, grad=True)
+    alpha = refine_scale(s, dims)
     grads = None
     for b, cache in enumerate(caches):
-        gb = backward(s, params, U, cache, gout[b:b + 1], dims)
+        gb = backward(s, params, U, cache, gout[b:b + 1] / alpha, dims)
         grads = gb if grads is None else [x + y for x, y in zip(grads, gb)]
     return L, grads
 
