@@ -94,9 +94,10 @@ void net_destroy(dwf_net *net);
 
 /* Refinement mode: a network with c_in = Ls and nout = 1 improves given
  * fields instead of drawing them.  Field v_b enters with its fifth dimension
- * as the c_in channels (h_0[s][spin](x, colour) = v_b(x, s, spin, colour)) and
- * leaves as v_b + head(h_L) (a skip connection: zero head weights return the
- * input).  in_dev: nfields complex128 fine fields, internal layout, device
+ * as the c_in channels, scaled by alpha = sqrt(Ls V 12)
+ * (h_0[s][spin](x, colour) = alpha v_b(x, s, spin, colour), entries of order
+ * one for a unit-norm field) and leaves as v_b + head(h_L) / alpha (a skip
+ * connection: zero head weights return the input).  in_dev: nfields complex128 fine fields, internal layout, device
  * (e.g. mg_get_adaptive_vectors after a short setup); out_dev: nfields
  * complex128 fields, canonical layout, device. */
 dwf_status net_refine(dwf_net *net, dwf_ctx *ctx, const void *in_dev, int nfields, void *out_dev);

@@ -31,6 +31,7 @@ struct dwf_net {
     // the columns: column (b*V + site)*3 + colour)
     int64_t V = -1;
     int B = 0;
+    float oscale = 1.f;  // head output scale: 1, or 1/alpha in refinement mode
     std::vector<dwf::DevBuf> h, a, S;
     dwf::DevBuf vh, v, F, R, gvh, gh, ga, yt, gws, gpart, gram, Y, info, lpart, lval, in64;
 };
@@ -243,9 +244,9 @@ __global__ void gate_bwd_kernel(float2 *__restrict__ ga, const float2 *__restric
 // head layout [(j*Ls + s)*4 + spin][x*3 + c]  <->  internal fine fields
 // ---------------------------------------------------------------------------
 // Output field f = j*B + b (output j of batch member b):
-// dir = 0: v_f <- vh;  dir = 1: vh <- v_f
+// dir = 0: v_f <- vh;  dir = 1: vh <- scale * v_f
 __global__ void head_to_internal_kernel(float2 *__restrict__ v, float2 *__restrict__ vh, int nout, int Ls,
-                                        int64_t V, int B, int dir) {
+                                        int64_t V, int B, int dir, float scale = 1.f) {
     const int64_t nelem = V * 12 * Ls, total = nelem * nout * B, cols = (int64_t)B * V * 3;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t f = t / nelem, e = t - f * nelem;
@@ -255,29 +256,30 @@ __global__ void head_to_internal_kernel(float2 *__restrict__ v, float2 *__restri
         const int comp = (int)(sc - x * 12);
         const int64_t hidx = ((j * Ls + s) * 4 + comp / 3) * cols + (b * V + x) * 3 + comp % 3;
         if (dir == 0) v[t] = vh[hidx];
-        else vh[hidx] = v[t];
+        else vh[hidx] = make_float2(scale * v[t].x, scale * v[t].y);
     }
 }
 
 // refinement input: h0[(s*4 + spin)][(b*V + x)*3 + c] = v_b[(x*12 + spin*3 + c)*Ls + s]
 __global__ void fields_to_input_kernel(float2 *__restrict__ h0, const double2 *__restrict__ v, int Ls, int64_t V,
-                                       int B) {
+                                       int B, double alpha) {
     const int64_t nelem = V * 12 * Ls, cols = (int64_t)B * V * 3;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nelem * B; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = t / nelem, e = t - b * nelem;
         const int s = (int)(e % Ls);
         const int64_t sc = e / Ls, x = sc / 12;
         const int comp = (int)(sc - x * 12);
-        h0[((int64_t)s * 4 + comp / 3) * cols + (b * V + x) * 3 + comp % 3] = cvt<float2, double2>(v[t]);
+        h0[((int64_t)s * 4 + comp / 3) * cols + (b * V + x) * 3 + comp % 3] =
+            make_float2((float)(alpha * v[t].x), (float)(alpha * v[t].y));
     }
 }
 
-// out += in (FP32 += FP64): the skip connection of the refinement
-__global__ void add_skip_kernel(float2 *__restrict__ out, const double2 *__restrict__ in, int64_t n) {
+// out = oscale * out + in: the scaled head output plus the skip connection
+__global__ void add_skip_kernel(float2 *__restrict__ out, const double2 *__restrict__ in, int64_t n, double oscale) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float2 a = out[i];
         const double2 b = in[i];
-        out[i] = make_float2((float)((double)a.x + b.x), (float)((double)a.y + b.y));
+        out[i] = make_float2((float)(oscale * a.x + b.x), (float)(oscale * a.y + b.y));
     }
 }
 
@@ -643,6 +645,7 @@ void forward_core(dwf_net *net, dwf_ctx *c) {
 // the proposal from seeded (or given) noise
 void forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed) {
     ensure_ws(net, c, 1);
+    net->oscale = 1.f;
     const int64_t V = c->g.V, V3 = V * 3;
     const int64_t nin = (int64_t)cin4(net, 0) * V3;
     float2 *h0 = net->h[0].as<float2>();
@@ -669,10 +672,14 @@ void refine_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B) {
     DWF_REQUIRE(B >= 1, DWF_EINVAL, "no fields to refine");
     ensure_ws(net, c, B);
     const int64_t nelem = c->g.V * 12 * c->g.Ls;
-    fields_to_input_kernel<<<grid1(c, nelem * B), NT, 0, c->stream>>>(net->h[0].as<float2>(), fields, c->g.Ls, c->g.V, B);
+    // unit-norm fields scaled to entries of order one, where the gate acts
+    const double alpha = std::sqrt((double)nelem);
+    net->oscale = (float)(1.0 / alpha);
+    fields_to_input_kernel<<<grid1(c, nelem * B), NT, 0, c->stream>>>(net->h[0].as<float2>(), fields, c->g.Ls, c->g.V, B,
+                                                                       alpha);
     DWF_CHECK_LAUNCH();
     forward_core(net, c);
-    add_skip_kernel<<<grid1(c, nelem * B), NT, 0, c->stream>>>(net->v.as<float2>(), fields, nelem * B);
+    add_skip_kernel<<<grid1(c, nelem * B), NT, 0, c->stream>>>(net->v.as<float2>(), fields, nelem * B, 1.0 / alpha);
     DWF_CHECK_LAUNCH();
 }
 
@@ -740,7 +747,7 @@ double loss_grad_impl(dwf_net *net, dwf_ctx *c, const double2 *targets, int nt, 
     const int nhead = net->sh.nout * Ls * 4, C4 = 4 * net->sh.hidden, L = net->sh.layers;
     float2 *gvh = net->vh.as<float2>();
     head_to_internal_kernel<<<grid1(c, (int64_t)nhead * X3), NT, 0, c->stream>>>(gv, gvh, net->sh.nout, Ls, V, net->B,
-                                                                                  1);
+                                                                                  1, net->oscale);
     DWF_CHECK_LAUNCH();
     float2 *Gr = net->G.as<float2>();
     // head: dHd = gvh h_L^+,  dh_L = Hd^+ gvh
