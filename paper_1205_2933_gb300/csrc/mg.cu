@@ -358,6 +358,13 @@ template <typename R> class Runner {
     }
 
     void setup_level(int l, const void *start, bool start_on_host) {
+        init_vectors(l, start, start_on_host);
+        relax_vectors(l);
+        finish_level(l);
+    }
+
+    // the random (or given) start vectors of level l into L.vec64
+    void init_vectors(int l, const void *start, bool start_on_host) {
         Level &L = mg.lev[l];
         const mg_params &p = mg.p;
         const int64_t N = n(l);
@@ -373,15 +380,31 @@ template <typename R> class Runner {
         } else {
             gauss_fill<double2>(c, v, L.nadapt, N, L.lg.g.Ls, L.lg.g.V, l == 0, p.seed + (uint32_t)l, 4u);
         }
-        // start vectors: CGNR on A x = 0 from each random vector
-        T *xv = ws(l, 9), *bv = ws(l, 8);
+    }
+
+    // CGNR on A x = 0 from each start vector, one vector at a time
+    void relax_vectors(int l) {
+        Level &L = mg.lev[l];
+        const mg_params &p = mg.p;
+        const int64_t N = n(l);
+        double2 *v = L.vec64.as<double2>();
+        T *xv = ws(l, 9);
         for (int j = 0; j < L.nadapt; ++j) {
             bcopy<T, double2>(c, xv, v + (int64_t)j * N, N);
             cgnr(l, xv, nullptr, p.setup_iters0, false, true, p.setup_tol0);
             store_normalised(l, v + (int64_t)j * N, xv);
         }
+    }
+
+    // global orthonormalisation, the coarse level, optional sweeps
+    void finish_level(int l) {
+        Level &L = mg.lev[l];
+        const mg_params &p = mg.p;
+        double2 *v = L.vec64.as<double2>();
+        T *xv = ws(l, 9), *bv = ws(l, 8);
         orthonormalise_global(l, v, L.nadapt);
         build(l);
+        const int64_t N = n(l);
         // inverse-iteration sweeps: v <- (approximate) A^-1 v with the current
         // multigrid-preconditioned GCR, then the set is re-orthonormalised
         for (int sw = 0; sw < p.setup_sweeps; ++sw) {
@@ -581,8 +604,25 @@ template <typename R> class BatchRunner {
         std::copy(c->hscal, c->hscal + (size_t)nr * SS, out.begin());
     }
 
-    // nu CGNR iterations on D x = b for every right-hand side, from x = 0
-    void cgnr_b(T *x, const T *b, int iters) {
+    // The setup's relaxation for all nr start vectors v (FP64, level 0) at
+    // once: CGNR on D x = 0 from x0 = v is CGNR on D e = -D x0 from e = 0
+    // with x = x0 + e (the same iterates); a vector stops counting once |D x|
+    // fell by rtol (checked every 8 iterations); the run ends when all have.
+    void relax(double2 *v, int iters, double rtol) {
+        const int64_t N = n(0), NT = N * nr;
+        T *x0 = wsb(0, 8), *e = wsb(0, 9), *bb = wsb(0, 10);
+        bcopy<T, double2>(c, x0, v, NT);
+        dslash(c, bb, x0, false, nr);
+        rscale<T>(c, bb, -1.0, NT);
+        cgnr_b(e, bb, iters, rtol);
+        caxpy<T>(c, x0, make_double2(1.0, 0.0), e, NT);
+        for (int r = 0; r < nr; ++r) one.store_normalised(0, v + (size_t)r * N, x0 + (size_t)r * N);
+    }
+
+    // nu CGNR iterations on D x = b for every right-hand side, from x = 0;
+    // with rtol > 0 the iteration also ends once every |r| fell by rtol
+    // (tested every 8 iterations)
+    void cgnr_b(T *x, const T *b, int iters, double rtol = 0.0) {
         const int64_t N = n(0), NT = N * nr;
         T *r = wsb(0, 0), *z = wsb(0, 1), *p = wsb(0, 2), *w = wsb(0, 3);
         bzero<T>(c, x, NT);
@@ -601,10 +641,24 @@ template <typename R> class BatchRunner {
             dslash(c, out, in, dag, nr);
             norm2_b<T>(c, mg.bscratch, SB + slot, SS, out, N, nr);
         };
+        const int irr = 3;
+        std::vector<double> r0(nr, 0.0), sv;
+        if (rtol > 0.0) {
+            norm2_b<T>(c, mg.bscratch, SB + irr, SS, r, N, nr);
+            read_block(sv);
+            for (int q = 0; q < nr; ++q) r0[q] = std::sqrt(sv[(size_t)q * SS + irr]);
+        }
         for (int it = 0; it < iters; ++it) {
             dnorm(w, p, false, iww);
             cg_xr_b<T>(c, x, r, p, w, SB, SS, izz, iww, N, nr);
             if (it + 1 == iters) break;
+            if (rtol > 0.0 && (it + 1) % 8 == 0) {
+                norm2_b<T>(c, mg.bscratch, SB + irr, SS, r, N, nr);
+                read_block(sv);
+                bool all = true;
+                for (int q = 0; q < nr; ++q) all &= std::sqrt(sv[(size_t)q * SS + irr]) <= rtol * r0[q];
+                if (all) break;
+            }
             dnorm(z, r, true, inew);
             cg_p_b<T>(c, p, z, SB, SS, inew, izz, N, nr);
             std::swap(izz, inew);
@@ -929,22 +983,16 @@ template <typename R> class BatchRunner {
     DevBuf dscale;  // per-RHS real scale factors (device)
 };
 
-template <typename R>
-dwf_status setup_t(dwf_ctx *c, MGState &mg, int levels, const void *start, bool start_on_host) {
-    Runner<R> run(c, mg);
-    mg.nlevels = 1;
-    for (int l = 0; l + 1 < levels; ++l) run.setup_level(l, start, start_on_host);
-    return DWF_OK;
-}
-
-// The batched path covers FP32 V-cycles on two levels with nu_1 = 0;
-// DWF_BATCH=0 in the environment turns it off.
-template <typename R> bool batch_eligible(const MGState &mg, int nrhs) {
-    static const bool batch_on = [] {
+bool batch_on() {
+    static const bool on = [] {
         const char *e = getenv("DWF_BATCH");
         return !(e && atoi(e) == 0);
     }();
-    return std::is_same<R, float>::value && nrhs > 1 && batch_on && mg.nlevels == 2 && mg.p.nu_pre == 0 &&
+    return on;
+}
+
+template <typename R> bool batch_eligible(const MGState &mg, int nrhs) {
+    return std::is_same<R, float>::value && nrhs > 1 && batch_on() && mg.nlevels == 2 && mg.p.nu_pre == 0 &&
            mg.p.outer_restart <= 32;
 }
 
@@ -966,6 +1014,30 @@ template <typename R> int batch_width(const MGState &mg, int nrhs, bool solve) {
     return nb;
 }
 
+template <typename R>
+dwf_status setup_t(dwf_ctx *c, MGState &mg, int levels, const void *start, bool start_on_host) {
+    Runner<R> run(c, mg);
+    mg.nlevels = 1;
+    for (int l = 0; l + 1 < levels; ++l) {
+        const int na = mg.lev[l].nadapt;
+        // the fine level's start vectors relax together in the FP32 V-cycle precision
+        if (l == 0 && std::is_same<R, float>::value && batch_on() && na > 1 && na <= 32 &&
+            batch_width<R>(mg, na, false) == std::min(na, 32)) {
+            run.init_vectors(0, start, start_on_host);
+            {
+                BatchRunner<R> br(c, mg, na);
+                br.relax(mg.lev[0].vec64.as<double2>(), mg.p.setup_iters0, mg.p.setup_tol0);
+            }
+            run.finish_level(0);
+        } else {
+            run.setup_level(l, start, start_on_host);
+        }
+    }
+    return DWF_OK;
+}
+
+// The batched path covers FP32 V-cycles on two levels with nu_1 = 0;
+// DWF_BATCH=0 in the environment turns it off.
 template <typename R>
 dwf_status solve_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, int nrhs, mg_stats &st) {
     const int width = batch_eligible<R>(mg, nrhs) ? batch_width<R>(mg, nrhs, true) : 1;
