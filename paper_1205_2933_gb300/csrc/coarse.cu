@@ -50,7 +50,8 @@ __device__ __forceinline__ int64_t shift_site(const Geom &g, int64_t site, int m
 
 template <typename R, typename LT, int NV, bool DAG>
 __global__ void __launch_bounds__(256) coarse_apply_kernel(C<R> *__restrict__ y, const C<R> *__restrict__ x,
-                                                           const LT *__restrict__ Y, Geom g) {
+                                                           const LT *__restrict__ Y, Geom g,
+                                                           const int *__restrict__ nbr) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t field = g.V * NV;
     if (i >= field) return;
@@ -62,11 +63,8 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(C<R> *__restrict__ y,
 #pragma unroll 1
     for (int d = 0; d < 9; ++d) {
         int64_t other = site;
-        if (d > 0) {
-            int mu = (d - 1) >> 1;
-            int dir = ((d - 1) & 1) ? -1 : +1;
-            other = shift_site(g, site, mu, DAG ? -dir : dir);
-        }
+        // table entry 2 mu: +mu, 2 mu + 1: -mu; D^+ reads the opposite neighbour
+        if (d > 0) other = nbr[site * 8 + (DAG ? ((d - 1) ^ 1) : (d - 1))];
         const C<R> *xv = x + other * NV;
         if (!DAG) {
             const int64_t row = ((site * 9 + d) * NV + k) * NV;
@@ -265,10 +263,12 @@ template <typename R, typename LT>
 void coarse_apply_t(dwf_ctx *c, const Level &L, C<R> *y, const C<R> *x, const LT *Y, bool dag, int nrhs) {
     const Geom &g = L.lg.g;
     int n = L.lg.ncomp;
+    const int *nbrt = L.nbr.as<int>();
+    DWF_REQUIRE(nbrt, DWF_ESTATE, "coarse level without a neighbour table");
     dim3 grid((unsigned)((g.V * n + 255) / 256), (unsigned)nrhs);
 #define CK(NV)                                                                                               \
-    if (dag) coarse_apply_kernel<R, LT, NV, true><<<grid, 256, 0, c->stream>>>(y, x, Y, g);                  \
-    else coarse_apply_kernel<R, LT, NV, false><<<grid, 256, 0, c->stream>>>(y, x, Y, g)
+    if (dag) coarse_apply_kernel<R, LT, NV, true><<<grid, 256, 0, c->stream>>>(y, x, Y, g, nbrt);            \
+    else coarse_apply_kernel<R, LT, NV, false><<<grid, 256, 0, c->stream>>>(y, x, Y, g, nbrt)
     NV_DISPATCH2(n, CK);
 #undef CK
     DWF_CHECK_LAUNCH();

@@ -47,6 +47,7 @@ template <> struct LRead<__half2> {
 
 template <typename R, typename LT> struct Args {
     const LT *Y;
+    const int *nbr;    // neighbour table [V][8]
     Geom g;            // coarse lattice (g.V sites)
     const C<R> *b;
     C<R> *x, *r, *Z, *W;   // Z, W: restart vectors each
@@ -55,15 +56,6 @@ template <typename R, typename LT> struct Args {
     int maxiter, restart;
     int *iters;        // accumulates the iteration count
 };
-
-__device__ __forceinline__ int64_t nbr(const Geom &g, int64_t site, int mu, int dir) {
-    int c[4];
-    site_coords(g, site, c);
-    c[mu] += dir;
-    if (c[mu] == g.L[mu]) c[mu] = 0;
-    if (c[mu] < 0) c[mu] = g.L[mu] - 1;
-    return site_index(g, c);
-}
 
 // out = A in on the owned sites [s0, s1): one warp per site, lane l holds
 // column l of every link row (coalesced loads) and the 9 neighbour values
@@ -76,8 +68,7 @@ __device__ void apply_owned(const Args<R, LT> &a, C<R> *out, const C<R> *in, int
         C<R> xv[9];
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
-            int64_t o = site;
-            if (d > 0) o = nbr(a.g, site, (d - 1) >> 1, ((d - 1) & 1) ? -1 : +1);
+            const int o = d > 0 ? a.nbr[site * 8 + d - 1] : (int)site;
             xv[d] = on ? in[o * NV + lane] : mk<R>(0, 0);
         }
         const LT *Ys = a.Y + site * 9 * NV * NV;
@@ -297,6 +288,7 @@ static void launch_t(dwf_ctx *c, const Level &L, const LT *Y, C<R> *x, const C<R
                      double2 *part, int *iters, double tol, int maxiter, int restart) {
     Args<R, LT> a;
     a.Y = Y;
+    a.nbr = L.nbr.as<int>();
     a.g = L.lg.g;
     a.b = b;
     a.x = x;

@@ -46,6 +46,7 @@ template <> struct BLRead<__half2> {
 
 template <typename R, typename LT> struct BArgs {
     const LT *Y;
+    const int *nbr;              // neighbour table [V][8]
     Geom g;                      // coarse lattice
     const C<R> *b;               // [nb][N]
     C<R> *x, *r;                 // [nb][N]
@@ -57,46 +58,36 @@ template <typename R, typename LT> struct BArgs {
     int *iters;
 };
 
-__device__ __forceinline__ int64_t bnbr(const Geom &g, int64_t site, int mu, int dir) {
-    int c[4];
-    site_coords(g, site, c);
-    c[mu] += dir;
-    if (c[mu] == g.L[mu]) c[mu] = 0;
-    if (c[mu] < 0) c[mu] = g.L[mu] - 1;
-    return site_index(g, c);
-}
-
 // out_r = A in_r on the owned sites for the active right-hand sides: one warp
 // per (site, rhs) task, lane l holds column l; consecutive tasks share the
 // site so its links stay in L1.
 template <typename R, typename LT, int NV>
-__device__ void apply_tasks(const BArgs<R, LT> &a, C<R> *out, const C<R> *in, int64_t N, int64_t s0, int64_t s1,
+__device__ void apply_tasks(const BArgs<R, LT> &a, C<R> *out, const C<R> *in, int N, int s0, int s1,
                             const int *act) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool on = lane < NV;
-    const int64_t ntask = (s1 - s0) * a.nb;
-    for (int64_t t = warp; t < ntask; t += BCT / 32) {
-        const int64_t site = s0 + t / a.nb;
-        const int rr = (int)(t % a.nb);
+    const int ntask = (s1 - s0) * a.nb;
+    for (int t = warp; t < ntask; t += BCT / 32) {
+        const int site = s0 + t / a.nb;
+        const int rr = t - (site - s0) * a.nb;
         if (!act[rr]) continue;
-        const C<R> *inr = in + (int64_t)rr * N;
-        C<R> *outr = out + (int64_t)rr * N;
+        const C<R> *inr = in + rr * N;
+        C<R> *outr = out + rr * N;
         C<R> xv[9];
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
-            int64_t o = site;
-            if (d > 0) o = bnbr(a.g, site, (d - 1) >> 1, ((d - 1) & 1) ? -1 : +1);
+            const int o = d > 0 ? a.nbr[site * 8 + d - 1] : site;
             xv[d] = on ? inr[o * NV + lane] : mk<R>(0, 0);
         }
-        const LT *Ys = a.Y + site * 9 * NV * NV;
+        const LT *Ys = a.Y + (int64_t)site * 9 * NV * NV;
 #pragma unroll 4
         for (int k = 0; k < NV; k += 2) {
             R r0 = 0, i0 = 0, r1 = 0, i1 = 0;
             if (on) {
 #pragma unroll
                 for (int d = 0; d < 9; ++d) {
-                    C<R> y0 = BLRead<LT>::template get<R>(Ys, ((int64_t)d * NV + k) * NV + lane);
-                    C<R> y1 = BLRead<LT>::template get<R>(Ys, ((int64_t)d * NV + k + 1) * NV + lane);
+                    C<R> y0 = BLRead<LT>::template get<R>(Ys, (d * NV + k) * NV + lane);
+                    C<R> y1 = BLRead<LT>::template get<R>(Ys, (d * NV + k + 1) * NV + lane);
                     r0 += y0.x * xv[d].x - y0.y * xv[d].y;
                     i0 += y0.x * xv[d].y + y0.y * xv[d].x;
                     r1 += y1.x * xv[d].x - y1.y * xv[d].y;
@@ -128,15 +119,15 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
     __shared__ int act[BMAXB], its[BMAXB];
     const int nb = a.nb, nblk = gridDim.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t V = a.g.V, N = V * NV;
-    const int64_t sites = (V + nblk - 1) / nblk;
-    const int64_t s0 = min((int64_t)blockIdx.x * sites, V), s1 = min(s0 + sites, V);
-    const int64_t e0 = s0 * NV, e1 = s1 * NV;
+    const int V = (int)a.g.V, N = V * NV;  // the coarsest field of one RHS is far below 2^31 elements
+    const int sites = (V + nblk - 1) / nblk;
+    const int s0 = min((int)blockIdx.x * sites, V), s1 = min(s0 + sites, V);
+    const int e0 = s0 * NV, e1 = s1 * NV;
 
     // Element work is spread as items (rr, e): every right-hand side's owned
     // elements padded to whole warps, so the 32 lanes of a warp round share
     // one right-hand side and its partial sums need no segmentation.
-    const int64_t E = e1 - e0, Epad = (E + 31) / 32 * 32, nitems = (int64_t)nb * Epad;
+    const int E = e1 - e0, Epad = (E + 31) / 32 * 32, nitems = nb * Epad;
 
     auto zero_red = [&](int nv) {
         for (int q = threadIdx.x; q < (BCT / 32) * nv; q += BCT) red[q / nv][q % nv] = make_double2(0, 0);
@@ -182,12 +173,12 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
 
     // x = 0, r = b, |b|^2 per right-hand side
     zero_red(nb);
-    for (int64_t base = warp * 32; base < nitems; base += BCT) {
+    for (int base = warp * 32; base < nitems; base += BCT) {
         const int rr = (int)(base / Epad);
-        const int64_t eo = base - rr * Epad + lane;
+        const int eo = base - rr * Epad + lane;
         double2 v = make_double2(0, 0);
         if (eo < E) {
-            const int64_t i = rr * N + e0 + eo;
+            const int i = rr * N + e0 + eo;
             a.x[i] = mk<R>(0, 0);
             const C<R> bv = a.b[i];
             a.r[i] = bv;
@@ -211,9 +202,9 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
         for (int rr = 0; rr < nb; ++rr) any |= act[rr] != 0;
         if (!any) break;
         C<R> *Zk = a.Z + (size_t)k * nb * N, *Wk = a.W + (size_t)k * nb * N;
-        for (int64_t base = warp * 32; base < nitems; base += BCT) {
+        for (int base = warp * 32; base < nitems; base += BCT) {
             const int rr = (int)(base / Epad);
-            const int64_t eo = base - rr * Epad + lane;
+            const int eo = base - rr * Epad + lane;
             if (act[rr] && eo < E) Zk[rr * N + e0 + eo] = a.r[rr * N + e0 + eo];
         }
         __threadfence();
@@ -221,12 +212,12 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
         apply_tasks<R, LT, NV>(a, Wk, Zk, N, s0, s1, act);
         for (int pass = 0; pass < 2 && k > 0; ++pass) {
             zero_red(k * nb);
-            for (int64_t base = warp * 32; base < nitems; base += BCT) {
+            for (int base = warp * 32; base < nitems; base += BCT) {
                 const int rr = (int)(base / Epad);
                 if (!act[rr]) continue;
-                const int64_t eo = base - rr * Epad + lane;
+                const int eo = base - rr * Epad + lane;
                 const bool ok = eo < E;
-                const int64_t ie = rr * N + e0 + eo;
+                const int ie = rr * N + e0 + eo;
                 const C<R> w = ok ? Wk[ie] : mk<R>(0, 0);
                 C<R> u[BMAXR];
 #pragma unroll
@@ -242,11 +233,11 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
                     }
             }
             finish(k * nb);
-            for (int64_t base = warp * 32; base < nitems; base += BCT) {
+            for (int base = warp * 32; base < nitems; base += BCT) {
                 const int rr = (int)(base / Epad);
-                const int64_t eo = base - rr * Epad + lane;
+                const int eo = base - rr * Epad + lane;
                 if (!act[rr] || eo >= E) continue;
-                const int64_t ie = rr * N + e0 + eo;
+                const int ie = rr * N + e0 + eo;
                 C<R> w = Wk[ie], z = Zk[ie];
                 C<R> wi[BMAXR], zi[BMAXR];
 #pragma unroll
@@ -271,13 +262,13 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
         }
         // |w|^2 and <w, r>
         zero_red(2 * nb);
-        for (int64_t base = warp * 32; base < nitems; base += BCT) {
+        for (int base = warp * 32; base < nitems; base += BCT) {
             const int rr = (int)(base / Epad);
             if (!act[rr]) continue;
-            const int64_t eo = base - rr * Epad + lane;
+            const int eo = base - rr * Epad + lane;
             double2 v0 = make_double2(0, 0), v1 = make_double2(0, 0);
             if (eo < E) {
-                const int64_t ie = rr * N + e0 + eo;
+                const int ie = rr * N + e0 + eo;
                 const C<R> w = Wk[ie], q = a.r[ie];
                 v0.x = (double)w.x * w.x + (double)w.y * w.y;
                 v1.x = (double)w.x * q.x + (double)w.y * q.y;
@@ -291,15 +282,15 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
             }
         }
         finish(2 * nb);
-        for (int64_t base = warp * 32; base < nitems; base += BCT) {
+        for (int base = warp * 32; base < nitems; base += BCT) {
             const int rr = (int)(base / Epad);
-            const int64_t eo = base - rr * Epad + lane;
+            const int eo = base - rr * Epad + lane;
             if (!act[rr] || eo >= E) continue;
             const double ww = tot[rr].x;
             if (!(ww > 0.0)) continue;  // breakdown: handled below, same in every CTA
             const double inv = 1.0 / sqrt(ww);
             const R sc = (R)inv, arr = (R)(tot[nb + rr].x * inv), aii = (R)(tot[nb + rr].y * inv);
-            const int64_t ie = rr * N + e0 + eo;
+            const int ie = rr * N + e0 + eo;
             C<R> z = Zk[ie], w = Wk[ie], xx = a.x[ie], q = a.r[ie];
             z.x *= sc; z.y *= sc; w.x *= sc; w.y *= sc;
             xx.x += arr * z.x - aii * z.y;
@@ -334,13 +325,13 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
                 grid.sync();
                 apply_tasks<R, LT, NV>(a, a.r, a.x, N, s0, s1, act);
                 zero_red(nb);
-                for (int64_t base = warp * 32; base < nitems; base += BCT) {
+                for (int base = warp * 32; base < nitems; base += BCT) {
                     const int rr = (int)(base / Epad);
                     if (!act[rr]) continue;
-                    const int64_t eo = base - rr * Epad + lane;
+                    const int eo = base - rr * Epad + lane;
                     double2 v = make_double2(0, 0);
                     if (eo < E) {
-                        const int64_t ie = rr * N + e0 + eo;
+                        const int ie = rr * N + e0 + eo;
                         const C<R> bv = a.b[ie], ax = a.r[ie];
                         const C<R> q = mk<R>(bv.x - ax.x, bv.y - ax.y);
                         a.r[ie] = q;
@@ -371,6 +362,7 @@ void launch_bt(dwf_ctx *c, const Level &L, const LT *Y, C<R> *x, const C<R> *b, 
                double2 *part, int *iters, double tol, int maxiter, int restart) {
     BArgs<R, LT> a;
     a.Y = Y;
+    a.nbr = L.nbr.as<int>();
     a.g = L.lg.g;
     a.b = b;
     a.x = x;
@@ -386,6 +378,9 @@ void launch_bt(dwf_ctx *c, const Level &L, const LT *Y, C<R> *x, const C<R> *b, 
     a.iters = iters;
     void *kargs[] = {&a};
     const int n = L.lg.ncomp;
+    DWF_REQUIRE(L.nbr.p, DWF_ESTATE, "coarse level without a neighbour table");
+    DWF_REQUIRE((int64_t)L.lg.g.V * n * nb < ((int64_t)1 << 31), DWF_EINVAL,
+                "batched coarse solve: nb coarse fields exceed 32-bit indexing");
     void *fn = nullptr;
     switch (n) {
         case 2: fn = (void *)coarse_gcr_batch_kernel<R, LT, 2>; break;

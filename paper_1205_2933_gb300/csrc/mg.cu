@@ -648,19 +648,27 @@ template <typename R> class BatchRunner {
             read_block(sv);
             for (int q = 0; q < nr; ++q) r0[q] = std::sqrt(sv[(size_t)q * SS + irr]);
         }
+        // x += a p is deferred into the direction update, so each iteration
+        // reads r, w (residual) and x, p, z (solution and direction) once
         for (int it = 0; it < iters; ++it) {
             dnorm(w, p, false, iww);
-            cg_xr_b<T>(c, x, r, p, w, SB, SS, izz, iww, N, nr);
-            if (it + 1 == iters) break;
-            if (rtol > 0.0 && (it + 1) % 8 == 0) {
-                norm2_b<T>(c, mg.bscratch, SB + irr, SS, r, N, nr);
-                read_block(sv);
-                bool all = true;
-                for (int q = 0; q < nr; ++q) all &= std::sqrt(sv[(size_t)q * SS + irr]) <= rtol * r0[q];
-                if (all) break;
+            bool last = it + 1 == iters;
+            if (!last) {
+                cg_r_b<T>(c, r, w, SB, SS, izz, iww, N, nr);
+                if (rtol > 0.0 && (it + 1) % 8 == 0) {
+                    norm2_b<T>(c, mg.bscratch, SB + irr, SS, r, N, nr);
+                    read_block(sv);
+                    bool all = true;
+                    for (int q = 0; q < nr; ++q) all &= std::sqrt(sv[(size_t)q * SS + irr]) <= rtol * r0[q];
+                    last = all;
+                }
+            }
+            if (last) {
+                cg_px_b<T>(c, x, p, z, SB, SS, izz, iww, inew, N, nr, true);  // x += a p
+                break;
             }
             dnorm(z, r, true, inew);
-            cg_p_b<T>(c, p, z, SB, SS, inew, izz, N, nr);
+            cg_px_b<T>(c, x, p, z, SB, SS, izz, iww, inew, N, nr, false);
             std::swap(izz, inew);
         }
     }
@@ -1134,6 +1142,26 @@ dwf_status mg_setup_impl(dwf_ctx *c, int levels, const int *nvec, const int (*bl
         Lc.lg.nelem = Lc.lg.g.V * nvec[l];
         dwf_prec yp = p.coarse_prec[l];
         Lc.yprec = (yp == DWF_F32 || yp == DWF_BF16 || yp == DWF_F16) ? yp : DWF_F64;
+        // periodic neighbours of every coarse site, once (the coarse kernels read them)
+        const Geom &g = Lc.lg.g;
+        std::vector<int> tab((size_t)g.V * 8);
+        for (int64_t site = 0; site < g.V; ++site) {
+            int co[4];
+            site_coords(g, site, co);
+            for (int mu = 0; mu < 4; ++mu)
+                for (int dir = 0; dir < 2; ++dir) {
+                    int cc[4] = {co[0], co[1], co[2], co[3]};
+                    cc[mu] = (cc[mu] + (dir == 0 ? 1 : g.L[mu] - 1)) % g.L[mu];
+                    tab[(size_t)site * 8 + 2 * mu + dir] = (int)site_index(g, cc);
+                }
+        }
+        try {
+            Lc.nbr.alloc(sizeof(int) * tab.size());
+            DWF_CUDA(cudaMemcpy(Lc.nbr.p, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice));
+        } catch (...) {
+            delete mg;
+            throw;
+        }
     }
     c->mg = mg;
     try {

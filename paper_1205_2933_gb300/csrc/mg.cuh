@@ -38,6 +38,8 @@ struct Level {
     DevBuf info;           // int per coarse site: Cholesky status
     // fused coarsest-level GCR: contiguous direction vectors, partial sums, counter
     DevBuf cgZ, cgW, cgPart, cgIters;
+    // coarse levels: neighbour table int [V][8], entry 2 mu (+mu) and 2 mu + 1 (-mu)
+    DevBuf nbr;
 };
 
 // ---- blasb.cu ---- batched vector kernels: nrhs fields of n elements, per-RHS
@@ -126,6 +128,11 @@ template <typename T> void multiaxpy_b(dwf_ctx *c, T *w, T *const *V, int k, int
 template <typename T>
 void cg_xr_b(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
 template <typename T> void cg_p_b(dwf_ctx *c, T *p, const T *z, int base, int stride, int inew, int iold, int64_t n, int nrhs);
+template <typename T>
+void cg_r_b(dwf_ctx *c, T *r, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
+template <typename T>
+void cg_px_b(dwf_ctx *c, T *x, T *p, const T *z, int base, int stride, int izz, int iww, int inew, int64_t n, int nrhs,
+             bool last);
 template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs);
 template <typename T> void gcr_wr_b(dwf_ctx *c, T *w, T *res, const double *sc, const double2 *al, int64_t n, int nrhs);
 template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const double2 *g, int64_t n, int nrhs);
