@@ -232,6 +232,23 @@ dwf_status mg_vcycle(dwf_ctx *ctx, void *x_dev, const void *b_dev);
  * layout, device.  Synchronous. */
 dwf_status mg_get_adaptive_vectors(dwf_ctx *ctx, int level, void *out_dev);
 
+/* ---- Low-mode diagnostic (Sec. 2, Fig. 1: the overlap of the low modes
+ * with the coarse space) -------------------------------------------------
+ * dwf_lowest_modes: the k (1..32) smallest eigenpairs of D^+ D by subspace
+ * iteration on (D^+ D)^-1 = D^-1 Gamma D^-1 Gamma, each D^-1 a multigrid
+ * solve of the current setup (mg_setup must have completed), with
+ * Rayleigh-Ritz on the iterated subspace; start vectors from Philox with key
+ * (seed, 8).  Stops when every relative residual |A v - lambda v| / lambda
+ * is <= tol or after max_iters iterations.  evals: k doubles (host,
+ * ascending); evecs_dev: k complex128 fine fields, internal layout, device,
+ * orthonormal; resid: NULL or k doubles (host); iters: NULL or the count.
+ * mg_coarse_overlap: for nfields complex128 fields of level `level`
+ * (internal layout, device) the shares |P^+ v|^2 / |v|^2 of each inside the
+ * coarse space of that level's transfer (host doubles).  Both synchronous. */
+dwf_status dwf_lowest_modes(dwf_ctx *ctx, int k, int max_iters, double tol, unsigned int seed, double *evals,
+                            void *evecs_dev, double *resid, int *iters);
+dwf_status mg_coarse_overlap(dwf_ctx *ctx, int level, const void *fields_dev, int nfields, double *overlap);
+
 /* The V-cycle of mg_vcycle (Sec. 2) for nrhs right-hand sides stored one
  * after another (nrhs fine FP64 fields each for x and b).  With an FP32
  * V-cycle on two levels and nu_1 = 0 the right-hand sides go through the

@@ -240,6 +240,23 @@ dwf_status mg_vcycle(dwf_ctx *c, void *x, const void *b) {
     return guarded(c, [&]() -> dwf_status { dwf::mg_vcycle_impl(c, (double2 *)x, (const double2 *)b, 1); return DWF_OK; });
 }
 
+dwf_status dwf_lowest_modes(dwf_ctx *c, int k, int max_iters, double tol, unsigned int seed, double *evals,
+                            void *evecs_dev, double *resid, int *iters) {
+    if (!c || !evals || !evecs_dev) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        dwf::lowest_modes_impl(c, k, max_iters, tol, seed, evals, (double2 *)evecs_dev, resid, iters);
+        return DWF_OK;
+    });
+}
+
+dwf_status mg_coarse_overlap(dwf_ctx *c, int level, const void *fields_dev, int nfields, double *overlap) {
+    if (!c || !fields_dev || !overlap || nfields < 1) return DWF_EINVAL;
+    return guarded(c, [&]() -> dwf_status {
+        dwf::coarse_overlap_impl(c, level, (const double2 *)fields_dev, nfields, overlap);
+        return DWF_OK;
+    });
+}
+
 dwf_status mg_get_adaptive_vectors(dwf_ctx *c, int level, void *out_dev) {
     if (!c || !out_dev || level < 0) return DWF_EINVAL;
     return guarded(c, [&]() -> dwf_status {

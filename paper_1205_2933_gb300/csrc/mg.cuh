@@ -76,6 +76,10 @@ void mg_prolong_impl(dwf_ctx *c, int level, double2 *fout, const double2 *cin);
 void mg_coarse_apply_impl(dwf_ctx *c, int level, void *out, const void *in, bool dag, dwf_prec prec);
 void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b, int nrhs);
 void mg_get_adaptive_impl(dwf_ctx *c, int level, double2 *out);
+// ---- eig.cu ---- low-mode diagnostic
+void lowest_modes_impl(dwf_ctx *c, int k, int max_iters, double tol, unsigned seed, double *evals, double2 *V,
+                       double *resid, int *iters_done);
+void coarse_overlap_impl(dwf_ctx *c, int level, const double2 *f, int nf, double *out);
 void mg_coarse_solve_impl(dwf_ctx *c, int level, void *x, const void *b);
 void mg_coarse_solve_static_impl(dwf_ctx *c, int level, void *x, const void *b);
 

@@ -130,6 +130,11 @@ def _load():
     L.net_refine_loss_grad.restype = st
     L.mg_get_adaptive_vectors.argtypes = [vp, i, vp]
     L.mg_get_adaptive_vectors.restype = st
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.dwf_lowest_modes.argtypes = [vp, i, i, ctypes.c_double, ctypes.c_uint, dp, vp, dp, ip]
+    L.dwf_lowest_modes.restype = st
+    L.mg_coarse_overlap.argtypes = [vp, i, vp, i, dp]
+    L.mg_coarse_overlap.restype = st
     for name in ("net_create", "net_num_params", "net_set_params", "net_get_params", "net_forward",
                  "net_loss_grad", "net_adam"):
         getattr(L, name).restype = st
@@ -396,3 +401,20 @@ def net_refine_loss_grad(net, ctx, fields, nfields, targets, nt, block, grad=Non
 
 def mg_get_adaptive_vectors(ctx, level, out):
     return _check(_lib.mg_get_adaptive_vectors(ctx, int(level), _ptr(out)), "mg_get_adaptive_vectors")
+
+
+def dwf_lowest_modes(ctx, k, evecs, max_iters=50, tol=1e-8, seed=1):
+    """(eigenvalues, residuals, iterations) of the k smallest eigenpairs of D^+ D; vectors into evecs."""
+    ev = (ctypes.c_double * k)()
+    rs = (ctypes.c_double * k)()
+    it = ctypes.c_int()
+    _check(_lib.dwf_lowest_modes(ctx, int(k), int(max_iters), float(tol), int(seed), ev, _ptr(evecs), rs,
+                                 ctypes.byref(it)), "dwf_lowest_modes")
+    return list(ev), list(rs), it.value
+
+
+def mg_coarse_overlap(ctx, level, fields, nfields):
+    out = (ctypes.c_double * nfields)()
+    _check(_lib.mg_coarse_overlap(ctx, int(level), _ptr(fields), int(nfields), out), "mg_coarse_overlap")
+    return list(out)
+
