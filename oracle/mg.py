@@ -441,6 +441,8 @@ class MGParams:
     setup_sweep_tol: float = 0.1       # MG-GCR relative tolerance of a sweep's solve
     split: bool = True                 # split each vector into its Gamma = +1 / -1 halves:
                                        # Nvec/2 adaptive vectors give Nvec coarse components
+    cycle: str = "K"                   # S2 on intermediate levels: "K" = GCR preconditioned by
+                                       # the next V-cycle; "W" = two V-cycles (Sec. 2's W-cycle)
 
 
 def gamma_halves(op, v):
@@ -499,11 +501,16 @@ class MG:
 
     def coarse_solve(self, l, b):
         """S2 on level l >= 1: GCR on R A P, preconditioned by the V-cycle of the
-        next level when there is one (the recursion of Sec. 2)."""
+        next level when there is one (the recursion of Sec. 2); with cycle "W"
+        S2 is two V-cycles of level l instead (Sec. 2: replacing S2 by two
+        V-cycles gives the W-cycle): x = V(b), then x += V(b - A x)."""
         A = self.levels[l].op.apply
         if l == self.nlevels - 1:
             x, _ = gcr(A, b, tol=self.p.coarsest_tol, maxiter=self.p.coarsest_maxiter,
                        restart=self.p.coarse_restart)
+        elif self.p.cycle == "W":
+            x = self.vcycle(l, b)
+            x = x + self.vcycle(l, b - A(x))
         else:
             x, _ = gcr(A, b, tol=self.p.coarse_tol, maxiter=self.p.coarse_maxiter,
                        restart=self.p.coarse_restart, M=lambda r: self.vcycle(l, r))
