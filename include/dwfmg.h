@@ -99,6 +99,9 @@ typedef struct {
     dwf_prec basis_prec;    /* with smoother_prec = F32: F16 keeps an FP16 copy of the block basis for
                                the V-cycle's restriction and prolongation (FP32 arithmetic), F32 none (F32) */
     uint32_t seed;          /* Philox seed of the random start vectors when none are given */
+    int cycle;              /* S2 on intermediate levels (3+ levels): 0 = GCR preconditioned by the next
+                               V-cycle (a K-cycle), 1 = two V-cycles, x = V(b), x += V(b - A x): the
+                               W-cycle of Sec. 2 (0) */
 } mg_params;
 
 typedef struct {

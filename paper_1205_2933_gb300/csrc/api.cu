@@ -63,6 +63,7 @@ void mg_default_params(mg_params *p) {
     for (int i = 0; i < 4; ++i) p->coarse_prec[i] = DWF_F64;
     p->basis_prec = DWF_F32;
     p->seed = 1u;
+    p->cycle = 0;
 }
 
 const char *dwf_strerror(dwf_status s) {

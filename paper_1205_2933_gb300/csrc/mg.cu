@@ -313,6 +313,17 @@ template <typename R> class Runner {
                                 L.cgIters.as<int>(), p.coarsest_tol, p.coarsest_maxiter, p.coarse_restart);
             return;
         }
+        if (!coarsest && p.cycle == 1) {
+            // W-cycle (Sec. 2): two V-cycles of this level, x = V(b); x += V(b - A x)
+            const int64_t N = n(l);
+            T *res = ws(l, 11), *t = ws(l, 12);
+            vcycle(l, x, b);
+            apply(l, res, x, false);
+            cxpay<T>(c, res, make_double2(-1.0, 0.0), b, N);
+            vcycle(l, t, res);
+            caxpy<T>(c, x, make_double2(1.0, 0.0), t, N);
+            return;
+        }
         gcr(l, x, b, coarsest ? p.coarsest_tol : p.coarse_tol, coarsest ? p.coarsest_maxiter : p.coarse_maxiter,
             p.coarse_restart, !coarsest, true, false);
     }

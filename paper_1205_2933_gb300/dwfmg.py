@@ -39,6 +39,7 @@ class mg_params(ctypes.Structure):
         ("coarse_prec", ctypes.c_int * 4),
         ("basis_prec", ctypes.c_int),
         ("seed", ctypes.c_uint32),
+        ("cycle", ctypes.c_int),
     ]
 
 

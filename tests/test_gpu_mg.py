@@ -35,6 +35,7 @@ def _oracle_params(nvec, block, gpu_params):
             "coarse_restart", "setup_iters0", "setup_tol0", "setup_sweeps", "setup_sweep_iters",
             "setup_sweep_tol", "split")
     return OM.MGParams(nvec=tuple(nvec), block=tuple(tuple(b) for b in block),
+                       cycle="W" if gpu_params.cycle == 1 else "K",
                        **{k: getattr(gpu_params, k) for k in keys})
 
 
@@ -310,6 +311,25 @@ def test_three_level_solve(G):
     G.mg_get_coarse_links(c.ctx.h, 2, Y)
     Yref = c.mg.levels[2].op.Y.reshape(-1)
     assert np.linalg.norm(Y.cpu().numpy() - Yref) / np.linalg.norm(Yref) < 1e-6
+    c.close()
+
+
+def test_three_level_w_cycle(G):
+    """The W-cycle of Sec. 2 (S2 on the intermediate level = two V-cycles):
+    the GPU solve reaches the oracle's solution."""
+    c = Case(G, dims=(4, 4, 4, 8), Ls=4, mf=0.1, nvec=[8, 8], block=[(2, 2, 2, 2), (2, 2, 2, 2)],
+             setup_sweeps=0, setup_iters0=20, setup_tol0=0.0, cycle=1)
+    from gpu_util import to_internal, to_canonical, rel_norm
+    b = I.gaussian_source(c.dims, c.Ls, 3)
+    bt = to_internal(c.ctx, b)
+    xt = torch.zeros_like(bt)
+    st = G.mg_solve(c.ctx.h, bt, xt, 1e-10)
+    assert st.true_res <= 1e-10 and st.coarse_applies[2] > 0
+    x = to_canonical(c.ctx, xt, b.shape)
+    assert rel_norm(x, _oracle_solution(c, b)) < 1e-8
+    # the oracle's W-cycle solve takes a similar number of outer iterations
+    xo, info = OM.mg_solve(c.mg, b.reshape(c.op.shape), tol=1e-10)
+    assert abs(info.iters - st.iters) <= max(2, info.iters // 10), (info.iters, st.iters)
     c.close()
 
 
