@@ -170,15 +170,13 @@ __device__ __forceinline__ void hop2(CP acc[12], const float2 *__restrict__ row,
 // wavefront instead of one per site.
 constexpr int LSTRIDE = 73;
 
-// NORM: also |out_r|^2 of every right-hand side r = blockIdx.y into
-// nslot[r * nstride]: one partial per CTA (FP32 per thread, FP64 across the
-// CTA), and the last CTA of each right-hand side (atomic ticket) adds the
-// partials in a fixed order.
+// NORM: also |out_r|^2 of every right-hand side r = blockIdx.y: one FP64
+// partial per CTA (FP32 per thread) into npart; norm_finish_kernel adds them
+// in a fixed order into the scalar slots.
 template <bool DAG, int LS, int MINB, bool NORM>
 __global__ void __launch_bounds__(128, MINB)
 dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, const float2 *__restrict__ U, Geom g,
-                   float diag, float mf, int spb, int64_t field, double *__restrict__ npart,
-                   unsigned *__restrict__ ncount, double *__restrict__ nslot, int nstride) {
+                   float diag, float mf, int spb, int64_t field, double *__restrict__ npart) {
     constexpr int TPS = LS / 2;  // threads per site
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *sL = reinterpret_cast<float4 *>(smem_raw);                 // [spb][LSTRIDE]
@@ -284,38 +282,34 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
     }
     if (NORM) {
         __shared__ double wsum[4];
-        __shared__ bool last;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
         const int warp = threadIdx.x >> 5;
         if (lane == 0) wsum[warp] = (double)nrm;
         __syncthreads();
-        const int nw = (blockDim.x + 31) >> 5;
-        double *pr = npart + (size_t)blockIdx.y * gridDim.x;
         if (threadIdx.x == 0) {
             double t = 0;
-            for (int w = 0; w < nw; ++w) t += wsum[w];
-            pr[blockIdx.x] = t;
-            __threadfence();
-            const unsigned ticket = atomicAdd(ncount + blockIdx.y, 1u);
-            last = (ticket == gridDim.x - 1);
+            for (int w = 0; w < ((int)blockDim.x + 31) >> 5; ++w) t += wsum[w];
+            npart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
         }
-        __syncthreads();
-        if (last) {
-            __threadfence();
-            double t = 0;
-            for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += ((volatile double *)pr)[i];
+    }
+}
+
+// nslot[r * nstride] = sum of the nb CTA partials of right-hand side r = blockIdx.x (fixed order)
+__global__ void __launch_bounds__(256) norm_finish_kernel(const double *__restrict__ npart, double *__restrict__ nslot,
+                                                          int nstride, int nb) {
+    __shared__ double red[8];
+    const double *pr = npart + (size_t)blockIdx.x * nb;
+    double t = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) t += pr[i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-            if (lane == 0) wsum[warp] = t;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double u = 0;
-                for (int w = 0; w < nw; ++w) u += wsum[w];
-                nslot[(size_t)blockIdx.y * nstride] = u;
-                ncount[blockIdx.y] = 0u;
-            }
-        }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0;
+        for (int w = 0; w < 8; ++w) u += red[w];
+        nslot[(size_t)blockIdx.x * nstride] = u;
     }
 }
 
@@ -336,22 +330,18 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
     float diag = (float)(5.0 - c->M5), mf = (float)c->mf;
     const float2 *U = c->U32.as<float2>();
     double *npart = nullptr;
-    unsigned *ncount = nullptr;
     if (nslot) {
         const size_t pb = sizeof(double) * (size_t)grid.x * nrhs;
         if (c->dn_part.bytes < pb) c->dn_part.alloc(pb);
-        if (c->dn_count.bytes < sizeof(unsigned) * (size_t)nrhs) {
-            c->dn_count.alloc(sizeof(unsigned) * (size_t)std::max(nrhs, 32));
-            DWF_CUDA(cudaMemsetAsync(c->dn_count.p, 0, c->dn_count.bytes, c->stream));
-        }
         npart = c->dn_part.as<double>();
-        ncount = c->dn_count.as<unsigned>();
     }
 #define PL(D, M, NRM) dslash_pair_kernel<D, LS, M, NRM><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, spb, \
-                                                                                              field, npart, ncount, nslot, nstride)
+                                                                                              field, npart)
     if (nslot) {
         if (dag) { if (minb == 4) PL(true, 4, true); else PL(true, 5, true); }
         else { if (minb == 4) PL(false, 4, true); else PL(false, 5, true); }
+        DWF_CHECK_LAUNCH();
+        norm_finish_kernel<<<nrhs, 256, 0, c->stream>>>(npart, nslot, nstride, (int)grid.x);
     } else {
         if (dag) { if (minb == 4) PL(true, 4, false); else PL(true, 5, false); }
         else { if (minb == 4) PL(false, 4, false); else PL(false, 5, false); }

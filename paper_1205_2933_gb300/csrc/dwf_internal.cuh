@@ -162,8 +162,8 @@ struct dwf_ctx {
     double *hscal = nullptr;
     // reduction partial sums + completion counter
     dwf::DevBuf red_part, red_count;
-    // partial sums and counters of the Dslash's fused output norms
-    dwf::DevBuf dn_part, dn_count;
+    // per-CTA partial sums of the Dslash's fused output norms
+    dwf::DevBuf dn_part;
     dwf::MGState *mg = nullptr;
     long long applies64 = 0, applies32 = 0;
     // event profiler
