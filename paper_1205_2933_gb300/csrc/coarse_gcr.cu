@@ -189,13 +189,10 @@ __global__ void __launch_bounds__(CT) coarse_gcr_kernel(Args<R, LT> a) {
             __threadfence();
             grid.sync();
             apply_owned<R, LT, NV>(a, Wk, Zk, s0, s1);
-            // classical Gram-Schmidt; a second pass only when the first removed
-            // more than 3/4 of |w|^2 (the same decision in every CTA)
             for (int pass = 0; pass < 2 && k > 0; ++pass) {
-                for (int i = 0; i <= k; ++i) v[i] = make_double2(0, 0);
+                for (int i = 0; i < k; ++i) v[i] = make_double2(0, 0);
                 for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) {
                     C<R> w = Wk[e];
-                    v[k].x += (double)w.x * w.x + (double)w.y * w.y;
                     // loads issued eight at a time before the products (the loop is latency-bound)
                     for (int i0 = 0; i0 < k; i0 += 8) {
                         C<R> u[8];
@@ -210,7 +207,7 @@ __global__ void __launch_bounds__(CT) coarse_gcr_kernel(Args<R, LT> a) {
                             }
                     }
                 }
-                reduce(v, k + 1, P[pass]);
+                reduce(v, k, P[pass]);
                 for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) {
                     C<R> w = Wk[e], z = Zk[e];
                     for (int i0 = 0; i0 < k; i0 += 8) {
@@ -234,11 +231,7 @@ __global__ void __launch_bounds__(CT) coarse_gcr_kernel(Args<R, LT> a) {
                     Wk[e] = w;
                     Zk[e] = z;
                 }
-                double removed = 0;
-                for (int i = 0; i < k; ++i) removed += tot[i].x * tot[i].x + tot[i].y * tot[i].y;
-                const bool again = removed >= 0.75 * tot[k].x;
                 __syncthreads();  // tot is rewritten by the next reduction
-                if (!again) break;
             }
             v[0] = v[1] = make_double2(0, 0);
             for (int64_t e = e0 + threadIdx.x; e < e1; e += CT) {

@@ -210,11 +210,8 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
         __threadfence();
         grid.sync();
         apply_tasks<R, LT, NV>(a, Wk, Zk, N, s0, s1, act);
-        // classical Gram-Schmidt against W_0..W_{k-1}; a second pass only when
-        // the first removed more than 3/4 of |w|^2 for some right-hand side
-        // (the same decision in every CTA: it reads the same totals)
         for (int pass = 0; pass < 2 && k > 0; ++pass) {
-            zero_red((k + 1) * nb);
+            zero_red(k * nb);
             for (int base = warp * 32; base < nitems; base += BCT) {
                 const int rr = (int)(base / Epad);
                 if (!act[rr]) continue;
@@ -234,11 +231,8 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
                         v = wsum(v);
                         if (lane == 0) red[warp][i * nb + rr] = red[warp][i * nb + rr] + v;
                     }
-                double2 ww = make_double2((double)w.x * w.x + (double)w.y * w.y, 0.0);
-                ww = wsum(ww);
-                if (lane == 0) red[warp][k * nb + rr] = red[warp][k * nb + rr] + ww;
             }
-            finish((k + 1) * nb);
+            finish(k * nb);
             for (int base = warp * 32; base < nitems; base += BCT) {
                 const int rr = (int)(base / Epad);
                 const int eo = base - rr * Epad + lane;
@@ -264,16 +258,7 @@ __global__ void __launch_bounds__(BCT) coarse_gcr_batch_kernel(BArgs<R, LT> a) {
                 Wk[ie] = w;
                 Zk[ie] = z;
             }
-            bool again = false;
-            for (int rr = 0; rr < nb; ++rr) {
-                if (!act[rr]) continue;
-                double removed = 0;
-                for (int i = 0; i < k; ++i) removed += tot[i * nb + rr].x * tot[i * nb + rr].x +
-                                                       tot[i * nb + rr].y * tot[i * nb + rr].y;
-                again |= removed >= 0.75 * tot[k * nb + rr].x;
-            }
             __syncthreads();
-            if (!again) break;
         }
         // |w|^2 and <w, r>
         zero_red(2 * nb);
