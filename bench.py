@@ -138,6 +138,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def replica_reduce(ms_total, steps, nrhs, world, dist=None, dev="cpu"):
+    """Replicas only (one independent set of right-hand sides per rank, no
+    collective on the data path): the job's time is the slowest rank's, and
+    the job solved nrhs x world systems per step.  Returns (ms per step,
+    seconds per solve)."""
+    import torch
+    if dist is not None:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / steps
+    return ms_step, ms_step / 1000.0 / (nrhs * world)
+
+
 def gen_inputs(nrhs, rank=0):
     U = I.heatbath_links(DIMS, BETA, HB_SWEEPS, HB_SEED)
     bs = np.stack([I.gaussian_source(DIMS, LS, 101 + 1000 * rank + i) for i in range(nrhs)])
@@ -314,12 +328,7 @@ def main():
     prof = {name: G.dwf_profile_read(ctx.h, k) for name, k in classes}
     units = {name: G.dwf_profile_units(ctx.h, k) for name, k in classes}
     G.dwf_profile(ctx.h, False)
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    value = ms_step / 1000.0 / (nrhs * world)
+    ms_step, value = replica_reduce(ms_total, args.steps, nrhs, world, dist, dev)
 
     # roofline of the dominant kernel: the FP32 fine Dslash
     n32, ms32 = prof["dslash_f32"]
