@@ -206,7 +206,7 @@ def run_reference(args):
     # cost of one solve in fine-operator applications, as measured on the GPU
     # path for this workload (FP64 + FP32 applications per solve, the setup's
     # amortised over the 12 right-hand sides)
-    applies = float(os.environ.get("DWF_APPLIES_PER_SOLVE", "4491"))
+    applies = float(os.environ.get("DWF_APPLIES_PER_SOLVE", "3724"))
     times = []
     for _ in range(args.warmup):
         cpu_baseline_sample(U, b, 3.0)
