@@ -335,15 +335,19 @@ namespace {
 // (KG*NB accumulators per lane); lanes stream over the block's elements, so
 // every basis value is read once and each field value is read by the 8
 // warps of the CTA (L1).  Lane partial sums are reduced with shuffles.
+// CTA b handles coarse site b / ngroups and the right-hand sides
+// r0 = (b % ngroups) * NB ...: the CTAs of one coarse site are adjacent, so
+// its basis block is read from HBM once and from L2 by the others.
 template <typename R, int NV, int NB>
-__global__ void __launch_bounds__(TT, 2) restrict_b_kernel(C<R> *__restrict__ cout, const C<R> *__restrict__ f,
-                                                        const C<R> *__restrict__ Q, BlockMap m, int nrhs, int r0,
+__global__ void __launch_bounds__(TT, 4) restrict_b_kernel(C<R> *__restrict__ cout, const C<R> *__restrict__ f,
+                                                        const C<R> *__restrict__ Q, BlockMap m, int nrhs, int ngroups,
                                                         int64_t cstride) {
     constexpr int NW = TT / 32;
     constexpr int KG = (NV + NW - 1) / NW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = warp * KG;
-    const int64_t xc = blockIdx.x;
+    const int64_t xc = blockIdx.x / ngroups;
+    const int r0 = (int)(blockIdx.x - xc * ngroups) * NB;
     C<R> acc[KG][NB];
 #pragma unroll
     for (int a = 0; a < KG; ++a)
@@ -420,12 +424,14 @@ void restrict_batch(dwf_ctx *c, const Level &L, C<R> *cout, const C<R> *fin, con
     BlockMap m = make_map(L);
     ProfScope ps(c, K_RESTRICT, nrhs);
     const int64_t cstride = ncoarse(m) * L.nv;
-    for (int r0 = 0; r0 < nrhs; r0 += 12) {
-#define RB(NV) restrict_b_kernel<R, NV, 12><<<(unsigned)ncoarse(m), TT, 0, c->stream>>>(cout, fin, Q, m, nrhs, r0, cstride)
-        NV_DISPATCH(L.nv, RB);
+    constexpr int NB = 4;  // right-hand sides per CTA
+    const int ngroups = (nrhs + NB - 1) / NB;
+    const int64_t nblk = ncoarse(m) * ngroups;
+    DWF_REQUIRE(nblk < ((int64_t)1 << 31), DWF_EINVAL, "batched restriction grid too large");
+#define RB(NV) restrict_b_kernel<R, NV, NB><<<(unsigned)nblk, TT, 0, c->stream>>>(cout, fin, Q, m, nrhs, ngroups, cstride)
+    NV_DISPATCH(L.nv, RB);
 #undef RB
-        DWF_CHECK_LAUNCH();
-    }
+    DWF_CHECK_LAUNCH();
 }
 
 template <typename R>
