@@ -34,7 +34,7 @@ def _rank(rank, world, port, out):
 def test_replica_reduction_two_gloo_ranks():
     import torch.multiprocessing as mp
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
