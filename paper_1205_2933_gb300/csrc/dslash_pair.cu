@@ -296,9 +296,9 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
 }
 
 // nslot[r * nstride] = sum of the nb CTA partials of right-hand side r = blockIdx.x (fixed order)
-__global__ void __launch_bounds__(256) norm_finish_kernel(const double *__restrict__ npart, double *__restrict__ nslot,
-                                                          int nstride, int nb) {
-    __shared__ double red[8];
+__global__ void __launch_bounds__(1024) norm_finish_kernel(const double *__restrict__ npart, double *__restrict__ nslot,
+                                                           int nstride, int nb) {
+    __shared__ double red[32];
     const double *pr = npart + (size_t)blockIdx.x * nb;
     double t = 0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) t += pr[i];
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) norm_finish_kernel(const double *__restri
     __syncthreads();
     if (threadIdx.x == 0) {
         double u = 0;
-        for (int w = 0; w < 8; ++w) u += red[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
         nslot[(size_t)blockIdx.x * nstride] = u;
     }
 }
@@ -341,7 +341,7 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
         if (dag) { if (minb == 4) PL(true, 4, true); else PL(true, 5, true); }
         else { if (minb == 4) PL(false, 4, true); else PL(false, 5, true); }
         DWF_CHECK_LAUNCH();
-        norm_finish_kernel<<<nrhs, 256, 0, c->stream>>>(npart, nslot, nstride, (int)grid.x);
+        norm_finish_kernel<<<nrhs, 1024, 0, c->stream>>>(npart, nslot, nstride, (int)grid.x);
     } else {
         if (dag) { if (minb == 4) PL(true, 4, false); else PL(true, 5, false); }
         else { if (minb == 4) PL(false, 4, false); else PL(false, 5, false); }
