@@ -85,6 +85,13 @@ dwf_status net_forward(dwf_net *net, dwf_ctx *ctx, const void *input, unsigned i
 dwf_status net_loss_grad(dwf_net *net, dwf_ctx *ctx, const void *input, unsigned int seed,
                          const void *targets_dev, int nt, const int block[4], double *loss, void *grad);
 
+/* Weight precision of the inference passes (net_forward, net_refine and the
+ * learned setup): DWF_F32 (default) or DWF_BF16, weights rounded to BF16
+ * (round to nearest even) with FP32 arithmetic and accumulation.  Training
+ * (net_loss_grad, net_refine_loss_grad, net_adam) always uses the FP32 master
+ * weights.  DWF_EINVAL for other precisions. */
+dwf_status net_set_weight_precision(dwf_net *net, dwf_prec prec);
+
 /* One Adam step (Kingma and Ba, 2015) on the real and imaginary parts of the
  * parameters with the gradient of the last net_loss_grad (the real gradient
  * of a complex parameter is 2 (Re G, Im G)). */

@@ -367,6 +367,14 @@ dwf_status net_loss_grad(dwf_net *net, dwf_ctx *c, const void *input, unsigned i
     });
 }
 
+dwf_status net_set_weight_precision(dwf_net *net, dwf_prec prec) {
+    if (!net) return DWF_EINVAL;
+    return guarded(nullptr, [&]() -> dwf_status {
+        dwf::net_set_wprec_impl(net, prec);
+        return DWF_OK;
+    });
+}
+
 dwf_status net_adam(dwf_net *net, double lr, double beta1, double beta2, double eps) {
     if (!net) return DWF_EINVAL;
     return guarded(nullptr, [&]() -> dwf_status {

@@ -172,6 +172,7 @@ double net_refine_loss_grad_impl(dwf_net *net, dwf_ctx *c, const double2 *fields
                                  const int block[4], void *grad, bool grad_dev);
 bool net_is_refiner(const dwf_net *net);
 long long net_nparams(const dwf_net *net);
+void net_set_wprec_impl(dwf_net *net, dwf_prec prec);
 int net_nout(const dwf_net *net);
 void net_free(dwf_net *net);
 

@@ -25,6 +25,10 @@ struct dwf_net {
     int64_t nparams = 0;
     std::vector<int64_t> off;  // parameter group offsets (layers..., head)
     dwf::DevBuf P, G, M1, M2;  // parameters, gradient, Adam moments (FP32 complex)
+    // inference weights: BF16-rounded copy of P when the weight precision is BF16
+    dwf::DevBuf Pi;
+    dwf_prec wprec = DWF_F32;
+    bool pi_valid = false;
     int adam_t = 0;
     bool have_grad = false;
     // workspaces for one lattice volume and batch (B fields side by side in
@@ -537,6 +541,15 @@ __global__ void convert_kernel(TO *__restrict__ out, const TI *__restrict__ in, 
         out[i] = cvt<TO, TI>(in[i]);
 }
 
+// out = in rounded to BF16 (round to nearest even) and back: FP32 values
+// that a BF16 weight store holds exactly
+__global__ void round_bf16_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = in[i];
+        out[i] = make_float2(__bfloat162float(__float2bfloat16_rn(v.x)), __bfloat162float(__float2bfloat16_rn(v.y)));
+    }
+}
+
 // Adam on (Re, Im) with the real gradient 2 (Re G, Im G)
 __global__ void adam_kernel(float2 *__restrict__ P, const float2 *__restrict__ G, float2 *__restrict__ M1,
                             float2 *__restrict__ M2, int64_t n, float lr, float b1, float b2, float eps, float c1,
@@ -619,7 +632,22 @@ void ensure_ws(dwf_net *net, dwf_ctx *c, int B) {
 }
 
 // layers and head on h[0] (already filled) for the current batch
-void forward_core(dwf_net *net, dwf_ctx *c) {
+// the weights a pass reads: FP32 masters (training), or their BF16 rounding
+// for inference when the weight precision is BF16
+const float2 *weights(dwf_net *net, dwf_ctx *c, bool infer) {
+    if (!infer || net->wprec != DWF_BF16) return net->P.as<float2>();
+    if (!net->pi_valid) {
+        const int64_t n = net->nparams;
+        if (net->Pi.bytes < sizeof(float2) * (size_t)n) net->Pi.alloc(sizeof(float2) * (size_t)n);
+        round_bf16_kernel<<<grid1(c, n), NT, 0, c->stream>>>(net->Pi.as<float2>(), net->P.as<float2>(), n);
+        DWF_CHECK_LAUNCH();
+        net->pi_valid = true;
+    }
+    return net->Pi.as<float2>();
+}
+
+void forward_core(dwf_net *net, dwf_ctx *c, bool infer) {
+    const float2 *Pw = weights(net, c, infer);
     const int64_t V = c->g.V, X3 = V * 3 * net->B;
     const int L = net->sh.layers, C4 = 4 * net->sh.hidden;
     const double2 *U = c->U64.as<double2>();
@@ -628,22 +656,21 @@ void forward_core(dwf_net *net, dwf_ctx *c) {
         transport_kernel<<<grid1(c, ci * V * net->B), NT, 0, c->stream>>>(net->S[l].as<float2>(),
                                                                           net->h[l].as<float2>(), U, c->g, ci, net->B);
         DWF_CHECK_LAUNCH();
-        const float2 *W = net->P.as<float2>() + net->off[l];
+        const float2 *W = Pw + net->off[l];
         gemm(net, c, net->a[l].as<float2>(), W, net->S[l].as<float2>(), C4, (int)X3, 9 * ci, 9 * ci, X3, 0, 0);
         gate_kernel<<<grid1(c, C4 * V * net->B), NT, 0, c->stream>>>(net->h[l + 1].as<float2>(), net->a[l].as<float2>(),
                                                                        (int64_t)C4 * V * net->B);
         DWF_CHECK_LAUNCH();
     }
     const int nhead = net->sh.nout * net->sh.Ls * 4;
-    gemm(net, c, net->vh.as<float2>(), net->P.as<float2>() + net->off[L], net->h[L].as<float2>(), nhead, (int)X3, C4,
-         C4, X3, 0, 0);
+    gemm(net, c, net->vh.as<float2>(), Pw + net->off[L], net->h[L].as<float2>(), nhead, (int)X3, C4, C4, X3, 0, 0);
     head_to_internal_kernel<<<grid1(c, (int64_t)nhead * X3), NT, 0, c->stream>>>(
         net->v.as<float2>(), net->vh.as<float2>(), net->sh.nout, net->sh.Ls, V, net->B, 0);
     DWF_CHECK_LAUNCH();
 }
 
 // the proposal from seeded (or given) noise
-void forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed) {
+void forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed, bool infer) {
     ensure_ws(net, c, 1);
     net->oscale = 1.f;
     const int64_t V = c->g.V, V3 = V * 3;
@@ -662,11 +689,11 @@ void forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, u
         gauss_fill<double2>(c, net->in64.as<double2>(), 1, nin, 1, V, false, seed, STREAM_NETWORK);
         bcopy<float2, double2>(c, h0, net->in64.as<double2>(), nin);
     }
-    forward_core(net, c);
+    forward_core(net, c, infer);
 }
 
 // the refinement of B given internal FP64 fields: out_b = v_b + net(v_b)
-void refine_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B) {
+void refine_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B, bool infer) {
     DWF_REQUIRE(net->sh.c_in == net->sh.Ls && net->sh.nout == 1, DWF_EINVAL,
                 "a refinement network needs c_in = Ls and nout = 1");
     DWF_REQUIRE(B >= 1, DWF_EINVAL, "no fields to refine");
@@ -678,7 +705,7 @@ void refine_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B) {
     fields_to_input_kernel<<<grid1(c, nelem * B), NT, 0, c->stream>>>(net->h[0].as<float2>(), fields, c->g.Ls, c->g.V, B,
                                                                        alpha);
     DWF_CHECK_LAUNCH();
-    forward_core(net, c);
+    forward_core(net, c, infer);
     add_skip_kernel<<<grid1(c, nelem * B), NT, 0, c->stream>>>(net->v.as<float2>(), fields, nelem * B, 1.0 / alpha);
     DWF_CHECK_LAUNCH();
 }
@@ -823,6 +850,7 @@ void net_set_params_impl(dwf_net *net, const void *p, bool dev) {
     DWF_CUDA(cudaDeviceSynchronize());
     net->adam_t = 0;
     net->have_grad = false;
+    net->pi_valid = false;
 }
 
 void net_copy_out(dwf_net *net, const DevBuf &src, void *p, bool dev) {
@@ -838,20 +866,20 @@ void net_copy_out(dwf_net *net, const DevBuf &src, void *p, bool dev) {
 void net_get_params_impl(dwf_net *net, void *p, bool dev) { net_copy_out(net, net->P, p, dev); }
 
 void net_forward_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed, double2 *out) {
-    forward_impl(net, c, input, input_dev, seed);
+    forward_impl(net, c, input, input_dev, seed, true);
     unpack(c, out, net->v.p, DWF_F32, net->sh.nout);
     DWF_CUDA(cudaStreamSynchronize(c->stream));
 }
 
 void net_refine_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B, double2 *out) {
-    refine_impl(net, c, fields, B);
+    refine_impl(net, c, fields, B, true);
     unpack(c, out, net->v.p, DWF_F32, B);
     DWF_CUDA(cudaStreamSynchronize(c->stream));
 }
 
 double net_refine_loss_grad_impl(dwf_net *net, dwf_ctx *c, const double2 *fields, int B, const double2 *targets, int nt,
                                  const int block[4], void *grad, bool grad_dev) {
-    refine_impl(net, c, fields, B);
+    refine_impl(net, c, fields, B, false);
     const double L = loss_grad_impl(net, c, targets, nt, block);
     if (grad) net_copy_out(net, net->G, grad, grad_dev);
     return L;
@@ -861,7 +889,7 @@ bool net_is_refiner(const dwf_net *net) { return net->sh.c_in == net->sh.Ls && n
 
 double net_loss_grad_impl(dwf_net *net, dwf_ctx *c, const void *input, bool input_dev, unsigned seed,
                           const double2 *targets, int nt, const int block[4], void *grad, bool grad_dev) {
-    forward_impl(net, c, input, input_dev, seed);
+    forward_impl(net, c, input, input_dev, seed, false);
     const double L = loss_grad_impl(net, c, targets, nt, block);
     if (grad) net_copy_out(net, net->G, grad, grad_dev);
     return L;
@@ -871,6 +899,7 @@ void net_adam_impl(dwf_net *net, double lr, double b1, double b2, double eps) {
     DWF_REQUIRE(net->have_grad, DWF_ESTATE, "net_adam needs a gradient from net_loss_grad");
     DWF_REQUIRE(lr > 0 && b1 >= 0 && b1 < 1 && b2 >= 0 && b2 < 1 && eps > 0, DWF_EINVAL, "bad Adam parameters");
     net->adam_t++;
+    net->pi_valid = false;
     const float c1 = (float)(1.0 - std::pow(b1, net->adam_t)), c2 = (float)(1.0 - std::pow(b2, net->adam_t));
     const int64_t n = net->nparams;
     adam_kernel<<<(unsigned)std::min<int64_t>((n + NT - 1) / NT, 4096), NT>>>(
@@ -878,6 +907,12 @@ void net_adam_impl(dwf_net *net, double lr, double b1, double b2, double eps) {
         (float)b2, (float)eps, c1, c2);
     DWF_CHECK_LAUNCH();
     DWF_CUDA(cudaDeviceSynchronize());
+}
+
+void net_set_wprec_impl(dwf_net *net, dwf_prec prec) {
+    DWF_REQUIRE(prec == DWF_F32 || prec == DWF_BF16, DWF_EINVAL, "network weight precision must be F32 or BF16");
+    net->wprec = prec;
+    net->pi_valid = false;
 }
 
 long long net_nparams(const dwf_net *net) { return net->nparams; }

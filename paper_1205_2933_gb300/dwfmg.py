@@ -122,6 +122,8 @@ def _load():
     L.net_adam.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.net_destroy.argtypes = [vp]
     L.net_destroy.restype = None
+    L.net_set_weight_precision.argtypes = [vp, st]
+    L.net_set_weight_precision.restype = st
     L.mg_setup_learned.argtypes = [vp, vp, ctypes.c_uint, i, ip, ip, ctypes.POINTER(mg_params), i, i, ctypes.c_double,
                                    i, ip]
     L.mg_setup_learned.restype = st
@@ -366,6 +368,10 @@ def net_loss_grad(net, ctx, targets, nt, block, input=None, seed=0, grad=None):
     _check(_lib.net_loss_grad(net, ctx, _ptr(input), int(seed), _ptr(targets), int(nt), b, ctypes.byref(loss),
                               _ptr(grad)), "net_loss_grad")
     return loss.value
+
+
+def net_set_weight_precision(net, prec):
+    return _check(_lib.net_set_weight_precision(net, int(prec)), "net_set_weight_precision")
 
 
 def net_adam(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -250,3 +250,32 @@ def test_adaptive_vectors_and_refined_setup(G):
     assert G.mg_solve(ctx.h, b, x, 1e-10).true_res <= 1e-10
     G.net_destroy(net)
     ctx.close()
+
+
+def _bf16(x):
+    """Round to BF16 (nearest even) through FP32, as a BF16 weight store holds them."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_weights(G):
+    """BF16 inference weights: the forward pass equals the oracle's with the
+    weights rounded to BF16 (FP32 arithmetic); training keeps FP32 masters."""
+    U = I.epsilon_links(DIMS, 0.4, 14)
+    c = NetCase(G, U, pseed=80)
+    h0 = _input(SHAPE, DIMS, 81)
+    f32 = c.forward(h0)
+    G.net_set_weight_precision(c.net, G.DWF_BF16)
+    b16 = c.forward(h0)
+    pr = [_bf16(p.real) + 1j * _bf16(p.imag) for p in c.p]
+    ref, _ = N.forward(SHAPE, pr, U, h0, DIMS)
+    assert _rel(b16, ref) < 1e-5
+    assert 1e-5 < _rel(b16, f32) < 5e-2
+    back = np.empty(G.net_num_params(c.net), dtype=np.complex128)
+    G.net_get_params(c.net, back)                      # masters unchanged
+    assert np.abs(back - N.flatten(c.p)).max() < 1e-6 * np.abs(N.flatten(c.p)).max()
+    with pytest.raises(G.DWFError):
+        G.net_set_weight_precision(c.net, G.DWF_F16)
+    c.close()
