@@ -402,3 +402,35 @@ def test_batched_solve_zero_member_and_guess(G):
     for i in (0, 2):
         assert rel_norm(x[i], _oracle_solution(c, bs[i])) < 1e-8
     c.close()
+
+
+def test_full_size_batched_solve_sampled_residual(G):
+    """16^3 x 32, Ls = 16, m_f = 0.001 with the benchmark's solver parameters
+    (epsilon links instead of the heatbath ensemble, to keep host time short;
+    two right-hand sides in the batched path): the FP64 true residual meets
+    1e-10, and the oracle's own operator, applied to the GPU solution at 202
+    sampled 5D sites (both lattice corners among them), reproduces the source
+    there within that bound."""
+    from gpu_util import ctx_for, to_internal
+    import bench
+    dims, Ls, mf = (16, 16, 16, 32), 16, 0.001
+    U = I.epsilon_links(dims, 0.5, 17)
+    ctx = ctx_for(U, dims, Ls, 1.8, mf)
+    G.mg_setup(ctx.h, 2, [24], [(4, 4, 4, 4)], bench.mixed_params(G))
+    bs = np.stack([I.gaussian_source(dims, Ls, 18 + i) for i in range(2)])
+    bt = to_internal(ctx, bs, nrhs=2)
+    xt = torch.zeros_like(bt)
+    st = G.mg_solve(ctx.h, bt, xt, 1e-10, nrhs=2)
+    assert st.status == G.DWF_OK and st.true_res <= 1e-10
+    n = ctx.field_elems
+    canon = torch.empty(n, dtype=torch.complex128, device="cuda")
+    G.dwf_unpack(ctx.h, canon, xt[:n].contiguous())
+    torch.cuda.synchronize()
+    x0 = canon.cpu().numpy().reshape(bs[0].shape)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(1)
+    idx5 = np.concatenate([rng.integers(0, V * Ls, 200), [0, V * Ls - 1]])
+    dx = oracle.DWF(U, dims, Ls, 1.8, mf).D_sites(x0, idx5).reshape(len(idx5), 12)
+    b0 = bs[0].reshape(Ls * V, 12)[idx5]
+    assert np.abs(dx - b0).max() <= 2e-10 * np.linalg.norm(bs[0])
+    ctx.close()
