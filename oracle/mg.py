@@ -13,7 +13,10 @@ Fermions":
              the comparison, cost counted in fine-operator applications
   * Sec. 4   the fine operator's one-hop stencil (here the coarse operator
              R D P of the unsquared operator is the 9-point stencil that one
-             hop on the fine lattice produces on the coarse lattice)
+             hop on the fine lattice produces on the coarse lattice), and the
+             paper's own choice, the coarsened squared operator P^+ D^+ D P,
+             whose coarse stencil reaches two hops (33 coarse offsets with
+             blocks of extent >= 2 in every direction)
 
 Parity pins (tests/test_oracle_*.py):
   D, D^+                  free-field momentum-space closed form, Ls=1 Wilson
@@ -22,6 +25,10 @@ Parity pins (tests/test_oracle_*.py):
   block_orthonormalise    P^+ P = 1, span preserved, agrees with a QR
   Transfer.restrict/prolong  adjoint pair, R P = 1
   coarse_operator         equals the dense P^+ D P by brute force
+  squared_coarse_operator equals the dense (D P)^+ (D P) by brute force; no
+                          coupling beyond the 33 offsets; Hermitian positive;
+                          its coarse correction is the least-squares fit of
+                          the residual over range(P) (numpy lstsq)
   CoarseOp.apply          equals the dense coarse matrix
   gcr / mr / cgnr         dense-LU solutions, residual monotonicity
   vcycle                  Galerkin orthogonality of the coarse correction
@@ -270,6 +277,131 @@ def coarse_operator(op, T: Transfer) -> CoarseOp:
     return CoarseOp(Y, T.cdims)
 
 
+# The squared operator's coarse stencil (Sec. 4): offset 0, the 8 one-hop
+# offsets (1 + 2 mu: +mu, 2 + 2 mu: -mu) and the 24 two-hop diagonals
+# +-mu +-nu (mu < nu), index 9 + 4 p + 2 a + b with p the pair's rank in
+# (0,1), (0,2), (0,3), (1,2), (1,3), (2,3), a = 1 for -mu and b = 1 for -nu.
+MU_NU_PAIRS = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+
+
+def _offsets33():
+    out = [(0, 0, 0, 0)]
+    for mu in range(4):
+        for d in (+1, -1):
+            v = [0, 0, 0, 0]
+            v[mu] = d
+            out.append(tuple(v))
+    for mu, nu in MU_NU_PAIRS:
+        for a in (+1, -1):
+            for b in (+1, -1):
+                v = [0, 0, 0, 0]
+                v[mu], v[nu] = a, b
+                out.append(tuple(v))
+    return out
+
+
+OFFSETS33 = _offsets33()
+
+
+def _shift_vec(c, off):
+    """c(x + off) for a 4-vector offset (x, y, z, t), c shape (1, T, Z, Y, X, ...)."""
+    for mu in range(4):
+        if off[mu]:
+            c = np.roll(c, -off[mu], axis=4 - mu)
+    return c
+
+
+class SquaredCoarseOp:
+    """The coarsened squared operator P^+ D^+ D P (Sec. 4) as a 33-point
+    stencil of dense n x n complex blocks, Y shape (Tc, Zc, Yc, Xc, 33, n, n):
+      (A c)(x) = sum_j Y_j(x) c(x + OFFSETS33[j])   (periodic)."""
+
+    def __init__(self, Y, dims):
+        self.Y = Y
+        self.dims = tuple(int(d) for d in dims)
+        self.S = 1
+        self.n = Y.shape[-1]
+        X, Yd, Z, T = self.dims
+        self.shape = (1, T, Z, Yd, X, self.n)
+        self.count = 0
+
+    def apply(self, c):
+        self.count += 1
+        out = np.zeros_like(c)
+        for j, off in enumerate(OFFSETS33):
+            out = out + np.einsum("tzyxab,stzyxb->stzyxa", self.Y[..., j, :, :], _shift_vec(c, off))
+        return out
+
+    def apply_dag(self, c):
+        """(A^+ c)(x) = sum_j Y_j(x - o_j)^+ c(x - o_j)."""
+        self.count += 1
+        Yh = np.conj(np.swapaxes(self.Y, -1, -2))
+        out = np.zeros_like(c)
+        for j, off in enumerate(OFFSETS33):
+            t = np.einsum("tzyxab,stzyxb->stzyxa", Yh[..., j, :, :], c)
+            out = out + _shift_vec(t, tuple(-o for o in off))
+        return out
+
+
+def squared_coarse_operator(op, T: Transfer) -> SquaredCoarseOp:
+    """P^+ D^+ D P as a 33-point stencil (Sec. 4 coarsens the squared operator).
+
+    D q_l splits by where its terms read q_l: h_0 collects the terms that read
+    inside the block of x (diagonal, fifth-dimension hops, hops within the
+    block), h_{mu,d} the hop from x to x + d mu where it leaves the block.  So
+    on block b'' the field D (q_l on block b' only) equals h_sigma with
+    b' = b'' + sigma, and
+      (P^+ D^+ D P)[b, k; b', l] = sum_{b''} <D q_k|_b, D q_l|_b'>_{b''}
+                                 = sum over sigma1, sigma2 with b = b'' + sigma1,
+                                   b' = b'' + sigma2 of <h_{sigma1,k}, h_{sigma2,l}>_{b''},
+    the coarse offset b' - b = sigma2 - sigma1 kept as a vector (so that two
+    offsets that reach the same site of a small periodic coarse lattice stay
+    apart).  With every block extent >= 2, h_{+mu} (last layer of the block
+    in mu) and h_{-mu} (first layer) never share a site, so the offsets +-2 mu
+    vanish and 33 offsets remain."""
+    if min(T.block) < 2:
+        raise ValueError("the squared coarse stencil needs block extents >= 2")
+    Nv = T.Nv
+    Xc, Yc, Zc, Tc = T.cdims
+    src = [(0, 0, 0, 0)] + OFFSETS33[1:9]
+    pieces = np.empty((9, Nv, int(np.prod(T.cdims)), T.S * int(np.prod(T.block)) * T.n), dtype=np.complex128)
+    for l in range(Nv):
+        q = T.vector(l)
+        rest = op.apply(q)
+        op.count -= 1  # construction applies are not solver cost
+        for mu in range(4):
+            for d in (+1, -1):
+                h = op.hop(q, mu, d) * crossing_mask(op.dims, T.block, op.S, mu, d)
+                rest = rest - h
+                pieces[CoarseOp.dir_index(mu, d), l] = to_blocks(h, T.dims, T.block)
+        pieces[0, l] = to_blocks(rest, T.dims, T.block)
+    Y = np.zeros((Tc, Zc, Yc, Xc, 33, Nv, Nv), dtype=np.complex128)
+    index = {o: j for j, o in enumerate(OFFSETS33)}
+    for i1, s1 in enumerate(src):
+        for i2, s2 in enumerate(src):
+            delta = tuple(b - a for a, b in zip(s1, s2))
+            if delta not in index:
+                continue  # +-2 mu: disjoint supports (checked against brute force)
+            G = np.einsum("kbi,lbi->bkl", np.conj(pieces[i1]), pieces[i2])
+            G = G.reshape(1, Tc, Zc, Yc, Xc, Nv, Nv)
+            # row b = b'' + sigma1: the value at b is G(b - sigma1)
+            Y[..., index[delta], :, :] += _shift_vec(G, tuple(-o for o in s1))[0]
+    return SquaredCoarseOp(Y, T.cdims)
+
+
+def squared_coarse_bruteforce(op, T: Transfer) -> np.ndarray:
+    """Dense (D P)^+ (D P) from the dense prolongator (tiny cases only)."""
+    Nc = int(np.prod(T.cshape))
+    e = np.zeros(Nc, dtype=np.complex128)
+    cols = []
+    for j in range(Nc):
+        e[j] = 1.0
+        cols.append(op.apply(T.prolong(e.reshape(T.cshape))).ravel())
+        e[j] = 0.0
+    DP = np.stack(cols, axis=1)
+    return DP.conj().T @ DP
+
+
 def dense_matrix(apply: Callable, shape) -> np.ndarray:
     """Dense matrix of a linear map by applying it to every unit vector (tiny cases)."""
     N = int(np.prod(shape))
@@ -443,6 +575,8 @@ class MGParams:
                                        # Nvec/2 adaptive vectors give Nvec coarse components
     cycle: str = "K"                   # S2 on intermediate levels: "K" = GCR preconditioned by
                                        # the next V-cycle; "W" = two V-cycles (Sec. 2's W-cycle)
+    coarsen: str = "unsquared"         # "unsquared": R D P (9 points); "squared": the paper's
+                                       # P^+ D^+ D P (Sec. 4), two levels only
 
 
 def gamma_halves(op, v):
@@ -486,7 +620,12 @@ class MG:
             vectors = np.stack([h for v in vectors for h in gamma_halves(lev.op, v)])
         T = Transfer(vectors, lev.op.dims, self.p.block[l])
         lev.transfer = T
-        coarse = coarse_operator(lev.op, T)
+        if self.p.coarsen == "squared":
+            if len(self.p.nvec) != 1:
+                raise ValueError("the squared coarsening is built for two levels")
+            coarse = squared_coarse_operator(lev.op, T)
+        else:
+            coarse = coarse_operator(lev.op, T)
         del self.levels[l + 1:]
         self.levels.append(Level(coarse))
 
@@ -522,11 +661,16 @@ class MG:
           b2 = R (b - A x1)
           x2 = S2^nu2(R A P, b2)
           b3 = b - A (P x2 + x1)
-          x  = x1 + P x2 + S3^nu3(A, b3)"""
+          x  = x1 + P x2 + S3^nu3(A, b3)
+        With the squared coarsening the coarse problem is that of the normal
+        equations, D^+ D x = D^+ r, so b2 = R D^+ (b - A x1) (Sec. 4)."""
         A = self.levels[l].op.apply
         T = self.levels[l].transfer
         x1 = self.smooth(l, b, self.p.nu_pre)
-        b2 = T.restrict(b - A(x1)) if self.p.nu_pre else T.restrict(b)
+        r1 = b - A(x1) if self.p.nu_pre else b
+        if self.p.coarsen == "squared" and l == 0:
+            r1 = self.levels[0].op.apply_dag(r1)
+        b2 = T.restrict(r1)
         x2 = self.coarse_solve(l + 1, b2)
         Px2 = T.prolong(x2)
         b3 = b - A(Px2 + x1)

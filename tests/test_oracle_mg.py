@@ -217,3 +217,94 @@ def test_w_cycle():
     xs = _dense_solution(op, b)
     assert info.converged and M.norm(b - op.apply(x)) / M.norm(b) <= 1e-10
     assert M.norm(x - xs) / M.norm(xs) < 1e-8
+
+
+# ---- the coarsened squared operator (Sec. 4) ------------------------------
+
+@pytest.mark.parametrize("dims,block,Ls,nv", [
+    ((4, 6, 4, 4), (2, 2, 2, 2), 2, 4),     # coarse 2x3x2x2: +-mu meet on the extent-2 axes
+    ((8, 4, 4, 4), (2, 2, 2, 2), 2, 2),     # coarse 4x2x2x2: room for an offset of 2 in x
+    ((4, 4, 6, 4), (2, 2, 3, 2), 3, 4),     # anisotropic blocks
+])
+def test_squared_coarse_operator_equals_bruteforce(dims, block, Ls, nv):
+    """The 33-point stencil equals (D P)^+ (D P) built column by column; the
+    coarse matrix is Hermitian positive definite."""
+    op = _op(dims, Ls, 0.05, 0.5, 2)
+    T = M.Transfer(_vectors(op, nv), op.dims, block)
+    C = M.squared_coarse_operator(op, T)
+    dense = M.squared_coarse_bruteforce(op, T)
+    Ac = M.dense_matrix(C.apply, T.cshape)
+    assert np.abs(Ac - dense).max() < 1e-13 * np.abs(dense).max()
+    assert np.abs(M.dense_matrix(C.apply_dag, T.cshape) - Ac).max() < 1e-13 * np.abs(dense).max()
+    assert np.linalg.eigvalsh(0.5 * (dense + dense.conj().T)).min() > 0
+
+
+def test_squared_coarse_stencil_reach():
+    """Sec. 4 states that the squared operator's coarse stencil reaches two
+    hops.  With 2^4 blocks a coarse site couples to every site whose offset has
+    components in {-1, 0, 1} with at most two of them nonzero (33 sites) and to
+    no other: on a 6^4 coarse lattice exactly 33 coarse sites respond to a
+    point source, and no coupling reaches an offset of 2 in any direction."""
+    op = _op((12, 12, 12, 12), 1, 0.1, 0.3, 4)
+    T = M.Transfer(_vectors(op, 2), op.dims, (2, 2, 2, 2))
+    C = M.squared_coarse_operator(op, T)
+    c = np.zeros(T.cshape, complex)
+    c[0, 3, 3, 3, 3, :] = 1.0
+    out = np.abs(C.apply(c)).sum(axis=(0, -1))
+    hit = np.argwhere(out > 1e-14)
+    assert len(hit) == 33
+    d = np.abs(hit - 3)
+    assert d.max() == 1 and (d > 0).sum(axis=1).max() == 2
+    # brute force on a lattice with room for offset 2 along x
+    op2 = _op((8, 4, 4, 4), 2, 0.1, 0.5, 5)
+    T2 = M.Transfer(_vectors(op2, 2), op2.dims, (2, 2, 2, 2))
+    dense = M.squared_coarse_bruteforce(op2, T2).reshape(2, 2, 2, 4, 2, 2, 2, 2, 4, 2)
+    for x in range(4):
+        assert np.all(dense[:, :, :, x, :, :, :, :, (x + 2) % 4, :] == 0)
+
+
+def test_squared_coarse_correction_is_least_squares():
+    """With the squared coarse operator the exact coarse correction
+    P (P^+ D^+ D P)^-1 P^+ D^+ r minimises |r - D x| over x in range(P)
+    (numpy's lstsq on the dense D P)."""
+    op = _op((4, 4, 4, 4), 2, 0.1, 0.4, 6)
+    T = M.Transfer(_vectors(op, 4), op.dims, (2, 2, 2, 2))
+    C = M.squared_coarse_operator(op, T)
+    Ac = M.dense_matrix(C.apply, T.cshape)
+    r = I.gaussian_source(op.dims, op.S, 7).reshape(op.shape)
+    c = np.linalg.solve(Ac, T.restrict(op.apply_dag(r)).ravel()).reshape(T.cshape)
+    Nc = int(np.prod(T.cshape))
+    e = np.zeros(Nc, complex)
+    DP = []
+    for j in range(Nc):
+        e[j] = 1.0
+        DP.append(op.apply(T.prolong(e.reshape(T.cshape))).ravel())
+        e[j] = 0.0
+    cl, *_ = np.linalg.lstsq(np.stack(DP, axis=1), r.ravel(), rcond=None)
+    assert np.abs(c.ravel() - cl).max() < 1e-10 * np.abs(cl).max()
+
+
+def test_squared_vcycle_and_solve():
+    """nu = 0 and an exact coarse solve: P^+ D^+ (b - D x) = 0 after the
+    squared coarse correction; the adaptive MG with the squared coarsening
+    reaches the dense-LU solution with true residual <= 1e-10."""
+    op = _op((4, 4, 4, 4), 4, 0.1, 0.3, 1)
+    p = M.MGParams(nvec=(8,), block=((2, 2, 2, 2),), nu_pre=0, nu_post=0, coarsest_tol=1e-14,
+                   coarsest_maxiter=2000, coarse_restart=200, coarsen="squared")
+    mg = M.MG(op, p)
+    mg.build_from_vectors(0, _vectors(op, 4))
+    b = I.gaussian_source(op.dims, op.S, 2).reshape(op.shape)
+    x = mg.vcycle(0, b)
+    T = mg.levels[0].transfer
+    g = T.restrict(op.apply_dag(b - op.apply(x)))
+    assert np.abs(g).max() < 1e-11 * np.abs(T.restrict(op.apply_dag(b))).max()
+    op = _op((2, 2, 2, 4), 4, 0.1, 0.3, 1)
+    b = I.gaussian_source(op.dims, op.S, 2).reshape(op.shape)
+    mg = M.adaptive_setup(op, M.MGParams(nvec=(8,), block=((2, 2, 2, 2),), coarsen="squared"), [_vectors(op, 4)])
+    x, info = M.mg_solve(mg, b, tol=1e-10)
+    xs = _dense_solution(op, b)
+    assert info.converged and M.norm(b - op.apply(x)) / M.norm(b) <= 1e-10
+    assert M.norm(x - xs) / M.norm(xs) < 1e-8
+    with pytest.raises(ValueError):
+        M.MG(op, M.MGParams(nvec=(8,), block=((1, 2, 2, 2),), coarsen="squared")).build_from_vectors(
+            0, _vectors(op, 4))
