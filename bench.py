@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--nrhs", type=int, default=NRHS)
+    ap.add_argument("--coarsen", choices=["unsquared", "squared"], default="unsquared",
+                    help="coarse operator: R D P (9-point, default) or the squared operator's P^+ D^+ D P "
+                         "(33-point, Sec. 4; right-hand sides solved one after another)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="also time the plain FP64 method (1 solve)")
@@ -71,9 +74,11 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(nrhs):
+def workload_config(nrhs, coarsen="unsquared"):
+    coarse = ("BF16 coarse stencil" if coarsen == "unsquared" else
+              "BF16 33-point coarse stencil of the squared operator P^+D^+DP (RHS one after another)")
     return {"workload": f"DWF MG solve, 16^3x32 Ls=16 M5=1.8 mf=0.001, heatbath beta=6.0 ({HB_SWEEPS} sweeps, "
-                        f"seed {HB_SEED}), 2-level Nvec=24 blocks 4^4, FP32 V-cycle + BF16 coarse stencil + "
+                        f"seed {HB_SEED}), 2-level Nvec=24 blocks 4^4, FP32 V-cycle + {coarse} + "
                         f"FP64 outer GCR, 16 CGNR post-smoothing steps, coarsest GCR to 0.03, 600 setup iterations, "
                         f"setup amortised over "
                         f"{nrhs} Gaussian RHS",
@@ -158,7 +163,7 @@ def gen_inputs(nrhs, rank=0):
     return U, bs
 
 
-def mixed_params(G):
+def mixed_params(G, coarsen="unsquared"):
     """Mixed precision: FP32 fine V-cycle, BF16 coarse stencil, FP64 outer GCR;
     16 CGNR post-smoothing steps, coarsest GCR to 0.03 (at most 128
     iterations) and 600 setup relaxation iterations: the fastest of measured
@@ -172,6 +177,7 @@ def mixed_params(G):
     p.coarsest_tol = 0.03
     p.coarsest_maxiter = 128
     p.setup_iters0 = 600
+    p.coarsen = 1 if coarsen == "squared" else 0
     return p
 
 
@@ -217,7 +223,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "DWF MG solve time to |r|/|b|<=1e-10 (oracle, host cores)",
             "value": v, "unit": "s/solve", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.nrhs),
+            "data": "synthetic", "config": workload_config(args.nrhs, args.coarsen),
             "cpu_baseline": {"value": v, "unit": "s/solve", "cores": cores, "kind": "oracle",
                              "sample": f"{n} applications of the oracle's FP64 fine operator at 16^3x32x16 per "
                                        f"step, scaled by {applies:.0f} fine applications per solve"},
@@ -246,7 +252,7 @@ def profile_modes(args):
         canon = torch.from_numpy(bs).cuda()
         b = torch.empty(ctx.field_elems * args.nrhs, dtype=torch.complex128, device="cuda")
         G.dwf_pack(ctx.h, b, canon, G.DWF_F64, args.nrhs)
-        G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], mixed_params(G))
+        G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], mixed_params(G, args.coarsen))
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
@@ -288,7 +294,7 @@ def main():
     G.dwf_pack(ctx.h, b, canon, G.DWF_F64, nrhs)
     x = torch.zeros_like(b)
     del canon
-    p = mixed_params(G)
+    p = mixed_params(G, args.coarsen)
 
     def step(stats_out=None):
         G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p)
@@ -354,7 +360,7 @@ def main():
             "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+bf16 (fp64 outer)", "data": "synthetic (seeded heatbath links, Gaussian sources)",
-            "config": workload_config(nrhs), "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
+            "config": workload_config(nrhs, args.coarsen), "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
             "solve_stats": stats[-1] if stats else None,
             "kernel_time_ms": {k: {"launches": v[0], "fields": units[k], "ms": v[1]} for k, v in prof.items()}}
 

@@ -102,6 +102,12 @@ typedef struct {
     int cycle;              /* S2 on intermediate levels (3+ levels): 0 = GCR preconditioned by the next
                                V-cycle (a K-cycle), 1 = two V-cycles, x = V(b), x += V(b - A x): the
                                W-cycle of Sec. 2 (0) */
+    int coarsen;            /* coarse operator: 0 = R D P, the 9-point stencil of the unsquared
+                               operator; 1 = P^+ D^+ D P, the coarsened squared operator that
+                               Sec. 4 uses (33-point stencil: offset 0, the 8 one-hop offsets and
+                               the 24 two-hop diagonals; two levels only, every block extent >= 2;
+                               the V-cycle restricts D^+ r instead of r, and several right-hand
+                               sides are solved one after another) (0) */
 } mg_params;
 
 typedef struct {
@@ -185,7 +191,11 @@ dwf_status mg_level_info(dwf_ctx *ctx, int level, int dims_out[4], int *ncomp_ou
 dwf_status mg_get_vectors(dwf_ctx *ctx, int level, void *out_dev);
 
 /* Copy the coarse stencil of level l >= 1: Y[site][d][k][m], d = 0 self,
- * 1+2mu (+mu), 2+2mu (-mu), FP64 (Sec. 2: the coarse operator R A P). */
+ * 1+2mu (+mu), 2+2mu (-mu), FP64 (Sec. 2: the coarse operator R A P).  With
+ * coarsen = 1 the stencil has 33 points: d as above for d < 9, then
+ * d = 9 + 4 p + 2 a + b for the diagonal +-mu +-nu, p the rank of (mu, nu) in
+ * (0,1), (0,2), (0,3), (1,2), (1,3), (2,3), a = 1 for -mu, b = 1 for -nu
+ * (out holds V * 33 * n * n complex numbers). */
 dwf_status mg_get_coarse_links(dwf_ctx *ctx, int level, void *out_dev);
 
 /* coarse_out (level l+1) = R fine_in (level l);  fine_out = P coarse_in. */
@@ -193,7 +203,8 @@ dwf_status mg_restrict(dwf_ctx *ctx, int level, void *coarse_out_dev, const void
 dwf_status mg_prolong(dwf_ctx *ctx, int level, void *fine_out_dev, const void *coarse_in_dev);
 
 /* out = A_l in (or A_l^+ in) with the coarse stencil of level l >= 1 in the
- * level's link precision; prec = DWF_F64 or DWF_F32 for the fields. */
+ * level's link precision; prec = DWF_F64 or DWF_F32 for the fields.  The
+ * squared operator's stencil (coarsen = 1) is Hermitian: dagger is ignored. */
 dwf_status mg_coarse_apply(dwf_ctx *ctx, int level, void *out_dev, const void *in_dev, int dagger, dwf_prec prec);
 
 /* x = S2(R A P, b) on the coarsest level (Sec. 2, third step of the

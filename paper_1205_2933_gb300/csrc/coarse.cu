@@ -48,7 +48,7 @@ __device__ __forceinline__ int64_t shift_site(const Geom &g, int64_t site, int m
     return site_index(g, c);
 }
 
-template <typename R, typename LT, int NV, bool DAG>
+template <typename R, typename LT, int NV, bool DAG, int NPTS>
 __global__ void __launch_bounds__(256) coarse_apply_kernel(C<R> *__restrict__ y, const C<R> *__restrict__ x,
                                                            const LT *__restrict__ Y, Geom g,
                                                            const int *__restrict__ nbr) {
@@ -61,17 +61,18 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(C<R> *__restrict__ y,
     const int k = (int)(i - site * NV);
     C<R> acc = mk<R>(0, 0);
 #pragma unroll 1
-    for (int d = 0; d < 9; ++d) {
+    for (int d = 0; d < NPTS; ++d) {
         int64_t other = site;
         // table entry 2 mu: +mu, 2 mu + 1: -mu; D^+ reads the opposite neighbour
-        if (d > 0) other = nbr[site * 8 + (DAG ? ((d - 1) ^ 1) : (d - 1))];
+        // (9 points only: the 33-point stencil is Hermitian)
+        if (d > 0) other = nbr[site * (NPTS - 1) + (DAG ? ((d - 1) ^ 1) : (d - 1))];
         const C<R> *xv = x + other * NV;
         if (!DAG) {
-            const int64_t row = ((site * 9 + d) * NV + k) * NV;
+            const int64_t row = ((site * NPTS + d) * NV + k) * NV;
 #pragma unroll 8
             for (int l = 0; l < NV; ++l) cfma(acc, LinkRead<LT>::template get<R>(Y, row + l), xv[l]);
         } else {
-            const int64_t base = (other * 9 + d) * NV * NV + k;
+            const int64_t base = (other * NPTS + d) * NV * NV + k;
 #pragma unroll 8
             for (int l = 0; l < NV; ++l) cfmac(acc, LinkRead<LT>::template get<R>(Y, base + (int64_t)l * NV), xv[l]);
         }
@@ -108,6 +109,40 @@ __device__ __forceinline__ void face_site(const FaceMap &m, int64_t xc, int mu, 
     }
     site = (((int64_t)(c[3] * m.b[3] + o[3]) * m.L[2] + (c[2] * m.b[2] + o[2])) * m.L[1] + (c[1] * m.b[1] + o[1])) *
                m.L[0] + (c[0] * m.b[0] + o[0]);
+}
+
+// The hop of the fine D from x = site (fifth coordinate s) to x + dir*mu,
+// -1/2 (1 -+ gamma_mu) U q(x +- mu) with the antiperiodic sign in t.
+template <typename R>
+__device__ __forceinline__ void fine_face_hop(C<R> acc12[12], const C<R> *ql, const C<R> *U, const Geom &g, int Ls,
+                                              int64_t site, int s, int mu, int dir) {
+    int c[4];
+    site_coords(g, site, c);
+    int cc[4] = {c[0], c[1], c[2], c[3]};
+    cc[mu] += dir;
+    bool wrap = (cc[mu] == g.L[mu] || cc[mu] < 0);
+    if (cc[mu] == g.L[mu]) cc[mu] = 0;
+    if (cc[mu] < 0) cc[mu] = g.L[mu] - 1;
+    int64_t nb = site_index(g, cc);
+    R coef = (mu == 3 && g.ap && wrap) ? R(0.5) : R(-0.5);
+    for (int e = 0; e < 12; ++e) acc12[e] = mk<R>(0, 0);
+    C<R> lk[9];
+    LinkIO<R>::load(U, dir > 0 ? site : nb, mu, lk);
+    if (dir > 0) {
+        switch (mu) {
+            case 0: hop<0, false, R>(acc12, ql, nb, Ls, s, lk, -1, coef); break;
+            case 1: hop<1, false, R>(acc12, ql, nb, Ls, s, lk, -1, coef); break;
+            case 2: hop<2, false, R>(acc12, ql, nb, Ls, s, lk, -1, coef); break;
+            default: hop<3, false, R>(acc12, ql, nb, Ls, s, lk, -1, coef); break;
+        }
+    } else {
+        switch (mu) {
+            case 0: hop<0, true, R>(acc12, ql, nb, Ls, s, lk, +1, coef); break;
+            case 1: hop<1, true, R>(acc12, ql, nb, Ls, s, lk, +1, coef); break;
+            case 2: hop<2, true, R>(acc12, ql, nb, Ls, s, lk, +1, coef); break;
+            default: hop<3, true, R>(acc12, ql, nb, Ls, s, lk, +1, coef); break;
+        }
+    }
 }
 
 // F[xc][dd][k][l], dd = 2*mu + (dir < 0): block-face contributions of one hop.
@@ -149,34 +184,8 @@ __global__ void __launch_bounds__(256) face_kernel(double2 *__restrict__ F, cons
             const C<R> *ql = Q + (int64_t)l * m.nelem;
             if (FINE) {
                 for (int e = 0; e < 12; ++e) a[e] = ql[(site * 12 + e) * m.Ls + s];
-                int c[4];
-                site_coords(g, site, c);
-                int cc[4] = {c[0], c[1], c[2], c[3]};
-                cc[mu] += dir;
-                bool wrap = (cc[mu] == g.L[mu] || cc[mu] < 0);
-                if (cc[mu] == g.L[mu]) cc[mu] = 0;
-                if (cc[mu] < 0) cc[mu] = g.L[mu] - 1;
-                int64_t nb = site_index(g, cc);
-                R coef = (mu == 3 && g.ap && wrap) ? R(0.5) : R(-0.5);
                 C<R> acc12[12];
-                for (int e = 0; e < 12; ++e) acc12[e] = mk<R>(0, 0);
-                C<R> lk[9];
-                LinkIO<R>::load(U, dir > 0 ? site : nb, mu, lk);
-                if (dir > 0) {
-                    switch (mu) {
-                        case 0: hop<0, false, R>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
-                        case 1: hop<1, false, R>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
-                        case 2: hop<2, false, R>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
-                        default: hop<3, false, R>(acc12, ql, nb, m.Ls, s, lk, -1, coef); break;
-                    }
-                } else {
-                    switch (mu) {
-                        case 0: hop<0, true, R>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
-                        case 1: hop<1, true, R>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
-                        case 2: hop<2, true, R>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
-                        default: hop<3, true, R>(acc12, ql, nb, m.Ls, s, lk, +1, coef); break;
-                    }
-                }
+                fine_face_hop<R>(acc12, ql, U, g, m.Ls, site, s, mu, dir);
                 for (int e = 0; e < 12; ++e) h[e] = acc12[e];
             } else {
                 for (int e = 0; e < run; ++e) a[e] = ql[site * run + e];
@@ -267,8 +276,9 @@ void coarse_apply_t(dwf_ctx *c, const Level &L, C<R> *y, const C<R> *x, const LT
     DWF_REQUIRE(nbrt, DWF_ESTATE, "coarse level without a neighbour table");
     dim3 grid((unsigned)((g.V * n + 255) / 256), (unsigned)nrhs);
 #define CK(NV)                                                                                               \
-    if (dag) coarse_apply_kernel<R, LT, NV, true><<<grid, 256, 0, c->stream>>>(y, x, Y, g, nbrt);            \
-    else coarse_apply_kernel<R, LT, NV, false><<<grid, 256, 0, c->stream>>>(y, x, Y, g, nbrt)
+    if (L.npts == 33) coarse_apply_kernel<R, LT, NV, false, 33><<<grid, 256, 0, c->stream>>>(y, x, Y, g, nbrt); \
+    else if (dag) coarse_apply_kernel<R, LT, NV, true, 9><<<grid, 256, 0, c->stream>>>(y, x, Y, g, nbrt);    \
+    else coarse_apply_kernel<R, LT, NV, false, 9><<<grid, 256, 0, c->stream>>>(y, x, Y, g, nbrt)
     NV_DISPATCH2(n, CK);
 #undef CK
     DWF_CHECK_LAUNCH();
@@ -287,7 +297,7 @@ template <typename R> void coarse_apply(dwf_ctx *c, const Level &L, C<R> *y, con
 }
 
 void convert_coarse_links(dwf_ctx *c, Level &L) {
-    int64_t n = L.lg.g.V * 9 * (int64_t)L.lg.ncomp * L.lg.ncomp;
+    int64_t n = L.lg.g.V * L.npts * (int64_t)L.lg.ncomp * L.lg.ncomp;
     unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)c->sm_count * 16);
     if (L.yprec == DWF_F32) {
         if (L.Y32.bytes < sizeof(float2) * n) L.Y32.alloc(sizeof(float2) * n);
@@ -348,6 +358,308 @@ template <typename R> void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, co
     DWF_CHECK_LAUNCH();
     convert_coarse_links(c, Lc);
 }
+
+// ---- the squared operator's coarse stencil (Sec. 4) -----------------------
+//
+// P^+ D^+ D P as 33 dense n x n blocks per coarse site.  D q_l splits by
+// where its terms read q_l: T_0 (diagonal, fifth-dimension hops, hops inside
+// the block of x) and T_sigma for the 8 hops x -> x + dir mu that leave the
+// block (sigma = 1 + 2 mu for dir = +1, 2 + 2 mu for dir = -1, supported on
+// the block's last resp. first layer in mu).  On block b'', D applied to the
+// basis piece of block b' = b'' + sigma is T_sigma there, so
+//   Y[b''+sigma1][sigma2 - sigma1][k][l] += <T_{sigma1,k}, T_{sigma2,l}>_{b''}
+// summed over b'' and the 73 pairs (sigma1, sigma2) whose supports meet
+// (the pairs +mu/-mu never do when every block extent is >= 2).
+
+namespace {
+
+constexpr int SQ_PAIRS = 73;
+
+struct PairTable {
+    int s1[SQ_PAIRS], s2[SQ_PAIRS], d[SQ_PAIRS];  // source offsets (0..8) and stencil index (0..32)
+};
+
+void sigma_vec(int sg, int v[4]) {
+    for (int i = 0; i < 4; ++i) v[i] = 0;
+    if (sg > 0) v[(sg - 1) >> 1] = ((sg - 1) & 1) ? -1 : +1;
+}
+
+PairTable make_pairs() {
+    int off[33][4];
+    squared_offsets(off);
+    PairTable t;
+    int n = 0;
+    for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 9; ++b) {
+            int va[4], vb[4], dv[4];
+            sigma_vec(a, va);
+            sigma_vec(b, vb);
+            for (int i = 0; i < 4; ++i) dv[i] = vb[i] - va[i];
+            int idx = -1;
+            for (int d = 0; d < 33 && idx < 0; ++d)
+                if (off[d][0] == dv[0] && off[d][1] == dv[1] && off[d][2] == dv[2] && off[d][3] == dv[3]) idx = d;
+            if (idx < 0) continue;  // +-2 mu
+            t.s1[n] = a;
+            t.s2[n] = b;
+            t.d[n] = idx;
+            ++n;
+        }
+    if (n != SQ_PAIRS) throw Error{DWF_ECUDA, "squared coarse stencil: pair table size"};
+    return t;
+}
+
+// face element f = i*Ls + s of block xc for (mu, dir): its fine site
+__device__ __forceinline__ int64_t face_elem_site(const FaceMap &m, int64_t xc, int mu, int dir, int64_t f, int &s) {
+    int64_t site;
+    face_site(m, xc, mu, dir, f, site, s);
+    return site;
+}
+
+// Hf[dd][l][xc][(i*12 + e)*Ls + s] = T_{1+dd}(q_l) at face element (i, s) of block xc
+template <typename R>
+__global__ void __launch_bounds__(256) face_terms_kernel(C<R> *__restrict__ Hf, const C<R> *__restrict__ Q,
+                                                         const C<R> *__restrict__ U, Geom g, FaceMap m, int64_t nc,
+                                                         int64_t nfe) {
+    const int64_t xc = blockIdx.x;
+    const int dd = blockIdx.y, l = blockIdx.z;
+    const int mu = dd >> 1, dir = (dd & 1) ? -1 : +1;
+    const int nv = gridDim.z;
+    const int64_t nface = (int64_t)m.b[0] * m.b[1] * m.b[2] * m.b[3] / m.b[mu] * m.Ls;
+    const C<R> *ql = Q + (int64_t)l * m.nelem;
+    C<R> *out = Hf + (((int64_t)dd * nv + l) * nc + xc) * nfe;
+    for (int64_t f = threadIdx.x; f < nface; f += blockDim.x) {
+        int s;
+        const int64_t site = face_elem_site(m, xc, mu, dir, f, s);
+        C<R> h[12];
+        fine_face_hop<R>(h, ql, U, g, m.Ls, site, s, mu, dir);
+        const int64_t i = f / m.Ls;
+        for (int e = 0; e < 12; ++e) out[(i * 12 + e) * m.Ls + s] = h[e];
+    }
+}
+
+// W_l -= T_{1+dd}(q_l) on the face of every block (one dd per launch: no two
+// threads of a launch touch the same element)
+template <typename R>
+__global__ void __launch_bounds__(256) subtract_faces_kernel(C<R> *__restrict__ W, const C<R> *__restrict__ Hf,
+                                                             FaceMap m, int64_t nc, int64_t nfe, int dd) {
+    const int64_t xc = blockIdx.x;
+    const int l = blockIdx.y, nv = gridDim.y;
+    const int mu = dd >> 1, dir = (dd & 1) ? -1 : +1;
+    const int64_t nface = (int64_t)m.b[0] * m.b[1] * m.b[2] * m.b[3] / m.b[mu] * m.Ls;
+    const C<R> *h = Hf + (((int64_t)dd * nv + l) * nc + xc) * nfe;
+    C<R> *w = W + (int64_t)l * m.nelem;
+    for (int64_t f = threadIdx.x; f < nface; f += blockDim.x) {
+        int s;
+        const int64_t site = face_elem_site(m, xc, mu, dir, f, s);
+        const int64_t i = f / m.Ls;
+        for (int e = 0; e < 12; ++e) {
+            C<R> v = w[(site * 12 + e) * m.Ls + s];
+            const C<R> t = h[(i * 12 + e) * m.Ls + s];
+            v.x -= t.x;
+            v.y -= t.y;
+            w[(site * 12 + e) * m.Ls + s] = v;
+        }
+    }
+}
+
+// T_sg(q_l) at block-local coordinates o, component e, fifth coordinate s of block xc
+template <typename R>
+__device__ __forceinline__ C<R> t_value(const C<R> *W, const C<R> *Hf, const FaceMap &m, int64_t xc, const int xcc[4],
+                                        int sg, int l, int nv, int64_t nc, int64_t nfe, const int o[4], int e, int s) {
+    if (sg == 0) {
+        const int64_t site = (((int64_t)(xcc[3] * m.b[3] + o[3]) * m.L[2] + (xcc[2] * m.b[2] + o[2])) * m.L[1] +
+                              (xcc[1] * m.b[1] + o[1])) * m.L[0] + (xcc[0] * m.b[0] + o[0]);
+        return W[(int64_t)l * m.nelem + (site * 12 + e) * m.Ls + s];
+    }
+    const int dd = sg - 1, mu = dd >> 1;
+    int64_t i = 0, stride = 1;
+    for (int nu = 0; nu < 4; ++nu)
+        if (nu != mu) {
+            i += o[nu] * stride;
+            stride *= m.b[nu];
+        }
+    return Hf[(((int64_t)dd * nv + l) * nc + xc) * nfe + (i * 12 + e) * m.Ls + s];
+}
+
+// Gp[xc][p][k][l] = <T_{s1(p),k}, T_{s2(p),l}> over the sites of block xc
+// where both are supported (FP64 accumulation across chunks of ch elements)
+template <int NV, typename R>
+__global__ void __launch_bounds__(256) pair_gram_kernel(double2 *__restrict__ Gp, const C<R> *__restrict__ W,
+                                                        const C<R> *__restrict__ Hf, FaceMap m, PairTable pt,
+                                                        int64_t nc, int64_t nfe, int ch) {
+    extern __shared__ unsigned char sm_raw[];
+    C<R> *sA = reinterpret_cast<C<R> *>(sm_raw);  // [NV][ch]
+    C<R> *sB = sA + (size_t)NV * ch;              // [NV][ch]
+    const int64_t xc = blockIdx.x;
+    const int p = blockIdx.y;
+    const int s1 = pt.s1[p], s2 = pt.s2[p];
+    int xcc[4];
+    {
+        int64_t t = xc;
+        xcc[0] = (int)(t % m.Lc[0]); t /= m.Lc[0];
+        xcc[1] = (int)(t % m.Lc[1]); t /= m.Lc[1];
+        xcc[2] = (int)(t % m.Lc[2]); xcc[3] = (int)(t / m.Lc[2]);
+    }
+    // the region where both pieces live: a box inside the block
+    int lo[4], ext[4];
+    for (int nu = 0; nu < 4; ++nu) { lo[nu] = 0; ext[nu] = m.b[nu]; }
+    const int sgs[2] = {s1, s2};
+    for (int j = 0; j < 2; ++j)
+        if (const int sg = sgs[j]; sg > 0) {
+            const int mu = (sg - 1) >> 1;
+            lo[mu] = ((sg - 1) & 1) ? 0 : m.b[mu] - 1;
+            ext[mu] = 1;
+        }
+    const int64_t nel = (int64_t)ext[0] * ext[1] * ext[2] * ext[3] * 12 * m.Ls;
+    constexpr int NP = NV * NV;
+    constexpr int PPT = (NP + 255) / 256;
+    double2 acc[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) acc[q] = make_double2(0, 0);
+    for (int64_t e0 = 0; e0 < nel; e0 += ch) {
+        for (int item = threadIdx.x; item < NV * ch; item += blockDim.x) {
+            const int l = item / ch, fl = item - l * ch;
+            const int64_t r = e0 + fl;
+            C<R> a = mk<R>(0, 0), b = mk<R>(0, 0);
+            if (r < nel) {
+                const int s = (int)(r % m.Ls);
+                int64_t t = r / m.Ls;
+                const int e = (int)(t % 12);
+                t /= 12;
+                int o[4];
+                for (int nu = 0; nu < 4; ++nu) {
+                    o[nu] = lo[nu] + (int)(t % ext[nu]);
+                    t /= ext[nu];
+                }
+                a = t_value<R>(W, Hf, m, xc, xcc, s1, l, NV, nc, nfe, o, e, s);
+                b = t_value<R>(W, Hf, m, xc, xcc, s2, l, NV, nc, nfe, o, e, s);
+            }
+            sA[(size_t)l * ch + fl] = a;
+            sB[(size_t)l * ch + fl] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            const int pp = threadIdx.x + q * 256;
+            if (pp < NP) {
+                const int k = pp / NV, l = pp - k * NV;
+                const C<R> *ak = sA + (size_t)k * ch, *bl = sB + (size_t)l * ch;
+                C<R> sum = mk<R>(0, 0);
+                for (int e = 0; e < ch; ++e) cfmac(sum, ak[e], bl[e]);
+                acc[q].x += (double)sum.x;
+                acc[q].y += (double)sum.y;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int pp = threadIdx.x + q * 256;
+        if (pp < NP) Gp[((int64_t)xc * SQ_PAIRS + p) * NP + pp] = acc[q];
+    }
+}
+
+// Y[b][d][k][l] = sum over pairs p with stencil index d of Gp[b - sigma1(p)][p][k][l],
+// pairs in a fixed order (deterministic)
+__global__ void assemble_squared_kernel(double2 *__restrict__ Y, const double2 *__restrict__ Gp, Geom gc,
+                                        PairTable pt, int nv) {
+    const int64_t np = (int64_t)nv * nv;
+    const int64_t total = gc.V * 33 * np;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / (33 * np);
+        const int d = (int)((i / np) % 33);
+        const int64_t kk = i % np;
+        int cb[4];
+        site_coords(gc, b, cb);
+        double2 y = make_double2(0, 0);
+        for (int p = 0; p < SQ_PAIRS; ++p) {
+            if (pt.d[p] != d) continue;
+            int cc[4] = {cb[0], cb[1], cb[2], cb[3]};
+            const int sg = pt.s1[p];
+            if (sg > 0) {
+                const int mu = (sg - 1) >> 1, dir = ((sg - 1) & 1) ? -1 : +1;
+                cc[mu] = (cc[mu] - dir + gc.L[mu]) % gc.L[mu];
+            }
+            const double2 g = Gp[(site_index(gc, cc) * SQ_PAIRS + p) * np + kk];
+            y.x += g.x;
+            y.y += g.y;
+        }
+        Y[i] = y;
+    }
+}
+
+}  // namespace
+
+void squared_offsets(int off[33][4]) {
+    for (int d = 0; d < 33; ++d)
+        for (int i = 0; i < 4; ++i) off[d][i] = 0;
+    for (int mu = 0; mu < 4; ++mu) {
+        off[1 + 2 * mu][mu] = +1;
+        off[2 + 2 * mu][mu] = -1;
+    }
+    static const int pairs[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+    for (int p = 0; p < 6; ++p)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                const int d = 9 + 4 * p + 2 * a + b;
+                off[d][pairs[p][0]] = a ? -1 : +1;
+                off[d][pairs[p][1]] = b ? -1 : +1;
+            }
+}
+
+template <typename R> void build_squared_coarse(dwf_ctx *c, Level &L, Level &Lc, const C<R> *Q, C<R> *W) {
+    DWF_REQUIRE(L.index == 0, DWF_EINVAL, "the squared coarsening starts from the fine lattice");
+    for (int i = 0; i < 4; ++i)
+        DWF_REQUIRE(L.block[i] >= 2, DWF_EINVAL, "the squared coarse stencil needs block extents >= 2");
+    const int nv = L.nv;
+    const int64_t nc = Lc.lg.g.V, np = (int64_t)nv * nv;
+    dslash(c, W, Q, false, nv);  // W_l = D q_l
+    FaceMap m;
+    for (int i = 0; i < 4; ++i) {
+        m.L[i] = L.lg.g.L[i];
+        m.b[i] = L.block[i];
+        m.Lc[i] = m.L[i] / m.b[i];
+    }
+    m.Ls = L.lg.g.Ls;
+    m.run = 12;
+    m.nelem = L.lg.nelem;
+    int64_t nfmax = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        nfmax = std::max<int64_t>(nfmax, (int64_t)m.b[0] * m.b[1] * m.b[2] * m.b[3] / m.b[mu]);
+    const int64_t nfe = nfmax * 12 * m.Ls;
+    DevBuf Hf(sizeof(C<R>) * (size_t)(8 * nv * nc * nfe));
+    const C<R> *Ul = std::is_same<R, double>::value ? (const C<R> *)c->U64.p : (const C<R> *)c->U32.p;
+    face_terms_kernel<R><<<dim3((unsigned)nc, 8, (unsigned)nv), 256, 0, c->stream>>>(Hf.as<C<R>>(), Q, Ul, L.lg.g, m,
+                                                                                      nc, nfe);
+    DWF_CHECK_LAUNCH();
+    for (int dd = 0; dd < 8; ++dd) {
+        subtract_faces_kernel<R><<<dim3((unsigned)nc, (unsigned)nv), 256, 0, c->stream>>>(W, Hf.as<C<R>>(), m, nc, nfe,
+                                                                                          dd);
+        DWF_CHECK_LAUNCH();
+    }
+    DevBuf Gp(sizeof(double2) * (size_t)(nc * SQ_PAIRS * np));
+    const PairTable pt = make_pairs();
+    const int ch = (int)std::max<int64_t>(1, (46 * 1024) / ((int64_t)2 * nv * sizeof(C<R>)));
+    const size_t smem = (size_t)2 * nv * ch * sizeof(C<R>);
+    dim3 grid((unsigned)nc, SQ_PAIRS);
+#define PK(NV) \
+    pair_gram_kernel<NV, R><<<grid, 256, smem, c->stream>>>(Gp.as<double2>(), W, Hf.as<C<R>>(), m, pt, nc, nfe, ch)
+    NV_DISPATCH2(nv, PK);
+#undef PK
+    DWF_CHECK_LAUNCH();
+    Lc.npts = 33;
+    const size_t yb = sizeof(double2) * (size_t)(nc * 33 * np);
+    if (Lc.Y64.bytes < yb) Lc.Y64.alloc(yb);
+    const unsigned blocks = (unsigned)std::min<int64_t>((nc * 33 * np + 255) / 256, (int64_t)c->sm_count * 16);
+    assemble_squared_kernel<<<blocks, 256, 0, c->stream>>>(Lc.Y64.as<double2>(), Gp.as<double2>(), Lc.lg.g, pt, nv);
+    DWF_CHECK_LAUNCH();
+    convert_coarse_links(c, Lc);
+    // Hf and Gp are freed on return: finish with them first
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+template void build_squared_coarse<double>(dwf_ctx *, Level &, Level &, const double2 *, double2 *);
+template void build_squared_coarse<float>(dwf_ctx *, Level &, Level &, const float2 *, float2 *);
 
 template void build_coarse_from<double>(dwf_ctx *, Level &, Level &, const double2 *, double2 *);
 template void build_coarse_from<float>(dwf_ctx *, Level &, Level &, const float2 *, float2 *);

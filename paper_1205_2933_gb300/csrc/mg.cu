@@ -259,17 +259,28 @@ template <typename R> class Runner {
     // One V-cycle for A_l x = b (Sec. 2):
     //   x1 = S1^nu1(A, b); b2 = R(b - A x1); x2 = S2(R A P, b2);
     //   b3 = b - A(P x2 + x1); x = x1 + P x2 + S3^nu3(A, b3)
+    // With the squared coarsening (Sec. 4) the coarse problem is that of the
+    // normal equations: b2 = R D^+ (b - A x1).
     void vcycle(int l, T *x, const T *b) {
         const int64_t N = n(l);
         Level &L = mg.lev[l];
         const mg_params &p = mg.p;
         T *res = ws(l, 4), *sm = ws(l, 5), *b3 = ws(l, 6);
         T *b2 = ws(l + 1, 8), *x2 = ws(l + 1, 9);
+        const bool squared = (l == 0 && p.coarsen == 1);
         if (p.nu_pre > 0) {
             cgnr(l, x, b, p.nu_pre, true, false);
             apply(l, res, x, false);
             cxpay<T>(c, res, make_double2(-1.0, 0.0), b, N);  // b - A x1
-            restrict_any(L, b2, res, l);
+            if (squared) {
+                apply(l, sm, res, true);
+                restrict_any(L, b2, sm, l);
+            } else {
+                restrict_any(L, b2, res, l);
+            }
+        } else if (squared) {
+            apply(l, sm, b, true);
+            restrict_any(L, b2, sm, l);
         } else {
             restrict_any(L, b2, b, l);
         }
@@ -357,7 +368,8 @@ template <typename R> class Runner {
         if (!block_orthonormalise<R>(c, L, Q(l)))
             throw Error{DWF_EBREAKDOWN, "block Gram-Schmidt met linearly dependent near-null vectors"};
         DevBuf W(sizeof(T) * N * L.nv);
-        build_coarse_from<R>(c, L, mg.lev[l + 1], Q(l), W.as<T>());
+        if (mg.p.coarsen == 1) build_squared_coarse<R>(c, L, mg.lev[l + 1], Q(l), W.as<T>());
+        else build_coarse_from<R>(c, L, mg.lev[l + 1], Q(l), W.as<T>());
         if (std::is_same<R, float>::value && mg.p.basis_prec == DWF_F16) {
             if (L.Q16.bytes < sizeof(__half2) * N * L.nv) L.Q16.alloc(sizeof(__half2) * N * L.nv);
             basis_to_half(c, L.Q16.as<__half2>(), L.Q32.as<float2>(), N * L.nv);
@@ -1012,7 +1024,7 @@ bool batch_on() {
 
 template <typename R> bool batch_eligible(const MGState &mg, int nrhs) {
     return std::is_same<R, float>::value && nrhs > 1 && batch_on() && mg.nlevels == 2 && mg.p.nu_pre == 0 &&
-           mg.p.outer_restart <= 32;
+           mg.p.outer_restart <= 32 && mg.p.coarsen == 0;
 }
 
 // Right-hand sides per batch: at most 32, and no more than the free device
@@ -1137,7 +1149,11 @@ dwf_status mg_setup_impl(dwf_ctx *c, int levels, const int *nvec, const int (*bl
         Level &Lc = mg->lev[l + 1];
         bool ok = nv_supported(nvec[l]) && (!p.split || nvec[l] % 2 == 0);
         for (int i = 0; i < 4; ++i) ok = ok && block[l][i] >= 1 && L.lg.g.L[i] % block[l][i] == 0;
-        if (!ok) {
+        if (p.coarsen == 1) {
+            ok = ok && levels == 2;
+            for (int i = 0; i < 4; ++i) ok = ok && block[l][i] >= 2;
+        }
+        if (!ok || (p.coarsen != 0 && p.coarsen != 1)) {
             delete mg;
             return DWF_EINVAL;
         }
@@ -1153,18 +1169,22 @@ dwf_status mg_setup_impl(dwf_ctx *c, int levels, const int *nvec, const int (*bl
         Lc.lg.nelem = Lc.lg.g.V * nvec[l];
         dwf_prec yp = p.coarse_prec[l];
         Lc.yprec = (yp == DWF_F32 || yp == DWF_BF16 || yp == DWF_F16) ? yp : DWF_F64;
-        // periodic neighbours of every coarse site, once (the coarse kernels read them)
+        // periodic neighbours of every coarse site, once (the coarse kernels
+        // read them): the offsets of the stencil after the site itself
+        Lc.npts = p.coarsen == 1 ? 33 : 9;
+        int off[33][4];
+        squared_offsets(off);  // its first 9 offsets are the 9-point stencil's
         const Geom &g = Lc.lg.g;
-        std::vector<int> tab((size_t)g.V * 8);
+        const int nn = Lc.npts - 1;
+        std::vector<int> tab((size_t)g.V * nn);
         for (int64_t site = 0; site < g.V; ++site) {
             int co[4];
             site_coords(g, site, co);
-            for (int mu = 0; mu < 4; ++mu)
-                for (int dir = 0; dir < 2; ++dir) {
-                    int cc[4] = {co[0], co[1], co[2], co[3]};
-                    cc[mu] = (cc[mu] + (dir == 0 ? 1 : g.L[mu] - 1)) % g.L[mu];
-                    tab[(size_t)site * 8 + 2 * mu + dir] = (int)site_index(g, cc);
-                }
+            for (int d = 1; d <= nn; ++d) {
+                int cc[4];
+                for (int mu = 0; mu < 4; ++mu) cc[mu] = (co[mu] + off[d][mu] + g.L[mu]) % g.L[mu];
+                tab[(size_t)site * nn + d - 1] = (int)site_index(g, cc);
+            }
         }
         try {
             Lc.nbr.alloc(sizeof(int) * tab.size());
@@ -1240,7 +1260,7 @@ void mg_get_vectors_impl(dwf_ctx *c, int level, double2 *out) {
 void mg_get_coarse_links_impl(dwf_ctx *c, int level, double2 *out) {
     MGState &mg = need_mg(c, level, 1, MAX_LEVELS);
     const Level &L = mg.lev[level];
-    DWF_CUDA(cudaMemcpyAsync(out, L.Y64.p, sizeof(double2) * L.lg.g.V * 9 * L.lg.ncomp * L.lg.ncomp,
+    DWF_CUDA(cudaMemcpyAsync(out, L.Y64.p, sizeof(double2) * L.lg.g.V * L.npts * L.lg.ncomp * L.lg.ncomp,
                              cudaMemcpyDeviceToDevice, c->stream));
 }
 

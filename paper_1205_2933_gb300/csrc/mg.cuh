@@ -30,7 +30,9 @@ struct Level {
     DevBuf Q64, Q32;       // nv block-orthonormalised fields of this level
     DevBuf Q16;            // FP16 copy used by the FP32 V-cycle's transfers (basis_prec = F16)
     DevBuf vec64;          // nadapt adaptive vectors (unsplit, normalised), FP64
-    // coarse operator of this level (levels >= 1): [V][9][n][n] complex
+    // coarse operator of this level (levels >= 1): [V][npts][n][n] complex,
+    // npts = 9 for R A P, 33 for the squared operator's P^+ D^+ D P
+    int npts = 9;
     DevBuf Y64, Y32, Y16;  // Y16 holds bf16 or fp16 pairs per coarse_prec
     dwf_prec yprec = DWF_F64;
     // block reductions scratch: [Vc][nv][nv] complex FP64
@@ -38,7 +40,8 @@ struct Level {
     DevBuf info;           // int per coarse site: Cholesky status
     // fused coarsest-level GCR: contiguous direction vectors, partial sums, counter
     DevBuf cgZ, cgW, cgPart, cgIters;
-    // coarse levels: neighbour table int [V][8], entry 2 mu (+mu) and 2 mu + 1 (-mu)
+    // coarse levels: neighbour table int [V][npts - 1], entry 2 mu (+mu) and
+    // 2 mu + 1 (-mu), then (33 points) the diagonals in stencil order
     DevBuf nbr;
 };
 
@@ -111,9 +114,19 @@ template <typename R> void coarse_apply(dwf_ctx *c, const Level &L, C<R> *y, con
 template <typename R> void build_coarse_from(dwf_ctx *c, Level &L, Level &Lc, const C<R> *Q, C<R> *W);
 // refresh the reduced-precision copies of Y on level l
 void convert_coarse_links(dwf_ctx *c, Level &L);
+// ---- coarse_sq.cu ---- the squared operator's coarse stencil (Sec. 4):
+// Y of level Lc = 1 as [V][33][n][n] = P^+ D^+ D P from the fine basis Q
+// (W: scratch of L.nv fine fields, same precision)
+template <typename R> void build_squared_coarse(dwf_ctx *c, Level &L, Level &Lc, const C<R> *Q, C<R> *W);
+// coarse offsets of the 33-point stencil: off[d][mu] in {-1, 0, 1}
+void squared_offsets(int off[33][4]);
 
 // ---- coarse_gcr.cu ----  fused coarsest-level GCR (one cooperative launch)
 bool coarse_gcr_fused_ok(const Level &L, int restart);
+// ---- coarse_gcr_sq.cu ---- the same kernel on the 33-point stencil
+template <typename R>
+void coarse_gcr_launch_squared(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, C<R> *r, C<R> *Z, C<R> *W,
+                               double2 *part, int *iters, double tol, int maxiter, int restart);
 // ---- coarse_gcr_batch.cu ---- the same solve for nb <= 16 right-hand sides in lockstep
 bool coarse_gcr_batch_ok(const Level &L, int restart, int nb);
 size_t coarse_gcr_batch_part_bytes(dwf_ctx *c);

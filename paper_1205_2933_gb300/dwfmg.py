@@ -40,6 +40,7 @@ class mg_params(ctypes.Structure):
         ("basis_prec", ctypes.c_int),
         ("seed", ctypes.c_uint32),
         ("cycle", ctypes.c_int),
+        ("coarsen", ctypes.c_int),
     ]
 
 

@@ -36,6 +36,7 @@ def _oracle_params(nvec, block, gpu_params):
             "setup_sweep_tol", "split")
     return OM.MGParams(nvec=tuple(nvec), block=tuple(tuple(b) for b in block),
                        cycle="W" if gpu_params.cycle == 1 else "K",
+                       coarsen="squared" if gpu_params.coarsen == 1 else "unsquared",
                        **{k: getattr(gpu_params, k) for k in keys})
 
 
@@ -433,4 +434,89 @@ def test_full_size_batched_solve_sampled_residual(G):
     dx = oracle.DWF(U, dims, Ls, 1.8, mf).D_sites(x0, idx5).reshape(len(idx5), 12)
     b0 = bs[0].reshape(Ls * V, 12)[idx5]
     assert np.abs(dx - b0).max() <= 2e-10 * np.linalg.norm(bs[0])
+    ctx.close()
+
+
+# ---- the coarsened squared operator P^+ D^+ D P (Sec. 4) ------------------
+
+SQ = dict(dims=(4, 6, 4, 4), Ls=4, mf=0.05, nvec=[8], block=[(2, 2, 2, 2)])        # coarse 2x3x2x2
+SQ_ANISO = dict(dims=(4, 4, 6, 4), Ls=3, mf=0.05, nvec=[6], block=[(2, 2, 3, 2)])  # coarse 2^4
+
+
+@pytest.mark.parametrize("cfg", [SQ, SQ_ANISO], ids=["2x3x2x2", "aniso"])
+@pytest.mark.parametrize("sp", [0, 1], ids=["f64", "f32"])
+def test_squared_coarse_operator_parity(G, cfg, sp):
+    """The GPU's 33-point P^+ D^+ D P from the same start vectors equals the
+    oracle's (FP64 build to rounding; FP32 products with FP64 sums to 1e-5)."""
+    c = Case(G, **cfg, setup_iters0=0, setup_sweeps=0, coarsen=1, smoother_prec=sp)
+    from gpu_util import rel_max
+    d, n = G.mg_level_info(c.ctx.h, 1)
+    Vc = int(np.prod(d))
+    Y = torch.empty(Vc * 33 * n * n, dtype=torch.complex128, device="cuda")
+    G.mg_get_coarse_links(c.ctx.h, 1, Y)
+    Yref = c.mg.levels[1].op.Y.reshape(Vc, 33, n, n)
+    assert rel_max(Y.cpu().numpy().reshape(Vc, 33, n, n), Yref) < (1e-12 if sp == 0 else 1e-5)
+    c.close()
+
+
+def test_squared_coarse_apply_solve_and_vcycle(G):
+    """FP64: the 33-point stencil apply (dagger ignored: Hermitian), the fused
+    coarsest GCR on it and one V-cycle, each against the oracle."""
+    c = Case(G, **SQ, setup_iters0=10, setup_sweeps=0, coarsen=1, coarsest_tol=1e-8, coarsest_maxiter=400,
+             coarse_restart=32)
+    from gpu_util import to_internal, to_canonical, rel_norm
+    A = c.mg.levels[1].op
+    d, n = G.mg_level_info(c.ctx.h, 1)
+    cv = I.gauss_complex((int(np.prod(d)) * n,), 34, 50)
+    ct = torch.from_numpy(cv).cuda()
+    for dag in (0, 1):
+        yt = torch.empty_like(ct)
+        G.mg_coarse_apply(c.ctx.h, 1, yt, ct, dag, G.DWF_F64)
+        ref = A.apply(cv.reshape(A.shape)).ravel()
+        assert np.abs(yt.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
+    xt = torch.empty_like(ct)
+    G.mg_coarse_solve(c.ctx.h, 1, xt, ct)
+    res = OM.norm(cv.reshape(A.shape) - A.apply(xt.cpu().numpy().reshape(A.shape))) / OM.norm(cv)
+    assert res < 2e-8, res
+    b = I.gaussian_source(c.dims, c.Ls, 35)
+    bt = to_internal(c.ctx, b)
+    xv = torch.empty_like(bt)
+    G.mg_vcycle(c.ctx.h, xv, bt)
+    got = to_canonical(c.ctx, xv, b.shape)
+    ref = c.mg.vcycle(0, b.reshape(c.op.shape)).reshape(b.shape)
+    assert rel_norm(got, ref) < 1e-7
+    c.close()
+
+
+@pytest.mark.parametrize("sp,cp", [(0, 0), (1, 2)], ids=["f64", "f32-bf16"])
+def test_squared_solve_matches_oracle(G, sp, cp):
+    """Whole solves with the squared coarsening: FP64 (and FP32 V-cycle with
+    BF16 coarse links, two right-hand sides one after another) reach the
+    oracle's solution with true residual <= 1e-10."""
+    c = Case(G, **SQ, setup_sweeps=0, coarsen=1, smoother_prec=sp, coarse_prec=[cp])
+    from gpu_util import to_internal, to_canonical, rel_norm
+    bs = np.stack([I.gaussian_source(c.dims, c.Ls, 80 + i) for i in range(2)])
+    bt = to_internal(c.ctx, bs, nrhs=2)
+    xt = torch.zeros_like(bt)
+    st = G.mg_solve(c.ctx.h, bt, xt, 1e-10, nrhs=2)
+    assert st.true_res <= 1e-10
+    x = to_canonical(c.ctx, xt, bs.shape, nrhs=2)
+    for i in range(2):
+        assert rel_norm(x[i], _oracle_solution(c, bs[i])) < 1e-8
+    if sp == 0:
+        xo, info = OM.mg_solve(c.mg, bs[0].reshape(c.op.shape), tol=1e-10, restart=c.p.outer_restart)
+        assert info.converged
+    c.close()
+
+
+def test_squared_setup_rejects_unsupported(G):
+    """Three levels, or a block of extent 1, are refused with the squared coarsening."""
+    from gpu_util import ctx_for
+    dims, Ls = (4, 4, 4, 4), 4
+    ctx = ctx_for(I.epsilon_links(dims, 0.3, 1), dims, Ls, 1.8, 0.1)
+    p = _params(G, setup_iters0=0, coarsen=1)
+    with pytest.raises(G.DWFError):
+        G.mg_setup(ctx.h, 3, [8, 8], [(2, 2, 2, 2), (2, 1, 1, 1)], p)
+    with pytest.raises(G.DWFError):
+        G.mg_setup(ctx.h, 2, [8], [(1, 2, 2, 2)], p)
     ctx.close()
