@@ -32,6 +32,8 @@ Parity pins (tests/test_oracle_*.py):
   CoarseOp.apply          equals the dense coarse matrix
   gcr / mr / cgnr         dense-LU solutions, residual monotonicity
   vcycle                  Galerkin orthogonality of the coarse correction
+  (with oracle/dwf2d.py)  the same code runs the 2D U(1) toy of Sec. 3; its
+                          whole solves are pinned by dense LU
   adaptive_setup          near-null Rayleigh quotients fall with sweeps
   mg_solve                dense-LU solution on tiny lattices, true residual
 Nothing here is "parity unpinned".
@@ -359,7 +361,7 @@ def squared_coarse_operator(op, T: Transfer) -> SquaredCoarseOp:
     apart).  With every block extent >= 2, h_{+mu} (last layer of the block
     in mu) and h_{-mu} (first layer) never share a site, so the offsets +-2 mu
     vanish and 33 offsets remain."""
-    if min(T.block) < 2:
+    if min(T.block[mu] for mu in getattr(op, "hop_dirs", range(4))) < 2:
         raise ValueError("the squared coarse stencil needs block extents >= 2")
     Nv = T.Nv
     Xc, Yc, Zc, Tc = T.cdims
@@ -583,7 +585,9 @@ def gamma_halves(op, v):
     """(1 + Gamma)/2 v and (1 - Gamma)/2 v.  On the fine level Gamma = gamma_5 R_5
     (spin sign +,+,-,- and s -> Ls-1-s); on a coarse level built from split
     vectors Gamma is +1 on even and -1 on odd coarse components."""
-    if isinstance(op, FineOp):
+    if hasattr(op, "gamma5r5"):
+        g = op.gamma5r5(v)
+    elif isinstance(op, FineOp):
         g = v[::-1].copy()
         g[..., 6:] *= -1
     else:

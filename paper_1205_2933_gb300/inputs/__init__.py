@@ -34,6 +34,7 @@ STREAM_NULLVEC = 4
 STREAM_Z2 = 5
 STREAM_GAUGE_TRANSFORM = 6
 STREAM_NETWORK = 7
+STREAM_U1 = 8
 
 
 def build(force: bool = False) -> pathlib.Path:
@@ -234,3 +235,60 @@ def random_gauge_transform(dims, seed: int) -> np.ndarray:
     """Random SU(3) matrix g(x) per 4D site, shape (T,Z,Y,X,3,3)."""
     V = int(np.prod(dims))
     return random_su3(V, seed, STREAM_GAUGE_TRANSFORM).reshape(lattice_shape(dims) + (3, 3))
+
+
+# ---------------------------------------------------------------------------
+# Two-dimensional compact U(1) gauge fields (the paper's 20^2 x 8 toy, Sec. 3)
+# ---------------------------------------------------------------------------
+
+def u1_plaquette_angles(theta: np.ndarray) -> np.ndarray:
+    """theta_P(x) = theta_x(x) + theta_y(x + x^) - theta_x(x + y^) - theta_y(x);
+    theta shape (2, Y, X), mu = 0 is x (axis 1 of each slice), 1 is y."""
+    tx, ty = theta[0], theta[1]
+    return tx + np.roll(ty, -1, axis=1) - np.roll(tx, -1, axis=0) - ty
+
+
+def u1_plaquette(theta: np.ndarray) -> float:
+    """Average of cos theta_P over the lattice."""
+    return float(np.mean(np.cos(u1_plaquette_angles(theta))))
+
+
+def u1_links_2d(dims2, beta: float, sweeps: int, seed: int, hits: int = 2, delta: float = 1.5,
+                trace: list | None = None) -> np.ndarray:
+    """Quenched 2D U(1) link angles, Wilson action beta * sum_P (1 - cos theta_P),
+    by Metropolis from a hot start: per sweep, for each direction and
+    checkerboard parity, `hits` proposals theta' = theta + delta (2u - 1)
+    accepted with probability min(1, exp(-dS)).  Links of one direction and
+    parity share no plaquette, so they are updated together.  Uniforms come
+    from the counter-based generator (stream STREAM_U1, one block of draws per
+    sweep).  Returns theta, shape (2, Y, X); `trace`, when given, receives the
+    average plaquette after every sweep."""
+    X, Y = int(dims2[0]), int(dims2[1])
+    V = X * Y
+    theta = (2.0 * uniform(2 * V, seed, STREAM_U1, 0xFFFF, 0) - 1.0).reshape(2, Y, X) * np.pi
+    yy, xx = np.meshgrid(np.arange(Y), np.arange(X), indexing="ij")
+    parity = (xx + yy) % 2
+    nk = 2 * 2 * int(hits) * 2
+    for sw in range(int(sweeps)):
+        u = uniform(nk * V, seed, STREAM_U1, sw, 0).reshape(nk, Y, X)
+        for mu in range(2):
+            for par in range(2):
+                mask = parity == par
+                for h in range(int(hits)):
+                    k = ((mu * 2 + par) * int(hits) + h) * 2
+                    new = theta.copy()
+                    new[mu] = np.where(mask, theta[mu] + delta * (2.0 * u[k] - 1.0), theta[mu])
+                    d = np.cos(u1_plaquette_angles(theta)) - np.cos(u1_plaquette_angles(new))
+                    # the two plaquettes holding link (mu, x): P(x) and P(x - nu^), nu the other direction
+                    dS = beta * (d + np.roll(d, 1, axis=(0 if mu == 0 else 1)))
+                    take = mask & (u[k + 1] < np.exp(-np.minimum(dS, 50.0)))
+                    theta[mu] = np.where(take, new[mu], theta[mu])
+        if trace is not None:
+            trace.append(u1_plaquette(theta))
+    return np.angle(np.exp(1j * theta))
+
+
+def u1_gauss_field(dims2, Ls: int, n: int, seed: int, stream: int = STREAM_SOURCE) -> np.ndarray:
+    """n Gaussian 2D-toy fermion fields, shape (n, Ls, 1, 1, Y, X, 2)."""
+    X, Y = int(dims2[0]), int(dims2[1])
+    return gauss_complex((int(n), int(Ls), 1, 1, Y, X, 2), seed, stream, 1.0)
