@@ -292,3 +292,19 @@ def u1_gauss_field(dims2, Ls: int, n: int, seed: int, stream: int = STREAM_SOURC
     """n Gaussian 2D-toy fermion fields, shape (n, Ls, 1, 1, Y, X, 2)."""
     X, Y = int(dims2[0]), int(dims2[1])
     return gauss_complex((int(n), int(Ls), 1, 1, Y, X, 2), seed, stream, 1.0)
+
+
+def embed_u1_2d(theta: np.ndarray, charges=(1, 1, -2)):
+    """The 2D U(1) field theta (2, Y, X) as SU(3) links of a 4D lattice
+    X x 1 x 1 x Y: the 2D x-links on mu = 0, the 2D y-links on mu = 3 (so that
+    the antiperiodic direction is the 4D t), identity on mu = 1, 2; colour c
+    carries charge charges[c] (diag(e^{i q_c theta}), det 1 for charges summing
+    to 0).  Returns (links (Y, 1, 1, X, 4, 3, 3), dims (X, 1, 1, Y))."""
+    Y, X = theta.shape[1], theta.shape[2]
+    U = np.zeros((Y, 1, 1, X, 4, 3, 3), dtype=np.complex128)
+    for mu in (1, 2):
+        U[..., mu, :, :] = np.eye(3)
+    for c, q in enumerate(charges):
+        U[:, 0, 0, :, 0, c, c] = np.exp(1j * q * theta[0])
+        U[:, 0, 0, :, 3, c, c] = np.exp(1j * q * theta[1])
+    return U, (X, 1, 1, Y)

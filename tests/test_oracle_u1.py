@@ -118,3 +118,25 @@ def test_fig2_mass_independence():
     assert cg[0.01] >= 1.3 * cg[0.10], cg
     assert mgc[0.01] <= 1.3 * mgc[0.10], mgc
     assert mgc[0.01] < 0.6 * cg[0.01], (mgc, cg)
+
+
+def test_4d_embedding_reproduces_the_2d_operator():
+    """The 2D toy on the four-dimensional operator: on X x 1 x 1 x Y with the
+    U(1) angles on diagonal SU(3) links of charges (1, 1, -2) and unit links in
+    the two extent-1 directions, those directions' hops add -2 to the
+    diagonal (5 - M5 -> 3 - M5) and the 4D spectrum is, per colour, twice the
+    2D spectrum for links e^{i q theta} (gamma_x, gamma_t and gamma_5 act on
+    two copies of the 2D spin space, the second with sigma_3 -> -sigma_3,
+    which R_5 maps back)."""
+    import oracle
+    dims2, Ls, M5, mf = (4, 4), 2, 1.0, 0.1
+    th = I.u1_links_2d(dims2, 1.0, 5, 21)
+    U, dims4 = I.embed_u1_2d(th)
+    d4 = oracle.DWF(U, dims4, Ls, M5, mf)
+    ev4 = np.linalg.eigvals(M.dense_matrix(d4.D, d4.shape))
+    ref = []
+    for q in (1, 1, -2):
+        op = DWF2D(q * th, dims2, Ls, M5, mf)
+        e = np.linalg.eigvals(M.dense_matrix(op.apply, op.shape))
+        ref += [e, e]
+    assert _match(ev4, np.concatenate(ref)) < 1e-10
