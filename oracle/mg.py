@@ -360,8 +360,12 @@ def squared_coarse_operator(op, T: Transfer) -> SquaredCoarseOp:
     offsets that reach the same site of a small periodic coarse lattice stay
     apart).  With every block extent >= 2, h_{+mu} (last layer of the block
     in mu) and h_{-mu} (first layer) never share a site, so the offsets +-2 mu
-    vanish and 33 offsets remain."""
-    if min(T.block[mu] for mu in getattr(op, "hop_dirs", range(4))) < 2:
+    vanish and 33 offsets remain.  A direction of lattice extent 1 (a lower-
+    dimensional lattice embedded in four dimensions) has hops that return to
+    the same site: they read inside the block and belong to h_0."""
+    dirs = getattr(op, "hop_dirs", range(4))
+    local = [mu for mu in range(4) if op.dims[mu] == 1]
+    if min([T.block[mu] for mu in dirs if mu not in local] or [2]) < 2:
         raise ValueError("the squared coarse stencil needs block extents >= 2")
     Nv = T.Nv
     Xc, Yc, Zc, Tc = T.cdims
@@ -373,6 +377,9 @@ def squared_coarse_operator(op, T: Transfer) -> SquaredCoarseOp:
         op.count -= 1  # construction applies are not solver cost
         for mu in range(4):
             for d in (+1, -1):
+                if mu in local:
+                    pieces[CoarseOp.dir_index(mu, d), l] = 0.0
+                    continue
                 h = op.hop(q, mu, d) * crossing_mask(op.dims, T.block, op.S, mu, d)
                 rest = rest - h
                 pieces[CoarseOp.dir_index(mu, d), l] = to_blocks(h, T.dims, T.block)

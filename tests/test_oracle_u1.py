@@ -140,3 +140,26 @@ def test_4d_embedding_reproduces_the_2d_operator():
         e = np.linalg.eigvals(M.dense_matrix(op.apply, op.shape))
         ref += [e, e]
     assert _match(ev4, np.concatenate(ref)) < 1e-10
+
+
+def test_squared_coarsening_of_the_embedded_toy():
+    """On the embedded lattice X x 1 x 1 x Y the hops along the extent-1
+    directions stay on the site: the squared coarse stencil (blocks of extent
+    1 there) still equals (D P)^+ (D P) by brute force, and the multigrid
+    with it reaches the dense-LU solution."""
+    import oracle
+    dims2, Ls = (8, 8), 2
+    U, dims4 = I.embed_u1_2d(I.u1_links_2d(dims2, 3.0, 20, 31))
+    op = M.FineOp(oracle.DWF(U, dims4, Ls, 1.0, 0.05))
+    rv = I.random_vectors(2, dims4, Ls, 32).reshape((2,) + op.shape)
+    vecs = np.stack([h for v in rv for h in M.gamma_halves(op, v)])
+    T = M.Transfer(vecs, op.dims, (4, 1, 1, 4))
+    C = M.squared_coarse_operator(op, T)
+    dense = M.squared_coarse_bruteforce(op, T)
+    assert np.abs(M.dense_matrix(C.apply, T.cshape) - dense).max() < 1e-13 * np.abs(dense).max()
+    b = I.gaussian_source(dims4, Ls, 33).reshape(op.shape)
+    mg = M.adaptive_setup(op, M.MGParams(nvec=(8,), block=((4, 1, 1, 4),), coarsen="squared"),
+                          [I.random_vectors(4, dims4, Ls, 34).reshape((4,) + op.shape)])
+    x, info = M.mg_solve(mg, b, tol=1e-10)
+    xs = np.linalg.solve(M.dense_matrix(op.apply, op.shape), b.ravel()).reshape(b.shape)
+    assert info.converged and M.norm(x - xs) / M.norm(xs) < 1e-8
