@@ -11,10 +11,14 @@ Contents
                  Cohen-Brower-Clark-Osborn, "Multigrid Algorithms for
                  Domain-Wall Fermions").
   mg.py        : blocking, block Gram-Schmidt, restrictor/prolongator, the
-                 Galerkin coarse operator R D P (brute force and by
-                 stencil), GCR / MR / CGNR, the V-cycle and the adaptive
-                 setup, in numpy FP64.
-Parity status of every function is listed in mg.py's header.
+                 Galerkin coarse operator R D P and the squared operator's
+                 P^+ D^+ D P (brute force and by stencil), GCR / MR / CGNR,
+                 the V-cycle and the adaptive setup, in numpy FP64.
+  net.py       : the learned near-null proposal's network, loss and gradient.
+  eig.py       : the low-mode diagnostic (dense eigenpairs of D^+ D, coarse
+                 overlaps).
+  dwf2d.py     : the 2D U(1) domain-wall operator of the toy model (Sec. 3).
+Parity status of every function is listed in each module's header.
 """
 from __future__ import annotations
 
