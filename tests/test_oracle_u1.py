@@ -95,14 +95,15 @@ def test_fig2_mass_independence():
     """Sec. 3, Fig. 2: on a 20^2 x 8 quenched U(1) lattice with 16 near-null
     vectors and 4^2 x 8 blocks, CG on the normal equations slows down as the
     mass falls while the multigrid (the paper's squared-operator coarsening)
-    needs about the same number of fine applications at every mass.  Lattice:
+    needs about the same number of fine applications at every mass, while the
+    coarse operator itself becomes ill-conditioned as the mass falls.  Lattice:
     beta = 6, 200 Metropolis sweeps (topological charge -6), M5 = 1,
     antiperiodic in y; masses 0.10 and 0.01."""
     dims2, Ls = (20, 20), 8
     th = I.u1_links_2d(dims2, 6.0, 200, 11)
     b = I.u1_gauss_field(dims2, Ls, 1, 12)[0]
     rv = I.u1_gauss_field(dims2, Ls, 8, 13, I.STREAM_NULLVEC)
-    cg, mgc = {}, {}
+    cg, mgc, lmin = {}, {}, {}
     for mf in (0.10, 0.01):
         op = DWF2D(th, dims2, Ls, 1.0, mf)
         _, info = M.cgnr(op.apply, op.apply_dag, b, tol=1e-10, maxiter=20000)
@@ -115,7 +116,11 @@ def test_fig2_mass_independence():
         x, info = M.mg_solve(mg, b, tol=1e-10, maxiter=300)
         assert info.converged and M.norm(b - op.apply(x)) / M.norm(b) <= 1e-10
         mgc[mf] = op.count - 1
+        # Fig. 2 (right): the coarse level does slow down; its smallest eigenvalue falls like m_f^2
+        A = mg.levels[1].op
+        lmin[mf] = np.linalg.eigvalsh(M.dense_matrix(A.apply, A.shape))[0]
     assert cg[0.01] >= 1.3 * cg[0.10], cg
+    assert lmin[0.01] < 0.02 * lmin[0.10], lmin
     assert mgc[0.01] <= 1.3 * mgc[0.10], mgc
     assert mgc[0.01] < 0.6 * cg[0.01], (mgc, cg)
 
