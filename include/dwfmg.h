@@ -105,7 +105,8 @@ typedef struct {
     int coarsen;            /* coarse operator: 0 = R D P, the 9-point stencil of the unsquared
                                operator; 1 = P^+ D^+ D P, the coarsened squared operator that
                                Sec. 4 uses (33-point stencil: offset 0, the 8 one-hop offsets and
-                               the 24 two-hop diagonals; two levels only, every block extent >= 2;
+                               the 24 two-hop diagonals; two levels only, every block extent >= 2
+                               except along lattice directions of extent 1;
                                the V-cycle restricts D^+ r instead of r, and several right-hand
                                sides are solved one after another) (0) */
 } mg_params;

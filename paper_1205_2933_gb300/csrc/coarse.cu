@@ -609,8 +609,11 @@ void squared_offsets(int off[33][4]) {
 
 template <typename R> void build_squared_coarse(dwf_ctx *c, Level &L, Level &Lc, const C<R> *Q, C<R> *W) {
     DWF_REQUIRE(L.index == 0, DWF_EINVAL, "the squared coarsening starts from the fine lattice");
+    // a direction of lattice extent 1 hops back onto the same site: its terms
+    // stay in T_0 (block-internal) and its pieces T_sigma are zero
     for (int i = 0; i < 4; ++i)
-        DWF_REQUIRE(L.block[i] >= 2, DWF_EINVAL, "the squared coarse stencil needs block extents >= 2");
+        DWF_REQUIRE(L.block[i] >= 2 || L.lg.g.L[i] == 1, DWF_EINVAL,
+                    "the squared coarse stencil needs block extents >= 2");
     const int nv = L.nv;
     const int64_t nc = Lc.lg.g.V, np = (int64_t)nv * nv;
     dslash(c, W, Q, false, nv);  // W_l = D q_l
@@ -633,6 +636,11 @@ template <typename R> void build_squared_coarse(dwf_ctx *c, Level &L, Level &Lc,
                                                                                       nc, nfe);
     DWF_CHECK_LAUNCH();
     for (int dd = 0; dd < 8; ++dd) {
+        if (m.L[dd >> 1] == 1) {
+            DWF_CUDA(cudaMemsetAsync(Hf.as<C<R>>() + (size_t)dd * nv * nc * nfe, 0,
+                                     sizeof(C<R>) * (size_t)nv * nc * nfe, c->stream));
+            continue;
+        }
         subtract_faces_kernel<R><<<dim3((unsigned)nc, (unsigned)nv), 256, 0, c->stream>>>(W, Hf.as<C<R>>(), m, nc, nfe,
                                                                                           dd);
         DWF_CHECK_LAUNCH();

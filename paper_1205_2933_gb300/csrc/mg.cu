@@ -1151,7 +1151,7 @@ dwf_status mg_setup_impl(dwf_ctx *c, int levels, const int *nvec, const int (*bl
         for (int i = 0; i < 4; ++i) ok = ok && block[l][i] >= 1 && L.lg.g.L[i] % block[l][i] == 0;
         if (p.coarsen == 1) {
             ok = ok && levels == 2;
-            for (int i = 0; i < 4; ++i) ok = ok && block[l][i] >= 2;
+            for (int i = 0; i < 4; ++i) ok = ok && (block[l][i] >= 2 || L.lg.g.L[i] == 1);
         }
         if (!ok || (p.coarsen != 0 && p.coarsen != 1)) {
             delete mg;
