@@ -46,12 +46,17 @@ NVEC = 24
 BLOCK = (4, 4, 4, 4)
 NRHS = 12
 TOL = 1e-10
+METRIC = "DWF MG solve time to |r|/|b|\u226410^-10 (chosen vs FP64 plain); Dslash HBM GB/s"
 FINE_BYTES_F32 = 204   # algorithmic bytes per 5D site of the FP32 Dslash
 # dram__bytes_read.sum + dram__bytes_write.sum of one one-field launch of the
-# current FP32 Dslash kernel from an ncu capture (profiles/); None until the
-# kernel as it stands has been captured
-DSLASH_TRAFFIC_PER_FIELD = 411171840  # 239.68 MB read + 171.49 MB written (profiles/dslash_f32_pair_16x16x16x32_Ls16.md)
+# current FP32 Dslash kernel from an ncu capture; None until the kernel as it
+# stands has been captured
+DSLASH_TRAFFIC_PER_FIELD = 411171840  # 239.68 MB read + 171.49 MB written
 FINE_BYTES_F64 = 408
+# fine-operator applications per solve of this workload on the GPU path (FP32 and
+# FP64, the setup's amortised over 12 right-hand sides), from the timed bench steps;
+# the reference arm scales its timed oracle applications by it
+APPLIES_PER_SOLVE = 3724
 
 
 def parse():
@@ -66,7 +71,11 @@ def parse():
                          "(33-point, Sec. 4; right-hand sides solved one after another)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--plain", action="store_true", help="also time the plain FP64 method (1 solve)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--plain-nrhs", type=int, default=2,
+                    help="right-hand sides solved by the plain FP64 method (their solutions are the FP64 "
+                         "reference of the per-solve errors)")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="timed end-to-end steps (after one warm-up)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling mode: setup, then one solve inside cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--dslash-only", action="store_true",
@@ -195,10 +204,61 @@ def cpu_baseline_sample(U, b, seconds_target=15.0):
     for _ in range(n):
         dwf.D(b)
     per = (time.perf_counter() - t0) / n
-    import ctypes
+    return per, n, host_threads()
+
+
+def host_threads():
     threads = os.environ.get("OMP_NUM_THREADS")
-    cores = int(threads) if threads else os.cpu_count()
-    return per, n, cores
+    return int(threads) if threads else os.cpu_count()
+
+
+# The plain method's small case: 4^4 lattice, Ls = 8, M5 = 1.8, m_f = 0.1,
+# eps-random links (eps = 0.3, seed 1), Gaussian source (seed 2), 2-level
+# FP64 multigrid with 2^4 blocks, Nvec = 8, 3 inverse-iteration setup sweeps.
+SMALL_DIMS, SMALL_LS, SMALL_MF = (4, 4, 4, 4), 8, 0.1
+
+
+def small_case_oracle():
+    """Full setup + solve of the small plain-FP64 case by the oracle on the host
+    cores (measured, not extrapolated); returns (seconds, iterations, solution)."""
+    import oracle
+    from oracle import mg as OM
+    U = I.epsilon_links(SMALL_DIMS, 0.3, 1)
+    b = I.gaussian_source(SMALL_DIMS, SMALL_LS, 2)
+    rv = I.random_vectors(4, SMALL_DIMS, SMALL_LS, 3)
+    t0 = time.perf_counter()
+    op = OM.FineOp(oracle.DWF(U, SMALL_DIMS, SMALL_LS, M5, SMALL_MF))
+    prm = OM.MGParams(nvec=(8,), block=((2, 2, 2, 2),), setup_sweeps=3)
+    mg = OM.adaptive_setup(op, prm, [rv.reshape((4,) + op.shape)])
+    x, info = OM.mg_solve(mg, b.reshape(op.shape), tol=TOL, restart=20)
+    return time.perf_counter() - t0, info.iters, x.reshape(b.shape)
+
+
+def small_case_gpu(G, torch):
+    """The same small case through the library (CUDA events around setup + solve)."""
+    U = I.epsilon_links(SMALL_DIMS, 0.3, 1)
+    b = I.gaussian_source(SMALL_DIMS, SMALL_LS, 2)
+    rv = torch.from_numpy(I.random_vectors(4, SMALL_DIMS, SMALL_LS, 3)).cuda()
+    ctx = G.Context(SMALL_DIMS, SMALL_LS, M5, SMALL_MF, torch.from_numpy(U).cuda())
+    bt = torch.empty(ctx.field_elems, dtype=torch.complex128, device="cuda")
+    G.dwf_pack(ctx.h, bt, torch.from_numpy(b).cuda(), G.DWF_F64, 1)
+    p = G.mg_default_params()
+    p.setup_sweeps = 3
+    times = []
+    for _ in range(4):  # one warm-up, three timed
+        x = torch.zeros_like(bt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.mg_setup(ctx.h, 2, [8], [(2, 2, 2, 2)], p, rv)
+        st = G.mg_solve(ctx.h, bt, x, TOL)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    xc = torch.empty_like(bt)
+    G.dwf_unpack(ctx.h, xc, x, G.DWF_F64, 1)
+    torch.cuda.synchronize()
+    out = xc.cpu().numpy().reshape(b.shape)
+    ctx.close()
+    return statistics.median(times[1:]), st.iters, st.true_res, out
 
 
 def run_reference(args):
@@ -212,21 +272,27 @@ def run_reference(args):
     # cost of one solve in fine-operator applications, as measured on the GPU
     # path for this workload (FP64 + FP32 applications per solve, the setup's
     # amortised over the 12 right-hand sides)
-    applies = float(os.environ.get("DWF_APPLIES_PER_SOLVE", "3724"))
+    applies = float(os.environ.get("DWF_APPLIES_PER_SOLVE", str(APPLIES_PER_SOLVE)))
     times = []
     for _ in range(args.warmup):
-        cpu_baseline_sample(U, b, 3.0)
+        cpu_baseline_sample(U, b, 1.0)
+    n = cores = 0
     for _ in range(args.steps):
-        per, n, cores = cpu_baseline_sample(U, b, 10.0)
+        per, n, cores = cpu_baseline_sample(U, b, 5.0)
         times.append(per * applies)
     v = statistics.median(times)
-    line = {"impl": "reference", "metric": "DWF MG solve time to |r|/|b|<=1e-10 (oracle, host cores)",
+    t_small, it_small, _ = small_case_oracle()
+    line = {"impl": "reference", "metric": METRIC,
             "value": v, "unit": "s/solve", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.nrhs, args.coarsen),
             "cpu_baseline": {"value": v, "unit": "s/solve", "cores": cores, "kind": "oracle",
-                             "sample": f"{n} applications of the oracle's FP64 fine operator at 16^3x32x16 per "
-                                       f"step, scaled by {applies:.0f} fine applications per solve"},
+                             "method": "extrapolated",
+                             "sample": f"per step {n} applications of the oracle's FP64 fine operator at "
+                                       f"16^3x32x16, scaled by {applies:.0f} fine applications per solve "
+                                       f"(the GPU path's count for this workload, setup amortised)"},
+            "small_case": {"workload": "4^4x8 plain FP64 MG (Nvec 8, 2^4 blocks, 3 setup sweeps), m_f=0.1",
+                           "oracle_s": t_small, "oracle_iters": it_small, "kind": "measured"},
             "e2e": {"value": v, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -356,74 +422,116 @@ def main():
     # (the paper's cost unit, Sec. 3): all fields the FP32 and FP64 Dslash processed
     applies_per_solve = (units["dslash_f32"] + units["dslash_f64"]) / (nrhs * args.steps) or None
 
-    line = {"metric": "DWF MG solve time to |r|/|b|<=1e-10 (setup amortised over 12 RHS); Dslash HBM GB/s",
+    line = {"metric": METRIC,
             "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+bf16 (fp64 outer)", "data": "synthetic (seeded heatbath links, Gaussian sources)",
-            "config": workload_config(nrhs, args.coarsen), "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
-            "solve_stats": stats[-1] if stats else None,
+            "config": workload_config(nrhs, args.coarsen), "gpu_launches": int(launches), "clocks": clk,
+            "roofline": roof, "solve_stats": stats[-1] if stats else None,
+            "applies_per_solve": applies_per_solve,
             "kernel_time_ms": {k: {"launches": v[0], "fields": units[k], "ms": v[1]} for k, v in prof.items()}}
-
-    if args.plain and rank == 0:
-        line["plain_fp64"] = run_plain(G, torch, ctx, b, nrhs)
-    # the end-to-end leg builds its own context: free this one's device memory first
+    # the chosen solutions of the last timed step stay on the device for the error check
     ctx.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_plain:
+        line["plain_fp64"] = run_plain(G, torch, U, b, x, min(args.plain_nrhs, nrhs), value)
     del b, x
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_e2e:
-        line["e2e"] = run_e2e(G, torch, U, bs, p, nrhs)
+        line["e2e"] = run_e2e(G, torch, U, bs, p, nrhs, args.e2e_steps)
     if rank == 0 and not args.no_cpu_baseline:
         per, n, cores = cpu_baseline_sample(U, bs[0])
         if applies_per_solve:
             line["cpu_baseline"] = {"value": per * applies_per_solve, "unit": "s/solve", "cores": cores,
-                                    "kind": "oracle",
+                                    "kind": "oracle", "method": "extrapolated",
                                     "sample": f"{n} applications of the oracle's FP64 fine operator at 16^3x32x16, "
                                               f"scaled by the {applies_per_solve:.0f} fine applications per solve "
                                               f"(setup amortised) of the timed GPU steps (the paper's cost unit)"}
+        t_or, it_or, x_or = small_case_oracle()
+        t_gpu, it_gpu, res_gpu, x_gpu = small_case_gpu(G, torch)
+        line["small_case"] = {"workload": "4^4x8 plain FP64 MG (Nvec 8, 2^4 blocks, 3 setup sweeps), m_f=0.1, "
+                                          "full setup + solve",
+                              "oracle_s": t_or, "oracle_iters": it_or, "oracle_cores": host_threads(),
+                              "gpu_s": t_gpu, "gpu_iters": it_gpu, "gpu_true_res": res_gpu,
+                              "rel_diff_vs_oracle": float(np.linalg.norm(x_gpu - x_or) / np.linalg.norm(x_or)),
+                              "kind": "measured"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_e2e(G, torch, U, bs, p, nrhs):
-    """Same metric through the public API with host buffers: links and sources
-    copied from pinned host memory, solutions read back, inside the region."""
+def run_e2e(G, torch, U, bs, p, nrhs, steps):
+    """Same metric through the public API with host buffers: every step creates
+    the context from pinned host links, copies the canonical host sources to
+    the device, converts them to the internal layout, runs the setup and the
+    solves, converts the solutions back and copies them to pinned host memory.
+    One warm-up step, then the median of `steps` timed steps."""
     Uh = torch.from_numpy(U).pin_memory()
-    # sources in the internal layout on the host (pinned)
-    tmp = G.Context(DIMS, LS, M5, MF, Uh)
-    canon = torch.from_numpy(bs).cuda()
-    bi = torch.empty(tmp.field_elems * nrhs, dtype=torch.complex128, device="cuda")
-    G.dwf_pack(tmp.h, bi, canon, G.DWF_F64, nrhs)
-    bh = bi.cpu().pin_memory()
-    xh = torch.zeros_like(bh).pin_memory()
-    tmp.close()
-    del canon, bi
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ctx = G.Context(DIMS, LS, M5, MF, Uh)
-    G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p)
-    G.mg_solve(ctx.h, bh, xh, TOL, nrhs)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    ctx.close()
-    return {"value": dt / nrhs, "unit": "s/solve", "h2d_bytes_per_step": int(Uh.numel() * 16 + 2 * bh.numel() * 16),
+    bh = torch.from_numpy(bs).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    times = []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = G.Context(DIMS, LS, M5, MF, Uh)
+        bd = bh.to("cuda", non_blocking=True)
+        bi = torch.empty(ctx.field_elems * nrhs, dtype=torch.complex128, device="cuda")
+        G.dwf_pack(ctx.h, bi, bd, G.DWF_F64, nrhs)
+        xi = torch.zeros_like(bi)
+        G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p)
+        G.mg_solve(ctx.h, bi, xi, TOL, nrhs)
+        G.dwf_unpack(ctx.h, bd, xi, G.DWF_F64, nrhs)
+        xh.copy_(bd, non_blocking=True)
+        torch.cuda.synchronize()
+        if i > 0:
+            times.append(time.perf_counter() - t0)
+        ctx.close()
+        del bd, bi, xi
+        torch.cuda.empty_cache()
+    return {"value": statistics.median(times) / nrhs, "unit": "s/solve", "steps": steps,
+            "h2d_bytes_per_step": int(Uh.numel() * 16 + bh.numel() * 16),
             "d2h_bytes_per_step": int(xh.numel() * 16)}
 
 
-def run_plain(G, torch, ctx, b, nrhs):
-    """The plain FP64 method on the same lattice: setup + one solve."""
-    p = G.mg_default_params()
-    x = torch.zeros(ctx.field_elems, dtype=torch.complex128, device="cuda")
+def run_plain(G, torch, U, b, x_chosen, nplain, chosen_value):
+    """The plain method, FP64 throughout (smoother, V-cycle, coarse stencil and
+    coarsest solve), with the chosen configuration's solver parameters, on the
+    same lattice: one setup and nplain solves.  Its solutions are the FP64
+    reference for the chosen solutions' errors."""
+    ctx = G.Context(DIMS, LS, M5, MF, torch.from_numpy(U).cuda())
+    N = ctx.field_elems
+    p = mixed_params(G)
+    p.smoother_prec = G.DWF_F64
+    p.coarse_prec[0] = G.DWF_F64
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p)
-    t1 = time.perf_counter()
-    st = G.mg_solve(ctx.h, b[:ctx.field_elems].contiguous(), x, TOL, 1, check=False)
-    t2 = time.perf_counter()
-    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "per_solve_amortised_12": (t1 - t0) / 12 + (t2 - t1),
-            "stats": st.as_dict(), "status": st.status}
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    solves, errors, iters, res = [], [], [], []
+    for i in range(nplain):
+        bi = b[i * N:(i + 1) * N].contiguous()
+        xp = torch.zeros_like(bi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = G.mg_solve(ctx.h, bi, xp, TOL, 1, check=False)
+        torch.cuda.synchronize()
+        solves.append(time.perf_counter() - t0)
+        iters.append(st.iters)
+        res.append(st.true_res)
+        xc = x_chosen[i * N:(i + 1) * N]
+        errors.append(float(torch.linalg.vector_norm(xc - xp) / torch.linalg.vector_norm(xp)))
+    ctx.close()
+    per = t_setup / NRHS + statistics.mean(solves)
+    return {"setup_s": t_setup, "solve_s": solves, "iters": iters, "true_res": res,
+            "per_solve_amortised_12": per, "chosen_over_plain": chosen_value / per,
+            "speedup_vs_plain": per / chosen_value,
+            "chosen_rel_error_vs_fp64": errors,
+            "note": f"plain FP64 MG (same parameters, FP64 everywhere) on the first {nplain} sources; "
+                    f"the errors compare the chosen solutions of the last timed step with these FP64 solutions"}
 
 
 if __name__ == "__main__":

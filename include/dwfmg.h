@@ -223,10 +223,12 @@ dwf_status mg_coarse_solve(dwf_ctx *ctx, int level, void *x_dev, const void *b_d
  * an interface choice of this library.  It allocates nothing: all scratch of
  * the solver lives in one static device array of 8 MiB that every GPU
  * loading the library holds until the process exits.
- *   Limits: coarse_restart <= 16 and (1 + 2*coarse_restart) coarse vectors
- *   of the V-cycle precision must fit in 8 MiB (e.g. 512 sites x 24
- *   components in FP32 at restart 16: 3.3 MiB); larger requests return
- *   DWF_EINVAL.
+ *   Limits: coarse_restart <= 16, and
+ *     256 + roundup256(1632 * SM count) + (1 + 2*coarse_restart) * vector bytes
+ *   must not exceed 8 MiB, a vector being one coarse field in the V-cycle
+ *   precision (e.g. 512 sites x 24 components in FP32 at restart 16:
+ *   33 x 98,304 B = 3.1 MiB, plus 0.24 MiB of FP64 partial sums on 152
+ *   SMs); larger requests return DWF_EINVAL.
  *   Set-up: the first call on a device looks up the array's device address
  *   (the context's device must be current); make that first call before
  *   any stream capture.
@@ -234,7 +236,8 @@ dwf_status mg_coarse_solve(dwf_ctx *ctx, int level, void *x_dev, const void *b_d
  *   cleared at each call); calls that overlap on the GPU -- on different
  *   streams or contexts of the same device -- race and must be serialised
  *   by the caller.
- * x and b are device fields as for mg_coarse_solve.  Synchronous. */
+ * x and b are device fields as for mg_coarse_solve and must not overlap
+ * (DWF_EINVAL).  Synchronous. */
 dwf_status mg_coarse_solve_static(dwf_ctx *ctx, int level, void *x_dev, const void *b_dev);
 
 /* x = one fine-level V-cycle applied to b (Sec. 2), run in the smoother

@@ -12,7 +12,7 @@ Contents
                  Domain-Wall Fermions").
   mg.py        : blocking, block Gram-Schmidt, restrictor/prolongator, the
                  Galerkin coarse operator R D P and the squared operator's
-                 P^+ D^+ D P (brute force and by stencil), GCR / MR / CGNR,
+                 P^+ D^+ D P (brute force and by stencil), GCR / CGNR,
                  the V-cycle and the adaptive setup, in numpy FP64.
   net.py       : the learned near-null proposal's network, loss and gradient.
   eig.py       : the low-mode diagnostic (dense eigenpairs of D^+ D, coarse

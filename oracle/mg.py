@@ -30,7 +30,7 @@ Parity pins (tests/test_oracle_*.py):
                           its coarse correction is the least-squares fit of
                           the residual over range(P) (numpy lstsq)
   CoarseOp.apply          equals the dense coarse matrix
-  gcr / mr / cgnr         dense-LU solutions, residual monotonicity
+  gcr / cgnr              dense-LU solutions, residual monotonicity
   vcycle                  Galerkin orthogonality of the coarse correction
   (with oracle/dwf2d.py)  the same code runs the 2D U(1) toy of Sec. 3; its
                           whole solves are pinned by dense LU
@@ -503,21 +503,6 @@ def gcr(A: Callable, b, x0=None, tol=1e-10, maxiter=1000, restart=10,
     info.rel_res = rn / bnorm
     info.converged = rn / bnorm <= tol
     return x, info
-
-
-def mr(A: Callable, b, nsteps: int, omega: float = 1.0, x0=None):
-    """Minimal-residual relaxation: nsteps of x += omega*a*r, a = <A r, r>/<A r, A r>."""
-    x = np.zeros_like(b) if x0 is None else x0.copy()
-    r = b.copy() if x0 is None else b - A(x)
-    for _ in range(nsteps):
-        Ar = A(r)
-        den = vdot(Ar, Ar).real
-        if den == 0.0:
-            break
-        a = omega * vdot(Ar, r) / den
-        x = x + a * r
-        r = r - a * Ar
-    return x
 
 
 def cgnr(A: Callable, Adag: Callable, b, tol=1e-10, maxiter=100000, x0=None, info=None, check_every=1):

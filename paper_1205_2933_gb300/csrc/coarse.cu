@@ -4,7 +4,8 @@
 // direction index d = 0 (self), 1 + 2*mu (+mu), 2 + 2*mu (-mu); storage
 // Y[x][d][k][l].  One fine hop crosses at most one block face, so the
 // unsquared operator coarsens to nearest neighbours (Sec. 4 contrasts this
-// with the squared operator's 17-site coarse stencil).
+// with the squared operator's two-hop coarse stencil, which has 33 points
+// when every block extent is at least 2).
 //
 // Construction (FP64): with q_l the block-orthonormal basis,
 //   Y_{mu,dir}(x)[k][l] = sum over the sites of block x whose hop along

@@ -92,17 +92,20 @@ template <typename R>
 static void static_solve_t(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, double tol, int maxiter, int restart) {
     const int64_t N = L.lg.nelem;
     const size_t vec = sizeof(C<R>) * (size_t)N;
-    const size_t part = coarse_gcr_part_bytes(c);
-    const size_t need = vec * (1 + 2 * (size_t)restart) + part + 256;
+    // carve: [counter (256 B)] [partial sums, rounded up to 256 B] [r] [Z: restart vectors] [W: restart vectors]
+    const size_t off = 256 + (coarse_gcr_part_bytes(c) + 255) / 256 * 256;
     DWF_REQUIRE(restart >= 1 && restart <= STATIC_MAX_RESTART, DWF_EINVAL,
                 "static coarse solve: coarse_restart must be in 1..16");
-    DWF_REQUIRE(need <= STATIC_SCRATCH_BYTES, DWF_EINVAL,
-                "static coarse solve: (1 + 2*restart) coarse vectors exceed the 8 MiB static scratch");
+    DWF_REQUIRE(off + vec * (1 + 2 * (size_t)restart) <= STATIC_SCRATCH_BYTES, DWF_EINVAL,
+                "static coarse solve: (1 + 2*restart) coarse vectors and the partial sums exceed the 8 MiB static "
+                "scratch");
+    // the solver writes x = 0 before it reads b: the two must not overlap
+    const unsigned char *xb = (const unsigned char *)x, *bb = (const unsigned char *)b;
+    DWF_REQUIRE(xb + vec <= bb || bb + vec <= xb, DWF_EINVAL, "static coarse solve: x and b must not overlap");
     unsigned char *base = (unsigned char *)static_scratch(c);
-    // carve: [counter (256 B)] [partial sums] [r] [Z: restart vectors] [W: restart vectors]
     int *iters = (int *)base;
     double2 *partials = (double2 *)(base + 256);
-    C<R> *r = (C<R> *)(base + 256 + ((part + 255) / 256) * 256);
+    C<R> *r = (C<R> *)(base + off);
     C<R> *Z = r + N;
     C<R> *W = Z + (size_t)restart * N;
     zero_int_kernel<<<1, 1, 0, c->stream>>>(iters);  // the counter must start at zero

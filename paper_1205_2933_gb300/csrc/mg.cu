@@ -1,8 +1,10 @@
 // Multigrid solver orchestration: the V-cycle (Sec. 2), its CGNR smoother,
 // GCR on coarse levels (S2, recursing through the V-cycle of the next level),
 // the adaptive setup (Sec. 2: Krylov iterations on A x = 0 from random
-// vectors, then re-applying the multigrid to A x = 0) and the outer flexible
-// GCR (Sec. 3) with FP64 true residuals at every restart.
+// vectors, optionally followed by inverse-iteration sweeps that replace each
+// vector by an approximate solution of A x = v with the current multigrid)
+// and the outer flexible GCR (Sec. 3) with FP64 true residuals at every
+// restart.
 //
 // Precision: the V-cycle, its smoother and all inner Krylov vectors run in R
 // (double for the plain method, float for the mixed one); coarse stencils use

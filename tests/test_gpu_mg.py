@@ -43,10 +43,10 @@ def _oracle_params(nvec, block, gpu_params):
 class Case:
     """One lattice, its oracle, a GPU context and matching MG setups."""
 
-    def __init__(self, G, dims, Ls, mf, nvec, block, seed=1, eps=0.3, hb=False, **kw):
+    def __init__(self, G, dims, Ls, mf, nvec, block, seed=1, eps=0.3, hb=False, hb_sweeps=20, **kw):
         from gpu_util import ctx_for, to_internal
         self.G, self.dims, self.Ls, self.nvec, self.block = G, dims, Ls, nvec, block
-        self.U = I.heatbath_links(dims, 6.0, 20, seed) if hb else I.epsilon_links(dims, eps, seed)
+        self.U = I.heatbath_links(dims, 6.0, hb_sweeps, seed) if hb else I.epsilon_links(dims, eps, seed)
         self.dwf = oracle.DWF(self.U, dims, Ls, 1.8, mf)
         self.op = OM.FineOp(self.dwf)
         self.ctx = ctx_for(self.U, dims, Ls, 1.8, mf)
