@@ -124,21 +124,39 @@ typedef struct {
 /* Fill p with the defaults listed above. */
 void mg_default_params(mg_params *p);
 
-/* Create a context for one lattice.
- *   dims        X, Y, Z, T (each >= 1)
+/* Create a context for nlat independent lattices of the same Ls, M5 and mf
+ * (Sec. 1-2 state the problem D x = b for one lattice; a batch holds several
+ * such problems, e.g. lattices of uneven size, behind one handle).
+ *   nlat        number of lattices (1 <= nlat <= 64)
+ *   dims        nlat rows of X, Y, Z, T (each >= 1)
  *   Ls          fifth-dimension extent (1 <= Ls <= 128)
  *   M5, mf      domain-wall height and quark mass
- *   links       complex128 U[V][4][3][3], host or device; copied
+ *   links       nlat pointers, each complex128 U[V_i][4][3][3] of lattice i,
+ *               host or device; copied
  *   antiperiodic_t  nonzero: antiperiodic fermion boundary in t
  *   stream      cudaStream_t to run on (NULL = legacy default stream)
+ * With nlat > 1 every field argument of dwf_apply, dwf_pack, dwf_unpack,
+ * mg_setup (start) and mg_solve holds the lattices one after another: the
+ * nrhs fields of lattice 0, then those of lattice 1, ...  Each lattice runs
+ * on a stream the library creates (joined to `stream` before the call
+ * returns for the asynchronous calls); mg_setup and mg_solve drive the
+ * lattices concurrently from host threads, with the same parameters for
+ * every lattice (each block must divide every lattice).  Every other call
+ * takes one lattice: get its handle with dwf_lattice.
  * Returns DWF_EINVAL for bad sizes, DWF_ENOMEM / DWF_ECUDA on CUDA failure. */
-dwf_status dwf_create(dwf_ctx **out, const int dims[4], int Ls, double M5, double mf,
-                      const void *links, int antiperiodic_t, void *stream);
+dwf_status dwf_create(dwf_ctx **out, int nlat, const int (*dims)[4], int Ls, double M5, double mf,
+                      const void *const *links, int antiperiodic_t, void *stream);
+
+/* The context of lattice i of a batch (for nlat = 1, i = 0 gives ctx itself).
+ * The handle is borrowed: it stays valid until dwf_destroy(ctx) and must not
+ * be destroyed by the caller.  Its calls run on the lattice's own stream. */
+dwf_status dwf_lattice(dwf_ctx *ctx, int i, dwf_ctx **out);
 
 /* out = D in (dagger = 0) or D^+ in (dagger != 0) for nrhs fields in the
  * internal layout, in FP64 or FP32 (prec = DWF_F64 or DWF_F32).  Fine
  * operator of Sec. 2 / Sec. 4 (the 11-site stencil).  out and in are
- * device pointers and must not overlap.  Asynchronous. */
+ * device pointers and must not overlap.  Asynchronous.  On a batch: nrhs
+ * fields of every lattice, lattices one after another. */
 dwf_status dwf_apply(dwf_ctx *ctx, void *out_dev, const void *in_dev, dwf_prec prec, int dagger,
                      int nrhs);
 
@@ -163,7 +181,8 @@ dwf_status dwf_unpack(dwf_ctx *ctx, void *canonical_dev, const void *internal_de
  *               device.  NULL: drawn on the device from Philox-4x32-10 with
  *               opt->seed.
  * Synchronous.  DWF_EBREAKDOWN if block Gram-Schmidt meets dependent
- * vectors. */
+ * vectors.  On a batch: every lattice gets the same levels, nvec, block
+ * and parameters; start (if given) holds each lattice's vectors in turn. */
 dwf_status mg_setup(dwf_ctx *ctx, int levels, const int *nvec, const int (*block)[4],
                     const mg_params *opt, const void *start);
 
@@ -173,7 +192,10 @@ dwf_status mg_setup(dwf_ctx *ctx, int levels, const int *nvec, const int (*block
  *               device; x holds the initial guess on entry and the solution
  *               on return (also on DWF_ENOCONV: the best iterate).
  *   stats       optional, filled on return (totals over the nrhs solves).
- * Synchronous. */
+ * Synchronous.  On a batch: nrhs right-hand sides per lattice, lattices one
+ * after another in b and x; stats sums iterations and applications over
+ * the lattices and gives the largest true residual; the status is the
+ * first lattice's that is not DWF_OK. */
 dwf_status mg_solve(dwf_ctx *ctx, const void *b, void *x, double tol, int nrhs, mg_stats *stats);
 
 /* ---- Component calls --------------------------------------------------
@@ -309,7 +331,8 @@ dwf_status dwf_cg_solve(dwf_ctx *ctx, const void *b, void *x, double tol, int ma
 /* Description of a status code (static string). */
 const char *dwf_strerror(dwf_status s);
 
-/* Release everything the context owns.  Safe on NULL. */
+/* Release everything the context owns (for a batch, every lattice's
+ * context and stream).  Safe on NULL. */
 void dwf_destroy(dwf_ctx *ctx);
 
 #ifdef __cplusplus

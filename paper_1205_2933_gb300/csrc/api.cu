@@ -2,6 +2,7 @@
 #include <cstring>
 #include <exception>
 
+#include "batch.cuh"
 #include "dwf_internal.cuh"
 #include "mg.cuh"
 
@@ -25,6 +26,10 @@ dwf_status fail(dwf_ctx *c, const Error &e) {
 }
 
 template <typename F> dwf_status guarded(dwf_ctx *c, F &&f) {
+    if (c && !c->members.empty()) {
+        dwf::set_last_error("a batch of lattices: this call takes one lattice (dwf_lattice)");
+        return DWF_EINVAL;
+    }
     if (c && c->sticky != DWF_OK) return DWF_ESTATE;
     try {
         return f();
@@ -81,7 +86,11 @@ const char *dwf_strerror(dwf_status s) {
     return "unknown status";
 }
 
-dwf_status dwf_create(dwf_ctx **out, const int dims[4], int Ls, double M5, double mf, const void *links,
+}  // extern "C"
+
+namespace dwf {
+
+dwf_status create_one(dwf_ctx **out, const int dims[4], int Ls, double M5, double mf, const void *links,
                       int antiperiodic_t, void *stream) {
     if (!out || !dims || !links) return DWF_EINVAL;
     *out = nullptr;
@@ -126,14 +135,44 @@ dwf_status dwf_create(dwf_ctx **out, const int dims[4], int Ls, double M5, doubl
     return DWF_OK;
 }
 
+}  // namespace dwf
+
+extern "C" {
+
+dwf_status dwf_create(dwf_ctx **out, int nlat, const int (*dims)[4], int Ls, double M5, double mf,
+                      const void *const *links, int antiperiodic_t, void *stream) {
+    if (!out || !dims || !links || nlat < 1 || nlat > 64) return DWF_EINVAL;
+    *out = nullptr;
+    if (nlat == 1) return dwf::create_one(out, dims[0], Ls, M5, mf, links[0], antiperiodic_t, stream);
+    return dwf::create_batch(out, nlat, dims, Ls, M5, mf, links, antiperiodic_t, stream);
+}
+
+dwf_status dwf_lattice(dwf_ctx *c, int i, dwf_ctx **out) {
+    if (!c || !out) return DWF_EINVAL;
+    *out = nullptr;
+    if (c->members.empty()) {
+        if (i != 0) return DWF_EINVAL;
+        *out = c;
+        return DWF_OK;
+    }
+    if (i < 0 || i >= (int)c->members.size()) return DWF_EINVAL;
+    *out = c->members[i];
+    return DWF_OK;
+}
+
 void dwf_destroy(dwf_ctx *c) {
     if (!c) return;
+    if (!c->members.empty()) {
+        dwf::destroy_batch(c);
+        return;
+    }
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     dwf::prof_reset(c);
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
     dwf::mg_free(c);
     if (c->hscal) cudaFreeHost(c->hscal);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
@@ -141,6 +180,11 @@ dwf_status dwf_apply(dwf_ctx *c, void *out, const void *in, dwf_prec prec, int d
     if (!c || !out || !in || nrhs < 1 || nrhs > 65535) return DWF_EINVAL;
     if (prec != DWF_F64 && prec != DWF_F32) return DWF_EINVAL;
     if (out == in) return DWF_EINVAL;
+    if (!c->members.empty())
+        return dwf::batch_async(c, [&](dwf_ctx *m, size_t off) {
+            const size_t e = prec == DWF_F64 ? 16 : 8;
+            return dwf_apply(m, (char *)out + off * e, (const char *)in + off * e, prec, dagger, nrhs);
+        }, nrhs);
     return guarded(c, [&]() -> dwf_status {
         if (prec == DWF_F64)
             dwf::dslash(c, (double2 *)out, (const double2 *)in, dagger != 0, nrhs);
@@ -153,6 +197,11 @@ dwf_status dwf_apply(dwf_ctx *c, void *out, const void *in, dwf_prec prec, int d
 dwf_status dwf_pack(dwf_ctx *c, void *internal, const void *canonical, dwf_prec prec, int nrhs) {
     if (!c || !internal || !canonical || nrhs < 1) return DWF_EINVAL;
     if (prec != DWF_F64 && prec != DWF_F32) return DWF_EINVAL;
+    if (!c->members.empty())
+        return dwf::batch_async(c, [&](dwf_ctx *m, size_t off) {
+            const size_t e = prec == DWF_F64 ? 16 : 8;
+            return dwf_pack(m, (char *)internal + off * e, (const char *)canonical + off * 16, prec, nrhs);
+        }, nrhs);
     return guarded(c, [&]() -> dwf_status {
         dwf::pack(c, internal, (const double2 *)canonical, prec, nrhs);
         return DWF_OK;
@@ -162,6 +211,11 @@ dwf_status dwf_pack(dwf_ctx *c, void *internal, const void *canonical, dwf_prec 
 dwf_status dwf_unpack(dwf_ctx *c, void *canonical, const void *internal, dwf_prec prec, int nrhs) {
     if (!c || !internal || !canonical || nrhs < 1) return DWF_EINVAL;
     if (prec != DWF_F64 && prec != DWF_F32) return DWF_EINVAL;
+    if (!c->members.empty())
+        return dwf::batch_async(c, [&](dwf_ctx *m, size_t off) {
+            const size_t e = prec == DWF_F64 ? 16 : 8;
+            return dwf_unpack(m, (char *)canonical + off * 16, (const char *)internal + off * e, prec, nrhs);
+        }, nrhs);
     return guarded(c, [&]() -> dwf_status {
         dwf::unpack(c, (double2 *)canonical, internal, prec, nrhs);
         return DWF_OK;
@@ -171,6 +225,16 @@ dwf_status dwf_unpack(dwf_ctx *c, void *canonical, const void *internal, dwf_pre
 dwf_status mg_setup(dwf_ctx *c, int levels, const int *nvec, const int (*block)[4], const mg_params *opt,
                     const void *start) {
     if (!c || levels < 2 || levels > 4 || !nvec || !block) return DWF_EINVAL;
+    if (!c->members.empty()) {
+        mg_params p;
+        if (opt) p = *opt;
+        else mg_default_params(&p);
+        const int nad = p.split ? nvec[0] / 2 : nvec[0];
+        const bool host = start && !is_device_ptr(start);
+        return dwf::batch_sync(c, [&](dwf_ctx *m, size_t off) {
+            return mg_setup(m, levels, nvec, block, &p, start ? (const char *)start + off * 16 : nullptr);
+        }, nad, host);
+    }
     return guarded(c, [&]() -> dwf_status {
         mg_params p;
         if (opt) p = *opt;
@@ -181,6 +245,7 @@ dwf_status mg_setup(dwf_ctx *c, int levels, const int *nvec, const int (*block)[
 
 dwf_status mg_solve(dwf_ctx *c, const void *b, void *x, double tol, int nrhs, mg_stats *stats) {
     if (!c || !b || !x || nrhs < 1 || !(tol > 0.0)) return DWF_EINVAL;
+    if (!c->members.empty()) return dwf::batch_solve(c, b, x, tol, nrhs, stats, !is_device_ptr(b) || !is_device_ptr(x));
     return guarded(c, [&]() -> dwf_status {
         bool host = !is_device_ptr(b) || !is_device_ptr(x);
         return dwf::mg_solve_impl(c, b, x, tol, nrhs, stats, host);
@@ -306,7 +371,7 @@ dwf_status dwf_profile_read(dwf_ctx *c, int kernel_class, long long *launches, d
 }
 
 dwf_status dwf_profile_units(dwf_ctx *c, int kernel_class, long long *units) {
-    if (!c || !units || kernel_class < 0 || kernel_class >= dwf::K_NCLASS) return DWF_EINVAL;
+    if (!c || !units || kernel_class < 0 || kernel_class >= dwf::K_NCLASS || !c->members.empty()) return DWF_EINVAL;
     long long u = 0;
     for (auto &r : c->prof_rec)
         if (r.cls == kernel_class) u += r.units;
@@ -409,6 +474,7 @@ dwf_status mg_setup_learned(dwf_ctx *c, dwf_net *net, unsigned int seed, int lev
                             const int (*block)[4], const mg_params *opt, int pre_iters0, int fallback_iters0,
                             double probe_tol, int probe_max_iters, int *used_fallback) {
     if (!c || !net || !nvec || !block || levels < 2 || pre_iters0 < 0) return DWF_EINVAL;
+    if (!c->members.empty()) return DWF_EINVAL;  // one lattice at a time (dwf_lattice)
     if (used_fallback) *used_fallback = 0;
     mg_params p;
     if (opt) p = *opt;

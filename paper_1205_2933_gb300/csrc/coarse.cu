@@ -311,6 +311,7 @@ void convert_coarse_links(dwf_ctx *c, Level &L) {
         convert_kernel<__half2><<<blocks, 256, 0, c->stream>>>(L.Y16.as<__half2>(), L.Y64.as<double2>(), n);
     }
     DWF_CHECK_LAUNCH();
+    build_tc_images(c, L);
 }
 
 // Build Y of level Lc = L+1 (FP64) from level L's basis Q in precision R:

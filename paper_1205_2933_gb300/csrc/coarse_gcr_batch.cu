@@ -13,6 +13,8 @@
 // the same totals, so all CTAs take identical decisions.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "mg.cuh"
 
 namespace cg = cooperative_groups;
@@ -399,7 +401,7 @@ void launch_bt(dwf_ctx *c, const Level &L, const LT *Y, C<R> *x, const C<R> *b, 
     // about four sites per CTA, at most one CTA per SM
     int64_t nblk = (L.lg.g.V + 3) / 4;
     nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, c->sm_count));
-    DWF_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)nblk), dim3(BCT), kargs, 0, c->stream));
+    DWF_CUDA(coop_launch(c, fn, dim3((unsigned)nblk), dim3(BCT), kargs, 0));
     DWF_CHECK_LAUNCH();
 }
 
@@ -409,12 +411,19 @@ bool coarse_gcr_batch_ok(const Level &L, int restart, int nb) {
     return restart >= 1 && restart <= BMAXR && nb >= 1 && nb <= BMAXB;
 }
 
-size_t coarse_gcr_batch_part_bytes(dwf_ctx *c) { return sizeof(double2) * (size_t)MAXV * (c->sm_count + 1); }
+// partial sums, totals and (tensor-core solver) an error word
+size_t coarse_gcr_batch_part_bytes(dwf_ctx *c) { return sizeof(double2) * (size_t)MAXV * (c->sm_count + 1) + 256; }
 
 template <typename R>
 void coarse_gcr_fused_batch(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, int nb, C<R> *r, C<R> *Z, C<R> *W,
                             double2 *part, int *iters, double tol, int maxiter, int restart) {
     DWF_REQUIRE(coarse_gcr_batch_ok(L, restart, nb), DWF_EINVAL, "batched coarse solve: restart <= 16, nb <= 16");
+    if constexpr (std::is_same<R, float>::value) {
+        if (coarse_gcr_tc_ok(c, L, restart, nb)) {
+            coarse_gcr_tc(c, L, x, b, nb, r, Z, W, part, iters, tol, maxiter, restart);
+            return;
+        }
+    }
     ProfScope ps(c, K_COARSE, nb);
     switch (L.yprec) {
         case DWF_F64: launch_bt<R, double2>(c, L, L.Y64.as<double2>(), x, b, nb, r, Z, W, part, iters, tol, maxiter, restart); break;

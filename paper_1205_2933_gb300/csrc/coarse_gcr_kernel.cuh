@@ -311,7 +311,7 @@ void launch_t(dwf_ctx *c, const Level &L, const LT *Y, C<R> *x, const C<R> *b, C
     int per_sm = 0;
     DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, CT, 0));
     DWF_REQUIRE(per_sm >= 1, DWF_ECUDA, "fused coarse solver cannot be co-resident");
-    DWF_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, kargs, 0, c->stream));
+    DWF_CUDA(coop_launch(c, fn, grid, block, kargs, 0));
     DWF_CHECK_LAUNCH();
 }
 

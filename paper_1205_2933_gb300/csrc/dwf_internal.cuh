@@ -136,6 +136,12 @@ constexpr int NSCALAR = 8192;
 
 struct MGState;
 
+// Serialises the cooperative launches of the member contexts of a batch
+// (each waits for the previous one to finish on the GPU).
+struct CoopGate;
+// cudaLaunchCooperativeKernel on c->stream, through c->gate when c belongs to a batch
+cudaError_t coop_launch(dwf_ctx *c, const void *fn, dim3 grid, dim3 block, void **args, size_t smem);
+
 // Kernel classes timed by the optional event profiler (see dwf_profile).
 enum KernelClass { K_DSLASH_F64 = 0, K_DSLASH_F32 = 1, K_RESTRICT = 2, K_PROLONG = 3, K_COARSE = 4, K_NCLASS = 5 };
 
@@ -165,6 +171,15 @@ struct dwf_ctx {
     // per-CTA partial sums of the Dslash's fused output norms
     dwf::DevBuf dn_part;
     dwf::MGState *mg = nullptr;
+    int *tc_err = nullptr;  // error word of the last tensor-core coarse solve (device)
+    // A batch of independent lattices (dwf_create with nlat > 1): one member
+    // context per lattice, each on a stream of its own; the batch context
+    // itself holds no lattice.  Cooperative launches of all members pass
+    // through one gate so that two grids that each fill the GPU never wait
+    // on one another.
+    std::vector<dwf_ctx *> members;
+    dwf::CoopGate *gate = nullptr;  // owned by the batch context, shared by its members
+    bool own_stream = false;        // member streams are created and destroyed by the library
     long long applies64 = 0, applies32 = 0;
     // event profiler
     bool prof = false;

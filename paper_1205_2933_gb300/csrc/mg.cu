@@ -1229,6 +1229,7 @@ dwf_status mg_solve_impl(dwf_ctx *c, const void *b, void *x, double tol, int nrh
                                                    : solve_t<double>(c, mg, bp, xp, tol, nrhs, st);
     if (host) DWF_CUDA(cudaMemcpyAsync(x, xd.p, xd.bytes, cudaMemcpyDefault, c->stream));
     DWF_CUDA(cudaStreamSynchronize(c->stream));
+    check_tc_timeout(c);
     st.fine_applies_f64 = c->applies64 - a64;
     st.fine_applies_f32 = c->applies32 - a32;
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1358,6 +1359,8 @@ void mg_vcycle_impl(dwf_ctx *c, double2 *x, const double2 *b, int nrhs) {
     MGState &mg = need_mg(c, 0, 0, 1);
     if (mg.p.smoother_prec == DWF_F32) vcycle_t<float>(c, mg, x, b, nrhs);
     else vcycle_t<double>(c, mg, x, b, nrhs);
+    DWF_CUDA(cudaStreamSynchronize(c->stream));
+    check_tc_timeout(c);
 }
 
 dwf_status cg_solve_impl(dwf_ctx *c, const void *b, void *x, double tol, int maxiter, int nrhs, dwf_prec prec,

@@ -34,6 +34,7 @@ struct Level {
     // npts = 9 for R A P, 33 for the squared operator's P^+ D^+ D P
     int npts = 9;
     DevBuf Y64, Y32, Y16;  // Y16 holds bf16 or fp16 pairs per coarse_prec
+    DevBuf Ytc;            // BF16 stencil as per-site tensor-core operand images (coarse_gcr_tc.cu)
     dwf_prec yprec = DWF_F64;
     // block reductions scratch: [Vc][nv][nv] complex FP64
     DevBuf G, F, Rinv;
@@ -134,6 +135,14 @@ template <typename R>
 void coarse_gcr_fused_batch(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, int nb, C<R> *r, C<R> *Z, C<R> *W,
                             double2 *part, int *iters, double tol, int maxiter, int restart);
 size_t coarse_gcr_part_bytes(dwf_ctx *c);
+// ---- coarse_gcr_tc.cu ---- the batched solve with the BF16 stencil on the tensor cores
+// (FP32 fields, 9-point stencil, Nvec in {8, 16, 24, 32}, nb <= 16, restart <= 16)
+bool coarse_gcr_tc_ok(dwf_ctx *c, const Level &L, int restart, int nb);
+void coarse_gcr_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, float2 *r, float2 *Z, float2 *W,
+                   double2 *part, int *iters, double tol, int maxiter, int restart);
+void build_tc_images(dwf_ctx *c, Level &L);
+// throws DWF_ETIMEOUT when a tensor-core solve since the last check gave up a bounded wait
+void check_tc_timeout(dwf_ctx *c);
 template <typename R>
 void coarse_gcr_fused(dwf_ctx *c, const Level &L, C<R> *x, const C<R> *b, C<R> *r, C<R> *Z, C<R> *W, double2 *part,
                       int *iters, double tol, int maxiter, int restart);

@@ -86,7 +86,9 @@ def _load():
     L.dwf_strerror.restype = ctypes.c_char_p
     L.dwf_last_error.argtypes = []
     L.dwf_last_error.restype = ctypes.c_char_p
-    L.dwf_create.argtypes = [ctypes.POINTER(vp), ip, i, ctypes.c_double, ctypes.c_double, vp, i, vp]
+    L.dwf_create.argtypes = [ctypes.POINTER(vp), i, vp, i, ctypes.c_double, ctypes.c_double, vp, i, vp]
+    L.dwf_lattice.argtypes = [vp, i, ctypes.POINTER(vp)]
+    L.dwf_lattice.restype = st
     L.dwf_destroy.argtypes = [vp]
     L.dwf_destroy.restype = None
     L.dwf_apply.argtypes = [vp, vp, vp, st, i, i]
@@ -187,11 +189,28 @@ def mg_default_params() -> mg_params:
 
 def dwf_create(dims, Ls, M5, mf, links, antiperiodic_t=True, stream=None):
     """Context handle (ctypes.c_void_p) for one lattice; links complex128 [V][4][3][3]."""
+    return dwf_create_batch([dims], Ls, M5, mf, [links], antiperiodic_t, stream)
+
+
+def dwf_create_batch(dims_list, Ls, M5, mf, links_list, antiperiodic_t=True, stream=None):
+    """Context handle for len(dims_list) independent lattices (one handle, fields of the
+    lattices one after another); links_list[i] complex128 [V_i][4][3][3]."""
+    n = len(dims_list)
+    if n != len(links_list):
+        raise ValueError("one links array per lattice")
     h = ctypes.c_void_p()
-    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    d = (ctypes.c_int * (4 * n))(*[int(x) for dims in dims_list for x in dims])
+    lk = (ctypes.c_void_p * n)(*[_ptr(u) for u in links_list])
     s = ctypes.c_void_p(int(stream)) if stream is not None else None
-    _check(_lib.dwf_create(ctypes.byref(h), d, int(Ls), float(M5), float(mf), _ptr(links),
-                           1 if antiperiodic_t else 0, s), "dwf_create")
+    _check(_lib.dwf_create(ctypes.byref(h), n, ctypes.cast(d, ctypes.c_void_p), int(Ls), float(M5), float(mf),
+                           ctypes.cast(lk, ctypes.c_void_p), 1 if antiperiodic_t else 0, s), "dwf_create")
+    return h
+
+
+def dwf_lattice(ctx, i):
+    """Borrowed handle of lattice i of a batch context."""
+    h = ctypes.c_void_p()
+    _check(_lib.dwf_lattice(ctx, int(i), ctypes.byref(h)), "dwf_lattice")
     return h
 
 
@@ -323,6 +342,45 @@ class Context:
     @property
     def field_elems(self):
         return self.V * 12 * self.Ls
+
+    def close(self):
+        if self.h is not None:
+            dwf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchContext:
+    """Owns one dwf_ctx holding several independent lattices (same Ls, M5, mf);
+    fields hold the lattices one after another (nrhs fields of each in turn)."""
+
+    def __init__(self, dims_list, Ls, M5, mf, links_list, antiperiodic_t=True, stream=None):
+        import torch
+        self.dims = [tuple(int(d) for d in dims) for dims in dims_list]
+        self.Ls = int(Ls)
+        self.V = [d[0] * d[1] * d[2] * d[3] for d in self.dims]
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self.h = dwf_create_batch(self.dims, Ls, M5, mf, links_list, antiperiodic_t, stream)
+
+    def field_elems(self, i=None):
+        """Complex elements of one field of lattice i (all lattices when i is None)."""
+        if i is None:
+            return sum(v * 12 * self.Ls for v in self.V)
+        return self.V[i] * 12 * self.Ls
+
+    def offset(self, i, nrhs=1):
+        """Element offset of lattice i's first field in a batch array of nrhs fields per lattice."""
+        return sum(self.V[j] * 12 * self.Ls for j in range(i)) * nrhs
+
+    def lattice(self, i):
+        return dwf_lattice(self.h, i)
 
     def close(self):
         if self.h is not None:

@@ -51,7 +51,11 @@ def test_library_loads_and_host_only_calls(libpath):
     # invalid arguments are rejected before any device work
     h = ctypes.c_void_p()
     d = (ctypes.c_int * 4)(4, 4, 4, 4)
-    assert G.lib().dwf_create(ctypes.byref(h), d, 0, 1.8, 0.1, None, 1, None) == G.DWF_EINVAL
+    assert G.lib().dwf_create(ctypes.byref(h), 1, ctypes.cast(d, ctypes.c_void_p), 0, 1.8, 0.1, None, 1, None) \
+        == G.DWF_EINVAL
+    assert G.lib().dwf_create(ctypes.byref(h), 0, ctypes.cast(d, ctypes.c_void_p), 8, 1.8, 0.1, None, 1, None) \
+        == G.DWF_EINVAL
+    assert G.lib().dwf_lattice(None, 0, ctypes.byref(h)) == G.DWF_EINVAL
     assert G.lib().dwf_apply(None, None, None, 0, 0, 1) == G.DWF_EINVAL
     assert G.lib().net_create(None, None, None) == G.DWF_EINVAL
     assert G.lib().net_adam(None, 1e-3, 0.9, 0.999, 1e-8) == G.DWF_EINVAL

@@ -62,7 +62,8 @@ def test_basis_and_coarse_links_nvec24(G, case):
     got = to_canonical(c.ctx, q, (nv,) + c.op.shape, nrhs=nv)
     T = c.mg.levels[0].transfer
     ref = np.stack([T.vector(k) for k in range(nv)])
-    assert rel_max(got, ref) < 1e-12
+    # the FP32 V-cycle's setup orthonormalises FP32 copies of the vectors (FP64 sums)
+    assert rel_max(got, ref) < 1e-6
     del q, got
     d, n = G.mg_level_info(c.ctx.h, 1)
     assert tuple(d) == (2, 2, 2, 2) and n == 24
