@@ -28,6 +28,7 @@
 // the caller reports DWF_ETIMEOUT.
 #include <cooperative_groups.h>
 
+#include <cstring>
 #include <type_traits>
 
 #include "mg.cuh"
@@ -653,7 +654,11 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
     a.W = W;
     a.part = part;
     a.tot = part + (size_t)TMAXV * c->sm_count;
-    a.err = reinterpret_cast<int *>(part + (size_t)TMAXV * (c->sm_count + 1));
+    if (!c->tc_err.p) {
+        c->tc_err.alloc(sizeof(int));
+        DWF_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
+    }
+    a.err = c->tc_err.as<int>();
     a.iters = iters;
     a.tol = tol;
     a.maxiter = maxiter;
@@ -661,8 +666,7 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
     a.nb = nb;
     a.nbp = (nb + 3) / 4 * 4;
     a.bbuf = TcGeom<NV>::bbuf(4 * a.nbp);
-    DWF_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), c->stream));
-    c->tc_err = a.err;
+    c->tc_used = true;
     void *kargs[] = {&a};
     void *fn = tc_kernel_fn<NV>();
     const size_t smem = tc_smem<NV>(nb);
@@ -697,11 +701,13 @@ void coarse_gcr_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int n
 }
 
 void check_tc_timeout(dwf_ctx *c) {
-    if (!c->tc_err) return;
-    int e = 0;
-    DWF_CUDA(cudaMemcpyAsync(&e, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (!c->tc_used) return;
+    c->tc_used = false;
+    DWF_CUDA(cudaMemcpyAsync(c->hscal, c->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DWF_CUDA(cudaStreamSynchronize(c->stream));
-    c->tc_err = nullptr;
+    int e = 0;
+    std::memcpy(&e, c->hscal, sizeof(int));
+    if (e != 0) DWF_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
     DWF_REQUIRE(e == 0, DWF_ETIMEOUT, "tensor-core coarse solve: a bounded wait on the tensor cores expired");
 }
 

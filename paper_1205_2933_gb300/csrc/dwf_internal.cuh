@@ -171,7 +171,10 @@ struct dwf_ctx {
     // per-CTA partial sums of the Dslash's fused output norms
     dwf::DevBuf dn_part;
     dwf::MGState *mg = nullptr;
-    int *tc_err = nullptr;  // error word of the last tensor-core coarse solve (device)
+    // error word of the tensor-core coarse solves (device int, owned by the
+    // context: the solves' scratch is freed before the word is read back)
+    dwf::DevBuf tc_err;
+    bool tc_used = false;
     // A batch of independent lattices (dwf_create with nlat > 1): one member
     // context per lattice, each on a stream of its own; the batch context
     // itself holds no lattice.  Cooperative launches of all members pass
