@@ -48,10 +48,11 @@ NRHS = 12
 TOL = 1e-10
 METRIC = "DWF MG solve time to |r|/|b|\u226410^-10 (chosen vs FP64 plain); Dslash HBM GB/s"
 FINE_BYTES_F32 = 204   # algorithmic bytes per 5D site of the FP32 Dslash
-# dram__bytes_read.sum + dram__bytes_write.sum of one one-field launch of the
-# current FP32 Dslash kernel from an ncu capture; None until the kernel as it
-# stands has been captured
-DSLASH_TRAFFIC_PER_FIELD = 411171840  # 239.68 MB read + 171.49 MB written
+# dram__bytes_read.sum + dram__bytes_write.sum of the FP32 Dslash with fused
+# output norms (the instantiation of nearly all timed launches) per 2,097,152
+# 5D sites (one 16^3x32x16 field), from an ncu capture of a two-field launch on
+# 16^3x16x16; None until the kernel as it stands has been captured
+DSLASH_TRAFFIC_PER_FIELD = 424523776  # 252.34 MB read + 172.18 MB written
 FINE_BYTES_F64 = 408
 # fine-operator applications per solve of this workload on the GPU path (FP32 and
 # FP64, the setup's amortised over 12 right-hand sides), from the timed bench steps;
@@ -80,6 +81,12 @@ def parse():
                     help="profiling mode: setup, then one solve inside cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--dslash-only", action="store_true",
                     help="profiling mode: a few FP32 Dslash applications of the workload (for ncu)")
+    ap.add_argument("--profile-coarse", action="store_true",
+                    help="profiling mode: four batched V-cycles of 12 right-hand sides on 16^3x32 with Ls=2 "
+                         "(the workload's coarse problem, 512 sites x 24, with small fine fields; for ncu)")
+    ap.add_argument("--profile-vcycle", action="store_true",
+                    help="profiling mode: two batched V-cycles of 2 right-hand sides on 16^3x16, Ls=16, Nvec=8 "
+                         "(the FP32 Dslash with fused output norms at 2 x 101 MB per launch; for ncu)")
     return ap.parse_args()
 
 
@@ -329,6 +336,37 @@ def profile_modes(args):
     ctx.close()
 
 
+def profile_small(args):
+    """Small device-memory cases of the timed kernels for ncu captures: the
+    batched coarsest solve at the workload's coarse size (--profile-coarse) and
+    the FP32 Dslash with fused norms inside the batched smoother (--profile-vcycle)."""
+    import torch
+    from paper_1205_2933_gb300 import dwfmg as G
+    if args.profile_coarse:
+        dims, Ls, nvec, nr = DIMS, 2, NVEC, 12
+    else:
+        dims, Ls, nvec, nr = (16, 16, 16, 16), LS, 8, 2
+    U = I.heatbath_links(dims, BETA, 20, HB_SEED)
+    ctx = G.Context(dims, Ls, M5, MF, torch.from_numpy(U).cuda())
+    p = mixed_params(G)
+    p.setup_iters0 = 50
+    G.mg_setup(ctx.h, 2, [nvec], [BLOCK], p)
+    bs = np.stack([I.gaussian_source(dims, Ls, 101 + i) for i in range(nr)])
+    canon = torch.from_numpy(bs).cuda()
+    b = torch.empty(ctx.field_elems * nr, dtype=torch.complex128, device="cuda")
+    G.dwf_pack(ctx.h, b, canon, G.DWF_F64, nr)
+    x = torch.empty_like(b)
+    G.mg_vcycle_batch(ctx.h, x, b, nr)  # workspaces allocated outside the profiled range
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(4 if args.profile_coarse else 2):
+        G.mg_vcycle_batch(ctx.h, x, b, nr)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("profile ok", float(x.abs().max()))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -336,6 +374,9 @@ def main():
         return
     if args.profile_solve or args.dslash_only:
         profile_modes(args)
+        return
+    if args.profile_coarse or args.profile_vcycle:
+        profile_small(args)
         return
     import torch
     from paper_1205_2933_gb300 import dwfmg as G
@@ -416,7 +457,8 @@ def main():
                 "frac": achieved / peak, "traffic": DSLASH_TRAFFIC_PER_FIELD, "peak_kind": peak_kind,
                 "avg_launch_us": ms32 / n32 * 1e3, "launches": n32, "fields": u32,
                 "bytes_per_launch": FINE_BYTES_F32 * V5 * u32 / n32,
-                "traffic_note": "ncu dram bytes per field application (one-field launch)"}
+                "traffic_note": "ncu dram bytes per field application (norm-epilogue kernel, two-field launch "
+                                "of 2 x 16^3x16x16 = one 16^3x32x16 field of sites)"}
 
     # fine-operator applications per solve in the timed region, setup included
     # (the paper's cost unit, Sec. 3): all fields the FP32 and FP64 Dslash processed
