@@ -70,8 +70,7 @@ struct TcArgs {
     const float2 *b;            // [nb][Nf]
     float2 *x, *r;              // [nb][Nf]
     float2 *Z, *W;              // [restart][nb][Nf]
-    double2 *part;              // [TMAXV][gridDim.x] per-CTA partial sums
-    double2 *tot;               // [TMAXV] totals
+    float2 *part;               // [2][gridDim.x][TMAXV] per-CTA partial sums, two alternating buffers
     int *err;                   // set on an expired wait
     int *iters;
     double tol;
@@ -300,7 +299,7 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ float red[NWARP][2 * TMAXV];
     __shared__ double2 tot[TMAXV];
-    __shared__ double rn2[TMAXB], stop[TMAXB];
+    __shared__ double rn2[TMAXB], stop[TMAXB], wwv[TMAXB];
     __shared__ int act[TMAXB], its[TMAXB];
     __shared__ __align__(8) uint64_t bars[4];
     __shared__ uint32_t tbase;
@@ -349,41 +348,46 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
         for (int q = tid; q < NWARP * 2 * nv; q += TCT) red[q / (2 * nv)][q % (2 * nv)] = 0.f;
         __syncthreads();
     };
-    // totals of complex values 0..nv-1 (warps, then CTAs in a fixed order) into tot[] of every CTA
+    // Totals of the complex values 0..nv-1 into tot[] of every CTA through one
+    // grid barrier: each CTA writes its FP32 partials (warps summed in a fixed
+    // order) and its error flag to one of two alternating buffers, then every
+    // CTA adds all CTAs' partials in the same order, so all hold identical
+    // totals and take identical decisions.  The two buffers keep a CTA that
+    // runs ahead to the next reduction off the partials others still read.
+    int phase = 0;
     auto finish = [&](int nv) {
         __syncthreads();
-        for (int p = tid; p < nv; p += TCT) {
-            double2 s = make_double2(0, 0);
-            for (int w = 0; w < NWARP; ++w) {
-                s.x += (double)red[w][2 * p];
-                s.y += (double)red[w][2 * p + 1];
+        float2 *pb = a.part + (size_t)(phase & 1) * TMAXV * nblk;
+        for (int p = tid; p <= nv; p += TCT) {
+            float2 v = make_float2(0.f, 0.f);
+            if (p < nv) {
+                for (int w = 0; w < NWARP; ++w) {
+                    v.x += red[w][2 * p];
+                    v.y += red[w][2 * p + 1];
+                }
+            } else {
+                v.x = bad ? 1.f : 0.f;
             }
-            a.part[(size_t)p * nblk + blockIdx.x] = s;
+            pb[(size_t)blockIdx.x * TMAXV + p] = v;
         }
         if (tid == 0 && bad) atomicOr(a.err, 1);
         __threadfence();
         grid.sync();
-        if (warp == 0)
-            for (int p = blockIdx.x; p < nv; p += nblk) {
-                double sx = 0, sy = 0;
-                for (int j = lane; j < nblk; j += 32) {
-                    const double2 q = __ldcg(a.part + (size_t)p * nblk + j);
-                    sx += q.x;
-                    sy += q.y;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    sx += __shfl_down_sync(0xffffffffu, sx, o);
-                    sy += __shfl_down_sync(0xffffffffu, sy, o);
-                }
-                if (lane == 0) a.tot[p] = make_double2(sx, sy);
+        for (int p = tid; p <= nv; p += TCT) {
+            float sx = 0.f, sy = 0.f;
+#pragma unroll 8
+            for (int j = 0; j < nblk; ++j) {
+                const float2 q = __ldcg(pb + (size_t)j * TMAXV + p);
+                sx += q.x;
+                sy += q.y;
             }
-        __threadfence();
-        grid.sync();
-        for (int p = tid; p < nv; p += TCT) tot[p] = __ldcg(a.tot + p);
-        if (tid == 0) quit = __ldcg(a.err) != 0;
+            if (p < nv) tot[p] = make_double2(sx, sy);
+            else quit = sx > 0.f;
+        }
+        ++phase;
         __syncthreads();
     };
+
     // x = 0, r = b, |b|^2 per right-hand side
     zero_red(nb);
     for (int base = warp * 32; base < nitems; base += TCT) {
@@ -405,13 +409,14 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
     if (tid < nb) {
         rn2[tid] = tot[tid].x;
         stop[tid] = a.tol * a.tol * tot[tid].x;
-        act[tid] = (tot[tid].x > 0.0 && a.maxiter > 0) ? 1 : 0;
+        act[tid] = (tot[tid].x > 0.0 && a.maxiter > 0 && !quit) ? 1 : 0;
         its[tid] = 0;
     }
     __syncthreads();
 
-    // one Gram-Schmidt pass of W_k (and Z_k) against W_0..W_{k-1}: P values per element
-    auto cgs_dots = [&](auto Pc, int k) {
+    // Gram-Schmidt dots <W_i, W_k> of the k stored directions (values i*nb + rr);
+    // with NORMS also |W_k|^2 (value k*nb + rr) and <W_k, r> ((k+1)*nb + rr)
+    auto gs_dots = [&](auto Pc, int k, bool norms) {
         constexpr int P = decltype(Pc)::value;
         constexpr int lp = log2p<P>();
         const float2 *Wk = a.W + (size_t)k * nb * Nf;
@@ -422,22 +427,55 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
             const bool ok = eo < E;
             const int ie = rr * Nf + e0 + eo;
             const float2 w = ok ? Wk[ie] : make_float2(0.f, 0.f);
-            float v[P];
+            if (k > 0) {
+                float v[P];
 #pragma unroll
-            for (int i = 0; i < P / 2; ++i) {
-                float2 u = make_float2(0.f, 0.f);
-                if (i < k && ok) u = a.W[(size_t)i * nb * Nf + ie];
-                v[2 * i] = u.x * w.x + u.y * w.y;
-                v[2 * i + 1] = u.x * w.y - u.y * w.x;
+                for (int i = 0; i < P / 2; ++i) {
+                    float2 u = make_float2(0.f, 0.f);
+                    if (i < k && ok) u = a.W[(size_t)i * nb * Nf + ie];
+                    v[2 * i] = u.x * w.x + u.y * w.y;
+                    v[2 * i + 1] = u.x * w.y - u.y * w.x;
+                }
+                const float sv = warp_scatter_sum<P>(v);
+                const int vi = lane >> (5 - lp);
+                if ((lane & ((1 << (5 - lp)) - 1)) == 0 && vi < 2 * k)
+                    red[warp][2 * ((vi >> 1) * nb + rr) + (vi & 1)] += sv;
             }
-            const float s = warp_scatter_sum<P>(v);
-            const int vi = lane >> (5 - lp);
-            if ((lane & ((1 << (5 - lp)) - 1)) == 0 && vi < 2 * k) red[warp][2 * ((vi >> 1) * nb + rr) + (vi & 1)] += s;
+            if (norms) {
+                const float2 q = ok ? a.r[ie] : make_float2(0.f, 0.f);
+                float u[4] = {w.x * w.x + w.y * w.y, 0.f, w.x * q.x + w.y * q.y, w.x * q.y - w.y * q.x};
+                const float su = warp_scatter_sum<4>(u);
+                const int ui = lane >> 3;
+                if ((lane & 7) == 0) {
+                    if (ui == 0) red[warp][2 * (k * nb + rr)] += su;
+                    else if (ui >= 2) red[warp][2 * ((k + 1) * nb + rr) + (ui - 2)] += su;
+                }
+            }
         }
+    };
+    auto dots = [&](int k, bool norms) {
+        if (k <= 1) gs_dots(std::integral_constant<int, 2>{}, k, norms);
+        else if (k <= 2) gs_dots(std::integral_constant<int, 4>{}, k, norms);
+        else if (k <= 4) gs_dots(std::integral_constant<int, 8>{}, k, norms);
+        else if (k <= 8) gs_dots(std::integral_constant<int, 16>{}, k, norms);
+        else gs_dots(std::integral_constant<int, 32>{}, k, norms);
+    };
+    // w -= sum_i beta_i W_i, z -= sum_i beta_i Z_i with beta_i = tot[i*nb + rr]
+    auto project_out = [&](int k, float2 &w, float2 &z, int rr, int ie) {
+#pragma unroll
+        for (int i = 0; i < TMAXR; ++i)
+            if (i < k) {
+                const float br = (float)tot[i * nb + rr].x, bi = (float)tot[i * nb + rr].y;
+                const float2 wi = a.W[(size_t)i * nb * Nf + ie], zi = a.Z[(size_t)i * nb * Nf + ie];
+                w.x -= br * wi.x - bi * wi.y;
+                w.y -= br * wi.y + bi * wi.x;
+                z.x -= br * zi.x - bi * zi.y;
+                z.y -= br * zi.y + bi * zi.x;
+            }
     };
 
     int k = 0;
-    while (true) {
+    while (!quit) {
         bool any = false;
         for (int rr = 0; rr < nb; ++rr) any |= act[rr] != 0;
         if (!any) break;
@@ -450,13 +488,10 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
         __threadfence();
         grid.sync();
         tc_apply<NV>(a, pp, Wk, Zk, s0, s1, act, Nf, &bad);
-        for (int pass = 0; pass < 2 && k > 0; ++pass) {
+        // first classical Gram-Schmidt pass
+        if (k > 0) {
             zero_red(k * nb);
-            if (k <= 1) cgs_dots(std::integral_constant<int, 2>{}, k);
-            else if (k <= 2) cgs_dots(std::integral_constant<int, 4>{}, k);
-            else if (k <= 4) cgs_dots(std::integral_constant<int, 8>{}, k);
-            else if (k <= 8) cgs_dots(std::integral_constant<int, 16>{}, k);
-            else cgs_dots(std::integral_constant<int, 32>{}, k);
+            dots(k, false);
             finish(k * nb);
             if (quit) break;
             for (int base = warp * 32; base < nitems; base += TCT) {
@@ -465,56 +500,38 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
                 if (!act[rr] || eo >= E) continue;
                 const int ie = rr * Nf + e0 + eo;
                 float2 w = Wk[ie], z = Zk[ie];
-#pragma unroll
-                for (int i = 0; i < TMAXR; ++i)
-                    if (i < k) {
-                        const float br = (float)tot[i * nb + rr].x, bi = (float)tot[i * nb + rr].y;
-                        const float2 wi = a.W[(size_t)i * nb * Nf + ie], zi = a.Z[(size_t)i * nb * Nf + ie];
-                        w.x -= br * wi.x - bi * wi.y;
-                        w.y -= br * wi.y + bi * wi.x;
-                        z.x -= br * zi.x - bi * zi.y;
-                        z.y -= br * zi.y + bi * zi.x;
-                    }
+                project_out(k, w, z, rr, ie);
                 Wk[ie] = w;
                 Zk[ie] = z;
             }
             __syncthreads();
         }
+        // second pass, reduced together with |W_k|^2 and <W_k, r> of the first
+        // pass's W_k: after the second projection |W_k|^2 loses sum |beta_i|^2
+        // (the W_i are orthonormal) and <W_k, r> is unchanged (r is orthogonal
+        // to the W_i in GCR)
+        zero_red((k + 2) * nb);
+        dots(k, true);
+        finish((k + 2) * nb);
         if (quit) break;
-        // |w|^2 and <w, r>
-        zero_red(2 * nb);
-        for (int base = warp * 32; base < nitems; base += TCT) {
-            const int rr = base / Epad;
-            if (!act[rr]) continue;
-            const int eo = base - rr * Epad + lane;
-            float v[4] = {0.f, 0.f, 0.f, 0.f};
-            if (eo < E) {
-                const int ie = rr * Nf + e0 + eo;
-                const float2 w = Wk[ie], q = a.r[ie];
-                v[0] = w.x * w.x + w.y * w.y;
-                v[2] = w.x * q.x + w.y * q.y;
-                v[3] = w.x * q.y - w.y * q.x;
-            }
-            const float s = warp_scatter_sum<4>(v);
-            const int vi = lane >> 3;
-            // value 0: |w|^2 (real), 2, 3: <w, r>
-            if ((lane & 7) == 0) {
-                if (vi == 0) red[warp][2 * rr] += s;
-                else if (vi >= 2) red[warp][2 * (nb + rr) + (vi - 2)] += s;
-            }
+        if (tid < nb) {
+            double ww = tot[k * nb + tid].x;
+            for (int i = 0; i < k; ++i) ww -= tot[i * nb + tid].x * tot[i * nb + tid].x + tot[i * nb + tid].y * tot[i * nb + tid].y;
+            wwv[tid] = ww;
         }
-        finish(2 * nb);
-        if (quit) break;
+        __syncthreads();
         for (int base = warp * 32; base < nitems; base += TCT) {
             const int rr = base / Epad;
             const int eo = base - rr * Epad + lane;
             if (!act[rr] || eo >= E) continue;
-            const double ww = tot[rr].x;
+            const double ww = wwv[rr];
             if (!(ww > 0.0)) continue;  // breakdown: handled below, the same in every CTA
             const double inv = 1.0 / sqrt(ww);
-            const float sc = (float)inv, arr = (float)(tot[nb + rr].x * inv), aii = (float)(tot[nb + rr].y * inv);
+            const double2 wr = tot[(k + 1) * nb + rr];
+            const float sc = (float)inv, arr = (float)(wr.x * inv), aii = (float)(wr.y * inv);
             const int ie = rr * Nf + e0 + eo;
             float2 z = Zk[ie], w = Wk[ie], xx = a.x[ie], q = a.r[ie];
+            project_out(k, w, z, rr, ie);
             z.x *= sc; z.y *= sc; w.x *= sc; w.y *= sc;
             xx.x += arr * z.x - aii * z.y;
             xx.y += arr * z.y + aii * z.x;
@@ -524,12 +541,12 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
         }
         __syncthreads();
         if (tid < nb && act[tid]) {
-            const double ww = tot[tid].x;
+            const double ww = wwv[tid];
             if (!(ww > 0.0)) {
                 act[tid] = 0;
             } else {
-                const double ar = tot[nb + tid].x / sqrt(ww), ai = tot[nb + tid].y / sqrt(ww);
-                rn2[tid] -= ar * ar + ai * ai;
+                const double2 wr = tot[(k + 1) * nb + tid];
+                rn2[tid] -= (wr.x * wr.x + wr.y * wr.y) / ww;
                 its[tid]++;
                 if (rn2[tid] <= stop[tid] || its[tid] >= a.maxiter) act[tid] = 0;
             }
@@ -652,8 +669,9 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
     a.r = r;
     a.Z = Z;
     a.W = W;
-    a.part = part;
-    a.tot = part + (size_t)TMAXV * c->sm_count;
+    // two alternating buffers of FP32 partials: as many bytes as the caller's FP64 partials and totals
+    static_assert(2 * sizeof(float2) == sizeof(double2), "partial-sum buffer size");
+    a.part = reinterpret_cast<float2 *>(part);
     if (!c->tc_err.p) {
         c->tc_err.alloc(sizeof(int));
         DWF_CUDA(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), c->stream));
