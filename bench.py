@@ -77,6 +77,7 @@ def parse():
                     help="right-hand sides solved by the plain FP64 method (their solutions are the FP64 "
                          "reference of the per-solve errors)")
     ap.add_argument("--e2e-steps", type=int, default=2, help="timed end-to-end steps (after one warm-up)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-setup comparison")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling mode: setup, then one solve inside cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--dslash-only", action="store_true",
@@ -478,6 +479,8 @@ def main():
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_plain:
         line["plain_fp64"] = run_plain(G, torch, U, b, x, min(args.plain_nrhs, nrhs), value)
+    if rank == 0 and not args.no_learned:
+        line["learned_setup"] = run_learned(G, torch, U, b, p)
     del b, x
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
@@ -536,6 +539,43 @@ def run_e2e(G, torch, U, bs, p, nrhs, steps):
     return {"value": statistics.median(times) / nrhs, "unit": "s/solve", "steps": steps,
             "h2d_bytes_per_step": int(Uh.numel() * 16 + bh.numel() * 16),
             "d2h_bytes_per_step": int(xh.numel() * 16)}
+
+
+def run_learned(G, torch, U, b, p):
+    """The learned setup on this workload against the method without it: the
+    committed refinement network (trained at 8^4 x 16) refines the adaptive
+    vectors after 50 relaxation iterations and the setup relaxes 550 more,
+    against the chosen setup's 600 relaxation iterations from random vectors;
+    setup time and outer iterations of the first source's solve."""
+    import pathlib
+    from paper_1205_2933_gb300 import learned as Lm
+    shape, params, meta = Lm.load(pathlib.Path(Lm.__file__).parent / "weights" / "near_null_refine_8x8x8x8_Ls16.npz")
+    ctx = G.Context(DIMS, LS, M5, MF, torch.from_numpy(U).cuda())
+    N = ctx.field_elems
+    b0 = b[:N].contiguous()
+    net = Lm.make_net(ctx, shape, params)
+    out = {}
+    for name in ("plain", "learned"):
+        q = G.mg_params.from_buffer_copy(p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if name == "learned":
+            q.setup_iters0 = p.setup_iters0 - meta["pre_iters"]
+            G.mg_setup_learned(ctx.h, net, 11, 2, [NVEC], [BLOCK], q, pre_iters0=meta["pre_iters"])
+        else:
+            G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], q)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        x0 = torch.zeros_like(b0)
+        st = G.mg_solve(ctx.h, b0, x0, TOL, 1, check=False)
+        torch.cuda.synchronize()
+        out[name] = {"setup_s": ts, "iters": st.iters, "solve_s": st.seconds, "true_res": st.true_res,
+                     "status": st.status}
+    G.net_destroy(net)
+    ctx.close()
+    out["note"] = ("refinement network (8^4 x 16 training) after 50 relaxation iterations, then 550 more, "
+                   "against 600 relaxation iterations from random vectors; first source, one-RHS solve")
+    return out
 
 
 def run_plain(G, torch, U, b, x_chosen, nplain, chosen_value):

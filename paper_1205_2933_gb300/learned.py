@@ -150,14 +150,15 @@ def solve_iterations(ctx, src_seed, tol=1e-10):
     return {"iters": st.iters, "true_res": st.true_res, "status": st.status, "seconds": time.perf_counter() - t0}
 
 
-def compare_setups(ctx, net, nvec, block, refine_iters, seed, src_seed, full_iters=1000, pre_iters=0):
+def compare_setups(ctx, net, nvec, block, refine_iters, seed, src_seed, full_iters=1000, pre_iters=0,
+                   names=("adaptive", "random", "learned")):
     """Setup time and solve iterations of (a) the plain adaptive setup, (b)
     random vectors + pre_iters + refine_iters relaxation iterations, (c) the
     network's vectors (a refinement network: after pre_iters relaxation
     iterations) + refine_iters relaxation iterations."""
     import torch
     out = {}
-    for name in ("adaptive", "random", "learned"):
+    for name in names:
         p = solve_params(full_iters if name == "adaptive" else
                          (refine_iters + pre_iters if name == "random" else refine_iters))
         p.seed = seed
