@@ -78,6 +78,10 @@ def parse():
                          "reference of the per-solve errors)")
     ap.add_argument("--e2e-steps", type=int, default=2, help="timed end-to-end steps (after one warm-up)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-setup comparison")
+    ap.add_argument("--workload", choices=["headline", "config3", "config4"], default="headline",
+                    help="config3: 24^3x48 Ls=16 batched point (+Z2) sources; config4: the uneven batch "
+                         "8^4 + 12^3x24 + 16^3x32 in one context and a 3-level solve (one JSON line each; "
+                         "the default is the headline workload)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiling mode: setup, then one solve inside cudaProfilerStart/Stop (for ncu)")
     ap.add_argument("--dslash-only", action="store_true",
@@ -337,6 +341,115 @@ def profile_modes(args):
     ctx.close()
 
 
+def _timed(torch, f):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = f()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, r
+
+
+def run_workload(args):
+    """The survey's other measured configurations (one JSON line each):
+    config3: 24^3 x 48, Ls = 16, m_f = 0.001, heatbath beta = 6.0 (seed 200),
+      12 spin-colour point sources at the origin (plus args.nrhs - 12 Z2 noise
+      sources, seeds 201...), all solved as one batch with the chosen mixed
+      precision; per-RHS time, Dslash GB/s and the coarse solver's share.
+    config4: 8^4, 12^3 x 24 and 16^3 x 32 at Ls = 16, m_f = 0.002, heatbath
+      beta = 5.9 (seeds 300-302) in one batch context (one setup call, one
+      solve call over all three lattices) against the three lattices one after
+      another in contexts of their own; then a 3-level solve of the 16^3 x 32
+      lattice (4^4 then 2^4 blocks, Nvec 24 then 32)."""
+    import torch
+    from paper_1205_2933_gb300 import dwfmg as G
+    p = mixed_params(G)
+    line = {"metric": f"{args.workload}: solve time per right-hand side (setup amortised)", "unit": "s/rhs",
+            "higher_is_better": False, "dtype": "f32+bf16 (fp64 outer)", "data": "synthetic"}
+    if args.workload == "config3":
+        dims, mf = (24, 24, 24, 48), 0.001
+        nr = max(12, args.nrhs)
+        U = I.heatbath_links(dims, BETA, HB_SWEEPS, 200)
+        ctx = G.Context(dims, LS, M5, mf, torch.from_numpy(U).cuda())
+        N = ctx.field_elems
+        b = torch.empty(N * nr, dtype=torch.complex128, device="cuda")
+        for i in range(nr):  # one canonical source (2 GB) at a time on the host
+            if i < 12:  # spin-colour point source at the origin on the walls
+                eta = np.zeros(I.lattice_shape(dims) + (4, 3), dtype=np.complex128)
+                eta[0, 0, 0, 0, i // 3, i % 3] = 1.0
+                src = I.wall_source(eta, LS)
+            else:
+                src = I.z2_source(dims, LS, 201 + i - 12)
+            G.dwf_pack(ctx.h, b[i * N:(i + 1) * N], torch.from_numpy(src).cuda(), G.DWF_F64, 1)
+            del src
+        torch.cuda.synchronize()
+        x = torch.zeros_like(b)
+        G.dwf_profile(ctx.h, True)
+        ts, _ = _timed(torch, lambda: G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p))
+        tv, st = _timed(torch, lambda: G.mg_solve(ctx.h, b, x, TOL, nr, check=False))
+        n32, ms32 = G.dwf_profile_read(ctx.h, G.K_DSLASH_F32)
+        u32 = G.dwf_profile_units(ctx.h, G.K_DSLASH_F32)
+        nco, msco = G.dwf_profile_read(ctx.h, G.K_COARSE)
+        G.dwf_profile(ctx.h, False)
+        V5 = ctx.V * LS
+        line.update({"value": (ts + tv) / nr, "config": {"workload": f"24^3x48 Ls=16 mf=0.001 heatbath beta=6.0 "
+                     f"(200 sweeps, seed 200), 12 point + {nr - 12} Z2 sources in one batch, Nvec 24, 4^4 blocks",
+                     "nrhs": nr},
+                     "setup_s": ts, "solve_s": tv, "status": st.status, "iters": st.iters, "true_res": st.true_res,
+                     "dslash_f32_gbs": FINE_BYTES_F32 * V5 * u32 / (ms32 * 1e-3) / 1e9 if n32 else None,
+                     "coarse_ms": msco, "coarse_launches": nco, "wall_s": ts + tv})
+        ctx.close()
+    else:
+        dims_l = [(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32)]
+        mf = 0.002
+        Us = [I.heatbath_links(d, 5.9, HB_SWEEPS, 300 + i) for i, d in enumerate(dims_l)]
+        bs = [I.gaussian_source(d, LS, 310 + i) for i, d in enumerate(dims_l)]
+        # one context holding all three lattices: one setup call, one solve call
+        bc = G.BatchContext(dims_l, LS, M5, mf, [torch.from_numpy(u).cuda() for u in Us])
+        canon = torch.from_numpy(np.concatenate([s.reshape(-1) for s in bs])).cuda()
+        bb = torch.empty(bc.field_elems(), dtype=torch.complex128, device="cuda")
+        G.dwf_pack(bc.h, bb, canon, G.DWF_F64, 1)
+        xb = torch.zeros_like(bb)
+        G.mg_setup(bc.h, 2, [NVEC], [BLOCK], p)  # warm-up of both paths' kernels and workspaces
+        G.mg_solve(bc.h, bb, xb, TOL, 1)
+        xb.zero_()
+        ts_b, _ = _timed(torch, lambda: G.mg_setup(bc.h, 2, [NVEC], [BLOCK], p))
+        tv_b, st_b = _timed(torch, lambda: G.mg_solve(bc.h, bb, xb, TOL, 1, check=False))
+        bc.close()
+        seq = []
+        for i, d in enumerate(dims_l):
+            ctx = G.Context(d, LS, M5, mf, torch.from_numpy(Us[i]).cuda())
+            b1 = torch.empty(ctx.field_elems, dtype=torch.complex128, device="cuda")
+            G.dwf_pack(ctx.h, b1, torch.from_numpy(bs[i]).cuda(), G.DWF_F64, 1)
+            x1 = torch.zeros_like(b1)
+            ts, _ = _timed(torch, lambda: G.mg_setup(ctx.h, 2, [NVEC], [BLOCK], p))
+            tv, st = _timed(torch, lambda: G.mg_solve(ctx.h, b1, x1, TOL, 1, check=False))
+            seq.append({"dims": d, "setup_s": ts, "solve_s": tv, "iters": st.iters, "true_res": st.true_res,
+                        "status": st.status})
+            if i == 2:
+                # 3 levels: 4^4 blocks then 2^4 (coarse 4^3x8 -> 2^3x4), Nvec 24 then 32
+                p3 = mixed_params(G)
+                p3.coarse_prec[1] = G.DWF_BF16
+                x1.zero_()
+                ts3, _ = _timed(torch, lambda: G.mg_setup(ctx.h, 3, [NVEC, 32], [BLOCK, (2, 2, 2, 2)], p3))
+                tv3, st3 = _timed(torch, lambda: G.mg_solve(ctx.h, b1, x1, TOL, 1, check=False))
+                three = {"dims": d, "levels": 3, "nvec": [NVEC, 32], "blocks": [list(BLOCK), [2, 2, 2, 2]],
+                         "setup_s": ts3, "solve_s": tv3, "iters": st3.iters, "true_res": st3.true_res,
+                         "status": st3.status, "coarse_applies": list(st3.coarse_applies)}
+            ctx.close()
+        tseq = sum(r["setup_s"] + r["solve_s"] for r in seq)
+        line.update({"value": (ts_b + tv_b) / 3,
+                     "config": {"workload": "uneven batch 8^4 + 12^3x24 + 16^3x32, Ls=16, mf=0.002, heatbath "
+                                            "beta=5.9 (200 sweeps, seeds 300-302), one Gaussian source per lattice, "
+                                            "Nvec 24, 4^4 blocks, one batch context", "nrhs": 3},
+                     "batch": {"setup_s": ts_b, "solve_s": tv_b, "iters": st_b.iters, "true_res": st_b.true_res,
+                               "status": st_b.status},
+                     "one_after_another": seq, "one_after_another_s": tseq, "batch_s": ts_b + tv_b,
+                     "three_level_16x16x16x32": three,
+                     "note": "32^3x64 with three levels is not run: its FP64 and FP32 Nvec=24 bases alone "
+                             "hold 231 GB of the 288 GB"})
+    print(json.dumps(line), flush=True)
+
+
 def profile_small(args):
     """Small device-memory cases of the timed kernels for ncu captures: the
     batched coarsest solve at the workload's coarse size (--profile-coarse) and
@@ -378,6 +491,9 @@ def main():
         return
     if args.profile_coarse or args.profile_vcycle:
         profile_small(args)
+        return
+    if args.workload != "headline":
+        run_workload(args)
         return
     import torch
     from paper_1205_2933_gb300 import dwfmg as G

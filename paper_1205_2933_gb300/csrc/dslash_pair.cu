@@ -120,13 +120,12 @@ __device__ __forceinline__ void recon2(CP acc[12], int a, const CP &u0, const CP
     }
 }
 
-// One 4D hop for both slices.  sL: the staged link (9 elements as
-// float4 (re, re, im, im), hop coefficient included); ADJ: use its adjoint.
-template <int MU, bool ADJ, int LS>
-__device__ __forceinline__ void hop2(CP acc[12], const float2 *__restrict__ row, const float4 *sL, float sig) {
-    float4 p[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) p[k] = *reinterpret_cast<const float4 *>(row + k * LS);
+// One 4D hop for both slices from the neighbour's preloaded row p (the 12
+// components of the thread's two slices).  sL: the staged link (9 elements
+// as float4 (re, re, im, im), hop coefficient included); ADJ: use its
+// adjoint.
+template <int MU, bool ADJ>
+__device__ __forceinline__ void hop2(CP acc[12], const float4 p[12], const float4 *sL, float sig) {
     CP h[6];
     project2<MU>(p, sig, h);
 #pragma unroll
@@ -161,6 +160,12 @@ __device__ __forceinline__ void hop2(CP acc[12], const float2 *__restrict__ row,
         }
         recon2<MU>(acc, a, u0, u1, sig);
     }
+}
+
+// the 12 components of a thread's two slices in one site's row
+template <int LS> __device__ __forceinline__ void ldrow(float4 p[12], const float2 *__restrict__ row) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k] = *reinterpret_cast<const float4 *>(row + k * LS);
 }
 
 // CTA = spb whole 4D sites x LS/2 threads; LS/2 divides 32 so that the
@@ -224,12 +229,13 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
     const int site = site0 + ls;
     const bool active = (ls < spb) && (site < V);
     const int row = 12 * LS;
-    float4 self[12];
-    {
-        const float2 *p = in + (size_t)(active ? site : 0) * row + s0;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) self[k] = active ? *reinterpret_cast<const float4 *>(p + k * LS) : make_float4(0, 0, 0, 0);
-    }
+    const int *sNs = sN + ls * 8;
+    // the first two hops' rows are requested together with the thread's own
+    // row; each later row is requested while the hop before it computes
+    float4 pa[12], pb[12], self[12];
+    ldrow<LS>(pa, in + (size_t)(active ? sNs[0] : 0) * row + s0);
+    ldrow<LS>(pb, in + (size_t)(active ? sNs[4] : 0) * row + s0);
+    ldrow<LS>(self, in + (size_t)(active ? site : 0) * row + s0);
     // fifth dimension.  D: -P_- psi(s+1) (components 6..11), -P_+ psi(s-1)
     // (components 0..5), wrapping with +mf.  D^+: the two projectors swap.
     const int up_lo = DAG ? 0 : 6, dn_lo = DAG ? 6 : 0;
@@ -262,16 +268,15 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
     float nrm = 0.f;
     if (!NORM || active) {
         const float4 *sLs = sL + ls * LSTRIDE;
-        const int *sNs = sN + ls * 8;
         const float fs = DAG ? 1.f : -1.f;  // sig of the forward hops
-        hop2<0, false, LS>(acc, in + (size_t)sNs[0] * row + s0, sLs + 0 * 9, fs);
-        hop2<0, true, LS>(acc, in + (size_t)sNs[4] * row + s0, sLs + 4 * 9, -fs);
-        hop2<1, false, LS>(acc, in + (size_t)sNs[1] * row + s0, sLs + 1 * 9, fs);
-        hop2<1, true, LS>(acc, in + (size_t)sNs[5] * row + s0, sLs + 5 * 9, -fs);
-        hop2<2, false, LS>(acc, in + (size_t)sNs[2] * row + s0, sLs + 2 * 9, fs);
-        hop2<2, true, LS>(acc, in + (size_t)sNs[6] * row + s0, sLs + 6 * 9, -fs);
-        hop2<3, false, LS>(acc, in + (size_t)sNs[3] * row + s0, sLs + 3 * 9, fs);
-        hop2<3, true, LS>(acc, in + (size_t)sNs[7] * row + s0, sLs + 7 * 9, -fs);
+        hop2<0, false>(acc, pa, sLs + 0 * 9, fs);  ldrow<LS>(pa, in + (size_t)sNs[1] * row + s0);
+        hop2<0, true>(acc, pb, sLs + 4 * 9, -fs);  ldrow<LS>(pb, in + (size_t)sNs[5] * row + s0);
+        hop2<1, false>(acc, pa, sLs + 1 * 9, fs);  ldrow<LS>(pa, in + (size_t)sNs[2] * row + s0);
+        hop2<1, true>(acc, pb, sLs + 5 * 9, -fs);  ldrow<LS>(pb, in + (size_t)sNs[6] * row + s0);
+        hop2<2, false>(acc, pa, sLs + 2 * 9, fs);  ldrow<LS>(pa, in + (size_t)sNs[3] * row + s0);
+        hop2<2, true>(acc, pb, sLs + 6 * 9, -fs);  ldrow<LS>(pb, in + (size_t)sNs[7] * row + s0);
+        hop2<3, false>(acc, pa, sLs + 3 * 9, fs);
+        hop2<3, true>(acc, pb, sLs + 7 * 9, -fs);
         float2 *o = out + (size_t)site * row + s0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
