@@ -109,6 +109,10 @@ typedef struct {
                                except along lattice directions of extent 1;
                                the V-cycle restricts D^+ r instead of r, and several right-hand
                                sides are solved one after another) (0) */
+    int graph;              /* 1: the batched V-cycle (FP32, two levels, several right-hand sides)
+                               is captured once per solve call, batch width and direction slot as a
+                               CUDA graph and replayed; 0: launched kernel by kernel.  Ignored for a
+                               lattice of a batch context (dwf_create with nlat > 1) (1) */
 } mg_params;
 
 typedef struct {

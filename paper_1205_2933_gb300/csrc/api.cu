@@ -69,6 +69,7 @@ void mg_default_params(mg_params *p) {
     p->basis_prec = DWF_F32;
     p->seed = 1u;
     p->cycle = 0;
+    p->graph = 1;
 }
 
 const char *dwf_strerror(dwf_status s) {
@@ -359,8 +360,8 @@ dwf_status dwf_profile_read(dwf_ctx *c, int kernel_class, long long *launches, d
         double ms = 0.0;
         for (auto &r : c->prof_rec)
             if (r.cls == kernel_class) {
-                float t = 0.f;
-                DWF_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+                float t = r.ms;
+                if (r.a) DWF_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
                 ms += t;
                 ++n;
             }

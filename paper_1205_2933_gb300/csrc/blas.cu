@@ -195,6 +195,7 @@ template <typename T> void bnorm2(dwf_ctx *c, int slot, const T *x, int64_t n) {
 
 static unsigned long long g_launches = 0;
 void note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+void note_launches(unsigned long long n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 static cudaEvent_t take_event(dwf_ctx *c) {
@@ -217,14 +218,16 @@ ProfScope::ProfScope(dwf_ctx *ctx, int k, int nunits) : c(ctx), cls(k), units(nu
 
 ProfScope::~ProfScope() {
     if (!a) return;
-    if (cudaEventRecord(b, c->stream) == cudaSuccess) c->prof_rec.push_back(ProfRecord{cls, a, b, units});
+    if (cudaEventRecord(b, c->stream) == cudaSuccess)
+        (c->cap_rec ? *c->cap_rec : c->prof_rec).push_back(ProfRecord{cls, a, b, units, -1.f});
 }
 
 void prof_reset(dwf_ctx *c) {
-    for (auto &r : c->prof_rec) {
-        c->prof_pool.push_back(r.a);
-        c->prof_pool.push_back(r.b);
-    }
+    for (auto &r : c->prof_rec)
+        if (r.a) {
+            c->prof_pool.push_back(r.a);
+            c->prof_pool.push_back(r.b);
+        }
     c->prof_rec.clear();
 }
 

@@ -30,6 +30,7 @@
 
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "mg.cuh"
 
@@ -692,8 +693,50 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
     int per_sm = 0;
     DWF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TCT, smem));
     DWF_REQUIRE(per_sm >= 1, DWF_ECUDA, "tensor-core coarse solver cannot be co-resident");
-    int64_t nblk = (L.lg.g.V + 3) / 4;
-    nblk = std::max<int64_t>(1, std::min<int64_t>(nblk, c->sm_count));
+    // The grid (sites per CTA) is the solver's tile: fewer CTAs make the grid
+    // barriers cheaper and the per-CTA stencil pipeline longer.  The first
+    // solve of each batch width on a coarse operator times the co-resident
+    // candidates of 2, 4, 8, ... sites per CTA on its own inputs (every trial
+    // starts from x = 0, so they are repeatable) and keeps the fastest; the
+    // solve itself then runs with it.
+    const int64_t V = L.lg.g.V, maxg = (int64_t)per_sm * c->sm_count;
+    int nblk = L.tc_ctas[nb];
+    if (nblk == 0) {
+        std::vector<int> cand;
+        for (int64_t s = 2; s <= 64; s *= 2) {
+            const int64_t g = (V + s - 1) / s;
+            if (g <= maxg && g <= c->sm_count && (cand.empty() || cand.back() != (int)g)) cand.push_back((int)g);
+            if (g == 1) break;
+        }
+        if (cand.empty()) cand.push_back((int)std::max<int64_t>(1, std::min<int64_t>(V, c->sm_count)));
+        nblk = cand[0];
+        if (cand.size() > 1) {
+            if (!c->tc_trial.p) c->tc_trial.alloc(sizeof(int));
+            TcArgs t = a;
+            t.iters = c->tc_trial.as<int>();
+            void *targs[] = {&t};
+            cudaEvent_t e0, e1;
+            DWF_CUDA(cudaEventCreate(&e0));
+            DWF_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            for (int g : cand) {
+                DWF_CUDA(cudaEventRecord(e0, c->stream));
+                DWF_CUDA(coop_launch(c, fn, dim3((unsigned)g), dim3(TCT), targs, smem));
+                DWF_CHECK_LAUNCH();
+                DWF_CUDA(cudaEventRecord(e1, c->stream));
+                DWF_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                DWF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    nblk = g;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        L.tc_ctas[nb] = nblk;
+    }
     DWF_CUDA(coop_launch(c, fn, dim3((unsigned)nblk), dim3(TCT), kargs, smem));
     DWF_CHECK_LAUNCH();
 }
@@ -733,6 +776,7 @@ void check_tc_timeout(dwf_ctx *c) {
 // Nvec the tensor-core solver handles (8, 16, 24, 32); other levels get none.
 void build_tc_images(dwf_ctx *c, Level &L) {
     const int n = L.lg.ncomp;
+    for (int &g : L.tc_ctas) g = 0;  // a new operator is tuned anew
     if (L.yprec != DWF_BF16 || L.npts != 9 || !(n == 8 || n == 16 || n == 24 || n == 32)) {
         L.Ytc.release();
         return;

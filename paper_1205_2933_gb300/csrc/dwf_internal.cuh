@@ -71,6 +71,7 @@ struct Error {
     } while (0)
 
 void note_launch();
+void note_launches(unsigned long long n);  // kernels launched by a replayed graph
 #define DWF_CHECK_LAUNCH()               \
     do {                                 \
         DWF_CUDA(cudaGetLastError());    \
@@ -147,8 +148,9 @@ enum KernelClass { K_DSLASH_F64 = 0, K_DSLASH_F32 = 1, K_RESTRICT = 2, K_PROLONG
 
 struct ProfRecord {
     int cls;
-    cudaEvent_t a, b;
-    int units;  // fields (right-hand sides) the bracketed launch processed
+    cudaEvent_t a, b;  // null for a launch inside a replayed graph: ms holds its time
+    int units;         // fields (right-hand sides) the bracketed launch processed
+    float ms;
 };
 
 }  // namespace dwf
@@ -175,6 +177,7 @@ struct dwf_ctx {
     // context: the solves' scratch is freed before the word is read back)
     dwf::DevBuf tc_err;
     bool tc_used = false;
+    dwf::DevBuf tc_trial;  // iteration counter of the tensor-core solver's tuning trials
     // A batch of independent lattices (dwf_create with nlat > 1): one member
     // context per lattice, each on a stream of its own; the batch context
     // itself holds no lattice.  Cooperative launches of all members pass
@@ -187,6 +190,7 @@ struct dwf_ctx {
     // event profiler
     bool prof = false;
     std::vector<dwf::ProfRecord> prof_rec;
+    std::vector<dwf::ProfRecord> *cap_rec = nullptr;  // while a graph is captured: its launches' records
     std::vector<cudaEvent_t> prof_pool;
 };
 

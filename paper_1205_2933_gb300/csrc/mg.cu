@@ -10,6 +10,7 @@
 // (double for the plain method, float for the mixed one); coarse stencils use
 // the link precision chosen per level; the outer solution and residual, the
 // block Gram-Schmidt and the coarse-operator construction are FP64.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -774,7 +775,17 @@ template <typename R> class BatchRunner {
     }
 
     ~BatchRunner() {
-        if (side[0]) cudaStreamSynchronize(c->stream);
+        if (side[0] || gstream) cudaStreamSynchronize(c->stream);
+        for (auto &g : graphs) {
+            cudaGraphExecDestroy(g.exec);
+            for (auto &r : g.rec) {
+                c->prof_pool.push_back(r.a);
+                c->prof_pool.push_back(r.b);
+            }
+        }
+        if (gstream) cudaStreamDestroy(gstream);
+        if (g_fork) cudaEventDestroy(g_fork);
+        if (g_join) cudaEventDestroy(g_join);
         for (int i = 0; i < NS; ++i) {
             if (side[i]) cudaStreamDestroy(side[i]);
             if (ev_join[i]) cudaEventDestroy(ev_join[i]);
@@ -782,8 +793,110 @@ template <typename R> class BatchRunner {
         if (ev_fork) cudaEventDestroy(ev_fork);
     }
 
-    // one V-cycle for every right-hand side (nu_1 = 0)
+    // The batched V-cycle as CUDA graphs: the V-cycle for one (output, input,
+    // batch width) is captured at its first use and replayed afterwards, so
+    // its ~80 launches (transfers, the coarsest solve, the smoother's Dslash
+    // and vector kernels) leave the host as one.  A batch width is first run
+    // without capture once: the coarsest solver's tuning runs, and every
+    // workspace, side stream and scratch buffer is allocated there, outside
+    // any capture.  Launches the event profiler brackets inside a graph are
+    // timed after each replay from the graph's own events.
+    struct VGraph {
+        T *x;
+        const T *b;
+        int nr;
+        cudaGraphExec_t exec;
+        std::vector<ProfRecord> rec;
+        long long a64, a32;        // fine applications the graph performs
+        unsigned long long kernels; // kernels it launches
+    };
+    std::vector<VGraph> graphs;
+    std::vector<int> eager_nr;  // batch widths already run without capture
+    // graphs are captured and replayed on a stream of their own (capture is
+    // not possible on the legacy default stream a caller may have given),
+    // forked from and joined to the context's stream around every use
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t g_fork = nullptr, g_join = nullptr;
+
+    void graph_enter() {
+        if (!gstream) {
+            DWF_CUDA(cudaStreamCreateWithFlags(&gstream, cudaStreamNonBlocking));
+            DWF_CUDA(cudaEventCreateWithFlags(&g_fork, cudaEventDisableTiming));
+            DWF_CUDA(cudaEventCreateWithFlags(&g_join, cudaEventDisableTiming));
+        }
+        DWF_CUDA(cudaEventRecord(g_fork, c->stream));
+        DWF_CUDA(cudaStreamWaitEvent(gstream, g_fork, 0));
+    }
+    void graph_leave(cudaStream_t main) {
+        c->stream = main;
+        DWF_CUDA(cudaEventRecord(g_join, gstream));
+        DWF_CUDA(cudaStreamWaitEvent(main, g_join, 0));
+    }
+
     void vcycle_b(T *x, const T *b) {
+        if (!mg.p.graph || c->gate) return vcycle_body(x, b);
+        for (auto &g : graphs)
+            if (g.x == x && g.b == b && g.nr == nr) return replay(g);
+        if (std::find(eager_nr.begin(), eager_nr.end(), nr) == eager_nr.end()) {
+            eager_nr.push_back(nr);
+            return vcycle_body(x, b);
+        }
+        VGraph g{x, b, nr, nullptr, {}, 0, 0, 0};
+        cudaGraph_t graph = nullptr;
+        const long long a64 = c->applies64, a32 = c->applies32;
+        const unsigned long long k0 = launch_count();
+        cudaStream_t main = c->stream;
+        graph_enter();
+        c->stream = gstream;
+        DWF_CUDA(cudaStreamBeginCapture(gstream, cudaStreamCaptureModeThreadLocal));
+        c->cap_rec = &g.rec;
+        try {
+            vcycle_body(x, b);
+        } catch (...) {
+            c->cap_rec = nullptr;
+            cudaStreamEndCapture(gstream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            c->stream = main;
+            throw;
+        }
+        c->cap_rec = nullptr;
+        // the capture ran nothing: its counts are booked at every replay
+        g.a64 = c->applies64 - a64;
+        g.a32 = c->applies32 - a32;
+        g.kernels = launch_count() - k0;
+        c->applies64 = a64;
+        c->applies32 = a32;
+        cudaError_t e = cudaStreamEndCapture(gstream, &graph);
+        c->stream = main;
+        DWF_CUDA(e);
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        DWF_CUDA(e);
+        graph_leave(main);
+        graphs.push_back(std::move(g));
+        replay(graphs.back());
+    }
+
+    void replay(VGraph &g) {
+        cudaStream_t main = c->stream;
+        graph_enter();
+        DWF_CUDA(cudaGraphLaunch(g.exec, gstream));
+        graph_leave(main);
+        c->applies64 += g.a64;
+        c->applies32 += g.a32;
+        note_launches(g.kernels);
+        if (c->prof && !g.rec.empty()) {
+            DWF_CUDA(cudaStreamSynchronize(c->stream));
+            for (const ProfRecord &r : g.rec) {
+                float ms = 0.f;
+                DWF_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+                c->prof_rec.push_back(ProfRecord{r.cls, nullptr, nullptr, r.units, ms});
+            }
+        }
+    }
+
+    // one V-cycle for every right-hand side (nu_1 = 0)
+    void vcycle_body(T *x, const T *b) {
         Level &L = mg.lev[0];
         const int64_t N = n(0), NT = N * nr, Nc = n(1);
         T *res = wsb(0, 4), *sm = wsb(0, 5);
@@ -1033,17 +1146,30 @@ template <typename R> bool batch_eligible(const MGState &mg, int nrhs) {
 // memory holds (9 + 2 * restart fine fields in precision R and two FP64
 // fields per right-hand side, counting the batch workspaces already held).
 // 1 means: solve one at a time.
+// The widest batch (at most 32, at most nrhs) whose fine-level workspaces fit
+// in 90% of the free device memory.  A workspace already held is reused when
+// it is large enough and replaced when it is not (the old one is freed
+// first), so only the growth of each workspace the batch uses counts: the
+// FP32 fields 0-5, 8-10 (smoother, V-cycle, setup relaxation) and, for a
+// solve, the 2 x restart GCR directions from 16 on and the two FP64 fields.
 template <typename R> int batch_width(const MGState &mg, int nrhs, bool solve) {
     const int64_t N = mg.lev[0].lg.nelem;
     const int restart = std::min(mg.p.outer_restart, 32);
-    const double per = (double)N * ((solve ? 9 + 2 * restart : 8) * sizeof(C<R>) + (solve ? 2 * sizeof(double2) : 0));
-    double held = 0;
-    for (const DevBuf &d : mg.wsb[0]) held += (double)d.bytes;
-    for (const DevBuf &d : mg.wsb64) held += (double)d.bytes;
+    std::vector<int> used = {0, 1, 2, 3, 4, 5, 8, 9, 10};
+    if (solve)
+        for (int i = 0; i < 2 * restart; ++i) used.push_back(16 + i);
+    auto held = [&](const std::vector<DevBuf> &v, int i) { return i < (int)v.size() ? (double)v[i].bytes : 0.0; };
+    auto growth = [&](int nb) {
+        double g = 0;
+        for (int i : used) g += std::max(0.0, (double)N * nb * sizeof(C<R>) - held(mg.wsb[0], i));
+        if (solve)
+            for (int i = 0; i < 2; ++i) g += std::max(0.0, (double)N * nb * sizeof(double2) - held(mg.wsb64, i));
+        return g;
+    };
     size_t fr = 0, tot = 0;
     DWF_CUDA(cudaMemGetInfo(&fr, &tot));
     int nb = std::min(32, nrhs);
-    while (nb > 1 && nb * per - held > 0.9 * (double)fr) --nb;
+    while (nb > 1 && growth(nb) > 0.9 * (double)fr) --nb;
     return nb;
 }
 
@@ -1073,7 +1199,14 @@ dwf_status setup_t(dwf_ctx *c, MGState &mg, int levels, const void *start, bool 
 // DWF_BATCH=0 in the environment turns it off.
 template <typename R>
 dwf_status solve_t(dwf_ctx *c, MGState &mg, double2 *b, double2 *x, double tol, int nrhs, mg_stats &st) {
-    const int width = batch_eligible<R>(mg, nrhs) ? batch_width<R>(mg, nrhs, true) : 1;
+    int width = batch_eligible<R>(mg, nrhs) ? batch_width<R>(mg, nrhs, true) : 1;
+    if (batch_eligible<R>(mg, nrhs) && width < std::min(nrhs, 32) && !mg.wsb[0].empty()) {
+        // memory-bound: the workspaces another width left (e.g. the setup's
+        // relaxation of all start vectors) give way to the solve's own
+        for (int l = 0; l < MAX_LEVELS; ++l) mg.wsb[l].clear();
+        mg.wsb64.clear();
+        width = batch_width<R>(mg, nrhs, true);
+    }
     if (width > 1) {
         const int64_t N = mg.lev[0].lg.nelem;
         dwf_status worst = DWF_OK;

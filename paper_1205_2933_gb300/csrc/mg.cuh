@@ -35,6 +35,7 @@ struct Level {
     int npts = 9;
     DevBuf Y64, Y32, Y16;  // Y16 holds bf16 or fp16 pairs per coarse_prec
     DevBuf Ytc;            // BF16 stencil as per-site tensor-core operand images (coarse_gcr_tc.cu)
+    mutable int tc_ctas[17] = {0};  // grid of the tensor-core solver picked by timing, per batch width (0: not yet)
     dwf_prec yprec = DWF_F64;
     // block reductions scratch: [Vc][nv][nv] complex FP64
     DevBuf G, F, Rinv;

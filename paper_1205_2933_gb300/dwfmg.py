@@ -41,6 +41,7 @@ class mg_params(ctypes.Structure):
         ("seed", ctypes.c_uint32),
         ("cycle", ctypes.c_int),
         ("coarsen", ctypes.c_int),
+        ("graph", ctypes.c_int),
     ]
 
 

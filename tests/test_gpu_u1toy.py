@@ -31,15 +31,18 @@ def _embedded(dims2, beta, sweeps, seed):
     return U, dims4
 
 
+@pytest.mark.parametrize("sp", [0, 1], ids=["f64", "f32"])
 @pytest.mark.parametrize("coarsen", [0, 1], ids=["rdp", "squared"])
-def test_embedded_coarse_operator_parity(G, coarsen):
+def test_embedded_coarse_operator_parity(G, coarsen, sp):
+    """FP64 construction to rounding; with the FP32 V-cycle (FP32 products,
+    FP64 sums) to 1e-5, as on the 4D lattices."""
     from gpu_util import ctx_for, rel_max
     U, dims4 = _embedded((8, 8), 3.0, 20, 31)
     Ls, mf, nvec, block = 4, 0.05, 8, (4, 1, 1, 4)
     ctx = ctx_for(U, dims4, Ls, M5, mf)
     op = OM.FineOp(oracle.DWF(U, dims4, Ls, M5, mf))
     rv = I.random_vectors(nvec // 2, dims4, Ls, 32)
-    p = M._params(G, setup_iters0=0, setup_sweeps=0, coarsen=coarsen)
+    p = M._params(G, setup_iters0=0, setup_sweeps=0, coarsen=coarsen, smoother_prec=sp)
     G.mg_setup(ctx.h, 2, [nvec], [block], p, torch.from_numpy(rv).cuda())
     mg = OM.adaptive_setup(op, M._oracle_params([nvec], [block], p), [rv.reshape((nvec // 2,) + op.shape)])
     d, n = G.mg_level_info(ctx.h, 1)
@@ -48,7 +51,7 @@ def test_embedded_coarse_operator_parity(G, coarsen):
     Y = torch.empty(4 * npts * n * n, dtype=torch.complex128, device="cuda")
     G.mg_get_coarse_links(ctx.h, 1, Y)
     Yref = mg.levels[1].op.Y.reshape(4, npts, n, n)
-    assert rel_max(Y.cpu().numpy().reshape(4, npts, n, n), Yref) < 1e-12
+    assert rel_max(Y.cpu().numpy().reshape(4, npts, n, n), Yref) < (1e-12 if sp == 0 else 1e-5)
     ctx.close()
 
 
