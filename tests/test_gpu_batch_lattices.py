@@ -83,7 +83,10 @@ def test_batch_apply_and_layout(G):
 def test_batch_solve_matches_oracle_and_single(G, sp, cp):
     """Three uneven lattices, two right-hand sides each, in one mg_setup and
     one mg_solve: every solution equals the oracle's to 1e-8 (true residual
-    <= 1e-10) and the solution of the lattice solved in a context of its own."""
+    <= 1e-10) and, to the same bound, the solution of the lattice solved in a
+    context of its own (FP64: to 1e-10; with the FP32 V-cycle the two contexts
+    may time their tensor-core coarse solvers onto different grids, whose
+    reduction orders differ in rounding)."""
     from gpu_util import ctx_for, to_internal, to_canonical, rel_norm
     Ls, mf, nrhs = 8, 0.1, 2
     links = [I.epsilon_links(d, 0.3, 11 + i) for i, d in enumerate(DIMS3)]
@@ -110,7 +113,7 @@ def test_batch_solve_matches_oracle_and_single(G, sp, cp):
         for r in range(nrhs):
             xo, info = OM.cgnr(op.apply, op.apply_dag, bs[i][r].reshape(op.shape), tol=1e-13, maxiter=50000)
             assert rel_norm(xs[i][r], xo.reshape(bs[i][r].shape)) < 1e-8
-            assert rel_norm(xs[i][r], x1c[r]) < 1e-10
+            assert rel_norm(xs[i][r], x1c[r]) < (1e-10 if sp == 0 else 1e-8)
         ctx.close()
     bc.close()
 
