@@ -209,16 +209,22 @@ static cudaEvent_t take_event(dwf_ctx *c) {
     return e;
 }
 
+// Inside a graph capture the events are recorded as event-record nodes of
+// the graph (cudaEventRecordExternal), so that every replay records them.
+static cudaError_t record(dwf_ctx *c, cudaEvent_t e) {
+    return c->cap_rec ? cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal) : cudaEventRecord(e, c->stream);
+}
+
 ProfScope::ProfScope(dwf_ctx *ctx, int k, int nunits) : c(ctx), cls(k), units(nunits) {
     if (!c->prof) return;
     a = take_event(c);
     b = take_event(c);
-    DWF_CUDA(cudaEventRecord(a, c->stream));
+    DWF_CUDA(record(c, a));
 }
 
 ProfScope::~ProfScope() {
     if (!a) return;
-    if (cudaEventRecord(b, c->stream) == cudaSuccess)
+    if (record(c, b) == cudaSuccess)
         (c->cap_rec ? *c->cap_rec : c->prof_rec).push_back(ProfRecord{cls, a, b, units, -1.f});
 }
 

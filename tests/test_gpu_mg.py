@@ -520,3 +520,29 @@ def test_squared_setup_rejects_unsupported(G):
     with pytest.raises(G.DWFError):
         G.mg_setup(ctx.h, 2, [8], [(1, 2, 2, 2)], p)
     ctx.close()
+
+
+def test_batched_vcycle_graphs_and_profiler(G):
+    """The batched V-cycle replayed as CUDA graphs gives the solution of the
+    kernel-by-kernel path, and the event profiler and application counters
+    see the replayed launches: with the profiler on, both paths report the
+    same fine applications, and the profiler's FP32 Dslash units match them."""
+    from gpu_util import to_internal, to_canonical, rel_norm
+    res = {}
+    for graph in (0, 1):
+        c = Case(G, **SMALL, setup_iters0=20, setup_sweeps=0, smoother_prec=G.DWF_F32,
+                 coarse_prec=[G.DWF_BF16], graph=graph)
+        bs = np.stack([I.gaussian_source(c.dims, c.Ls, 90 + i) for i in range(3)])
+        bt = to_internal(c.ctx, bs, nrhs=3)
+        xt = torch.zeros_like(bt)
+        G.dwf_profile(c.ctx.h, True)
+        st = G.mg_solve(c.ctx.h, bt, xt, 1e-10, nrhs=3)
+        n32, ms32 = G.dwf_profile_read(c.ctx.h, G.K_DSLASH_F32)
+        u32 = G.dwf_profile_units(c.ctx.h, G.K_DSLASH_F32)
+        G.dwf_profile(c.ctx.h, False)
+        assert st.true_res <= 1e-10 and n32 > 0 and ms32 > 0
+        assert u32 == st.fine_applies_f32
+        res[graph] = (to_canonical(c.ctx, xt, bs.shape, nrhs=3), st.iters, st.fine_applies_f32)
+        c.close()
+    assert rel_norm(res[1][0], res[0][0]) < 1e-8
+    assert abs(res[1][1] - res[0][1]) <= 1 and abs(res[1][2] - res[0][2]) <= 2 * 20 * 3
