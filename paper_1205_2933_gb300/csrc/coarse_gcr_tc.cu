@@ -28,6 +28,8 @@
 // the caller reports DWF_ETIMEOUT.
 #include <cooperative_groups.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -71,7 +73,7 @@ struct TcArgs {
     const float2 *b;            // [nb][Nf]
     float2 *x, *r;              // [nb][Nf]
     float2 *Z, *W;              // [restart][nb][Nf]
-    float2 *part;               // [2][gridDim.x][TMAXV] per-CTA partial sums, two alternating buffers
+    float2 *part;               // [2][TMAXV][gridDim.x rounded up to even] per-CTA partial sums, two alternating buffers
     int *err;                   // set on an expired wait
     int *iters;
     double tol;
@@ -355,10 +357,14 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
     // CTA adds all CTAs' partials in the same order, so all hold identical
     // totals and take identical decisions.  The two buffers keep a CTA that
     // runs ahead to the next reduction off the partials others still read.
+    // Partials are stored value-major with an even row stride, so a thread
+    // reads its value's partials two CTAs at a time in 16-byte loads, many in
+    // flight, and still adds them in CTA order.
     int phase = 0;
+    const int pstride = (nblk + 1) & ~1;
     auto finish = [&](int nv) {
         __syncthreads();
-        float2 *pb = a.part + (size_t)(phase & 1) * TMAXV * nblk;
+        float2 *pb = a.part + (size_t)(phase & 1) * TMAXV * pstride;
         for (int p = tid; p <= nv; p += TCT) {
             float2 v = make_float2(0.f, 0.f);
             if (p < nv) {
@@ -369,18 +375,23 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
             } else {
                 v.x = bad ? 1.f : 0.f;
             }
-            pb[(size_t)blockIdx.x * TMAXV + p] = v;
+            pb[(size_t)p * pstride + blockIdx.x] = v;
         }
         if (tid == 0 && bad) atomicOr(a.err, 1);
         __threadfence();
         grid.sync();
         for (int p = tid; p <= nv; p += TCT) {
+            const float4 *row = reinterpret_cast<const float4 *>(pb + (size_t)p * pstride);
             float sx = 0.f, sy = 0.f;
-#pragma unroll 8
-            for (int j = 0; j < nblk; ++j) {
-                const float2 q = __ldcg(pb + (size_t)j * TMAXV + p);
-                sx += q.x;
-                sy += q.y;
+#pragma unroll 16
+            for (int q = 0; q < pstride / 2; ++q) {
+                const float4 w = __ldcg(row + q);
+                sx += w.x;
+                sy += w.y;
+                if (2 * q + 1 < nblk) {
+                    sx += w.z;
+                    sy += w.w;
+                }
             }
             if (p < nv) tot[p] = make_double2(sx, sy);
             else quit = sx > 0.f;
@@ -697,8 +708,8 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
     // barriers cheaper and the per-CTA stencil pipeline longer.  The first
     // solve of each batch width on a coarse operator times the co-resident
     // candidates of 2, 4, 8, ... sites per CTA on its own inputs (every trial
-    // starts from x = 0, so they are repeatable) and keeps the fastest; the
-    // solve itself then runs with it.
+    // starts from x = 0, so they are repeatable; one untimed run first warms
+    // the caches) and keeps the fastest; the solve itself then runs with it.
     const int64_t V = L.lg.g.V, maxg = (int64_t)per_sm * c->sm_count;
     int nblk = L.tc_ctas[nb];
     if (nblk == 0) {
@@ -718,6 +729,8 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
             cudaEvent_t e0, e1;
             DWF_CUDA(cudaEventCreate(&e0));
             DWF_CUDA(cudaEventCreate(&e1));
+            DWF_CUDA(coop_launch(c, fn, dim3((unsigned)cand[0]), dim3(TCT), targs, smem));
+            DWF_CHECK_LAUNCH();
             float best = 1e30f;
             for (int g : cand) {
                 DWF_CUDA(cudaEventRecord(e0, c->stream));
@@ -727,6 +740,9 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
                 DWF_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
                 DWF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (const char *v = getenv("DWF_VERBOSE"); v && atoi(v) > 0)
+                    fprintf(stderr, "[dwfmg] tensor-core coarse solve, %d right-hand sides: %d CTAs %.3f ms\n", nb, g,
+                            ms);
                 if (ms < best) {
                     best = ms;
                     nblk = g;

@@ -155,3 +155,28 @@ def test_batched_solve_12_rhs_bench_parameters(G):
         res = np.linalg.norm(bs[r] - D.D(x[r])) / np.linalg.norm(bs[r])
         assert res <= 1.0001e-10, (r, res)
     ctx.close()
+
+
+@pytest.mark.parametrize("nvec", [16, 32])
+def test_vcycle_batch_tensor_core_other_nvec(G, nvec):
+    """The tensor-core coarsest solver's other instantiations (Nvec 16 and 32,
+    one and two 8-row groups more than Nvec 8 and 24): the batched V-cycle of
+    five right-hand sides (padded to eight tensor-core columns per part)
+    against the oracle's V-cycle on the BF16-rounded coarse operator."""
+    from gpu_util import to_internal, to_canonical, rel_norm
+    c = M.Case(G, dims=(4, 4, 4, 4), Ls=8, mf=0.1, nvec=[nvec], block=[(2, 2, 2, 2)], setup_iters0=10,
+               setup_sweeps=0, smoother_prec=G.DWF_F32, coarse_prec=[G.DWF_BF16], coarsest_tol=0.0,
+               coarsest_maxiter=8, nu_post=4)
+    mg = c.mg
+    mg.levels[1].op = _rounded_coarse_op(c)  # the oracle's operator with the library's BF16 rounding
+    nr = 5
+    bs = np.stack([I.gaussian_source(c.dims, c.Ls, 700 + r) for r in range(nr)])
+    bt = to_internal(c.ctx, bs, nrhs=nr)
+    xb = torch.empty_like(bt)
+    G.mg_vcycle_batch(c.ctx.h, xb, bt, nr)
+    got = to_canonical(c.ctx, xb, bs.shape, nrhs=nr)
+    for r in range(nr):
+        ref = mg.vcycle(0, bs[r].reshape(c.op.shape)).reshape(bs[r].shape)
+        e = rel_norm(got[r], ref)
+        assert e < 1e-4, (r, e)
+    c.close()
