@@ -180,7 +180,7 @@ __global__ void cg_p_b_kernel(T *__restrict__ p, const T *__restrict__ z, const 
 //   px: a as above, b = s[inew] / s[izz]; x += a p; p = z + b p
 //   x:  x += a p (the last iteration, whose residual is not needed)
 template <typename T>
-__global__ void cg_r_b_kernel(T *__restrict__ rr, const T *__restrict__ w, const double *__restrict__ s, int base,
+__global__ void cg_r_b_kernel(T *rout, const T *rin, const T *__restrict__ w, const double *__restrict__ s, int base,
                               int stride, int izz, int iww, int64_t n) {
     using R = typename RealB<T>::type;
     const int r = blockIdx.y;
@@ -188,17 +188,17 @@ __global__ void cg_r_b_kernel(T *__restrict__ rr, const T *__restrict__ w, const
     const double ww = s[base + r * stride + iww];
     const R a = ww > 0.0 ? (R)(s[base + r * stride + izz] / ww) : R(0);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T rv = rr[off + i];
+        T rv = rin[off + i];
         const T wv = w[off + i];
         rv.x -= a * wv.x;
         rv.y -= a * wv.y;
-        rr[off + i] = rv;
+        rout[off + i] = rv;
     }
 }
 template <typename T>
-__global__ void cg_px_b_kernel(T *__restrict__ x, T *__restrict__ p, const T *__restrict__ z,
+__global__ void cg_px_b_kernel(T *__restrict__ x, T *pout, const T *pin, const T *__restrict__ z,
                                const double *__restrict__ s, int base, int stride, int izz, int iww, int inew,
-                               int64_t n, int last) {
+                               int64_t n, int last, int xinit) {
     using R = typename RealB<T>::type;
     const int r = blockIdx.y;
     const size_t off = (size_t)r * n;
@@ -206,15 +206,22 @@ __global__ void cg_px_b_kernel(T *__restrict__ x, T *__restrict__ p, const T *__
     const R a = ww > 0.0 ? (R)(zz / ww) : R(0);
     const R b = (!last && zz > 0.0) ? (R)(s[base + r * stride + inew] / zz) : R(0);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T pv = p[off + i], xv = x[off + i];
-        xv.x += a * pv.x;
-        xv.y += a * pv.y;
+        T pv = pin[off + i];
+        T xv;
+        if (xinit) {
+            xv.x = a * pv.x;
+            xv.y = a * pv.y;
+        } else {
+            xv = x[off + i];
+            xv.x += a * pv.x;
+            xv.y += a * pv.y;
+        }
         x[off + i] = xv;
         if (!last) {
             const T zv = z[off + i];
             pv.x = zv.x + b * pv.x;
             pv.y = zv.y + b * pv.y;
-            p[off + i] = pv;
+            pout[off + i] = pv;
         }
     }
 }
@@ -355,18 +362,18 @@ void cg_p_b(dwf_ctx *c, T *p, const T *z, int base, int stride, int inew, int io
 }
 
 template <typename T>
-void cg_r_b(dwf_ctx *c, T *r, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs) {
+void cg_r_b(dwf_ctx *c, T *r, const T *rin, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs) {
     dim3 g = grid_b(c, n, nrhs, 16);
-    cg_r_b_kernel<T><<<g, BT, 0, c->stream>>>(r, w, c->scal.as<double>(), base, stride, izz, iww, n);
+    cg_r_b_kernel<T><<<g, BT, 0, c->stream>>>(r, rin, w, c->scal.as<double>(), base, stride, izz, iww, n);
     DWF_CHECK_LAUNCH();
 }
 
 template <typename T>
-void cg_px_b(dwf_ctx *c, T *x, T *p, const T *z, int base, int stride, int izz, int iww, int inew, int64_t n, int nrhs,
-             bool last) {
+void cg_px_b(dwf_ctx *c, T *x, T *pout, const T *pin, const T *z, int base, int stride, int izz, int iww, int inew,
+             int64_t n, int nrhs, bool last, bool xinit) {
     dim3 g = grid_b(c, n, nrhs, 16);
-    cg_px_b_kernel<T><<<g, BT, 0, c->stream>>>(x, p, z, c->scal.as<double>(), base, stride, izz, iww, inew, n,
-                                               last ? 1 : 0);
+    cg_px_b_kernel<T><<<g, BT, 0, c->stream>>>(x, pout, pin, z, c->scal.as<double>(), base, stride, izz, iww, inew,
+                                               n, last ? 1 : 0, xinit ? 1 : 0);
     DWF_CHECK_LAUNCH();
 }
 
@@ -400,8 +407,9 @@ template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const d
     template void multiaxpy_b<T>(dwf_ctx *, T *, T *const *, int, int, int, double, int64_t, int);            \
     template void cg_xr_b<T>(dwf_ctx *, T *, T *, const T *, const T *, int, int, int, int, int64_t, int);    \
     template void cg_p_b<T>(dwf_ctx *, T *, const T *, int, int, int, int, int64_t, int);                     \
-    template void cg_r_b<T>(dwf_ctx *, T *, const T *, int, int, int, int, int64_t, int);                     \
-    template void cg_px_b<T>(dwf_ctx *, T *, T *, const T *, int, int, int, int, int, int64_t, int, bool);     \
+    template void cg_r_b<T>(dwf_ctx *, T *, const T *, const T *, int, int, int, int, int64_t, int);          \
+    template void cg_px_b<T>(dwf_ctx *, T *, T *, const T *, const T *, int, int, int, int, int, int64_t, int, bool, \
+                             bool);                                                                            \
     template void axpy_b<T>(dwf_ctx *, T *, const T *, const double2 *, int64_t, int);                        \
     template void gcr_wr_b<T>(dwf_ctx *, T *, T *, const double *, const double2 *, int64_t, int);            \
     template void combo_b<T>(dwf_ctx *, T *, T *const *, int, const double2 *, int64_t, int);

@@ -706,12 +706,16 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
     DWF_REQUIRE(per_sm >= 1, DWF_ECUDA, "tensor-core coarse solver cannot be co-resident");
     // The grid (sites per CTA) is the solver's tile: fewer CTAs make the grid
     // barriers cheaper and the per-CTA stencil pipeline longer.  The first
-    // solve of each batch width on a coarse operator times the co-resident
-    // candidates of 2, 4, 8, ... sites per CTA on its own inputs (every trial
-    // starts from x = 0, so they are repeatable; one untimed run first warms
-    // the caches) and keeps the fastest; the solve itself then runs with it.
+    // solve of a shape (coarse sites, Nvec, batch width) in a context times
+    // the co-resident candidates of 2, 4, 8, ... sites per CTA on its own
+    // inputs (every trial starts from x = 0, so they are repeatable; one
+    // untimed run first warms the caches), stopping once a candidate is 30%
+    // slower than the best, and keeps the fastest for that shape; the solve
+    // itself then runs with it.
     const int64_t V = L.lg.g.V, maxg = (int64_t)per_sm * c->sm_count;
-    int nblk = L.tc_ctas[nb];
+    int nblk = 0;
+    for (const auto &e : c->tc_grid)
+        if (e[0] == V && e[1] == NV && e[2] == nb) nblk = (int)e[3];
     if (nblk == 0) {
         std::vector<int> cand;
         for (int64_t s = 2; s <= 64; s *= 2) {
@@ -746,12 +750,14 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
                 if (ms < best) {
                     best = ms;
                     nblk = g;
+                } else if (ms > 1.3f * best) {
+                    break;  // fewer CTAs only get slower from here
                 }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
         }
-        L.tc_ctas[nb] = nblk;
+        c->tc_grid.push_back({V, (int64_t)NV, (int64_t)nb, (int64_t)nblk});
     }
     DWF_CUDA(coop_launch(c, fn, dim3((unsigned)nblk), dim3(TCT), kargs, smem));
     DWF_CHECK_LAUNCH();
@@ -792,7 +798,6 @@ void check_tc_timeout(dwf_ctx *c) {
 // Nvec the tensor-core solver handles (8, 16, 24, 32); other levels get none.
 void build_tc_images(dwf_ctx *c, Level &L) {
     const int n = L.lg.ncomp;
-    for (int &g : L.tc_ctas) g = 0;  // a new operator is tuned anew
     if (L.yprec != DWF_BF16 || L.npts != 9 || !(n == 8 || n == 16 || n == 24 || n == 32)) {
         L.Ytc.release();
         return;

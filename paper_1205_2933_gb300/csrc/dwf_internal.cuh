@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -178,6 +179,8 @@ struct dwf_ctx {
     dwf::DevBuf tc_err;
     bool tc_used = false;
     dwf::DevBuf tc_trial;  // iteration counter of the tensor-core solver's tuning trials
+    // grid the tensor-core solver picked by timing, per (coarse sites, Nvec, batch width)
+    std::vector<std::array<int64_t, 4>> tc_grid;
     // A batch of independent lattices (dwf_create with nlat > 1): one member
     // context per lattice, each on a stream of its own; the batch context
     // itself holds no lattice.  Cooperative launches of all members pass

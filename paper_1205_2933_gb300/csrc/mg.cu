@@ -645,19 +645,23 @@ template <typename R> class BatchRunner {
         for (int r = 0; r < nr; ++r) one.store_normalised(0, v + (size_t)r * N, x0 + (size_t)r * N);
     }
 
-    // nu CGNR iterations on D x = b for every right-hand side, from x = 0;
-    // with rtol > 0 the iteration also ends once every |r| fell by rtol
-    // (tested every 8 iterations)
-    void cgnr_b(T *x, const T *b, int iters, double rtol = 0.0) {
+    // nu CGNR iterations on D x = b for every right-hand side from x = 0
+    // (accumulate: added to what x holds); with rtol > 0 the iteration also
+    // ends once every |r| fell by rtol (tested every 8 iterations).  Nothing
+    // is copied: the first residual is b itself, the first direction is the
+    // first z (kept in the other of two z buffers), and x is first written,
+    // not read, unless it accumulates.
+    void cgnr_b(T *x, const T *b, int iters, double rtol = 0.0, bool accumulate = false) {
         const int64_t N = n(0), NT = N * nr;
-        T *r = wsb(0, 0), *z = wsb(0, 1), *p = wsb(0, 2), *w = wsb(0, 3);
-        bzero<T>(c, x, NT);
-        bcopy<T, T>(c, r, b, NT);
-        dslash(c, z, r, true, nr);
-        bcopy<T, T>(c, p, z, NT);
+        if (iters <= 0) {
+            if (!accumulate) bzero<T>(c, x, NT);
+            return;
+        }
+        T *r = wsb(0, 0), *p = wsb(0, 2), *w = wsb(0, 3);
+        T *zbuf[2] = {wsb(0, 1), wsb(0, 5)};
+        int zi = 0;
         int izz = 0, inew = 1;
         const int iww = 2;
-        norm2_b<T>(c, mg.bscratch, SB + izz, SS, z, N, nr);
         // the FP32 Dslash can produce the norms of its outputs in its epilogue
         bool fused = false;
         if constexpr (std::is_same<R, float>::value) fused = dslash_norm_fused(c);
@@ -667,20 +671,24 @@ template <typename R> class BatchRunner {
             dslash(c, out, in, dag, nr);
             norm2_b<T>(c, mg.bscratch, SB + slot, SS, out, N, nr);
         };
+        dnorm(zbuf[0], b, true, izz);  // z_0 = D^+ r_0 with r_0 = b
+        const T *rin = b, *pin = zbuf[0];
+        bool xinit = !accumulate;
         const int irr = 3;
         std::vector<double> r0(nr, 0.0), sv;
         if (rtol > 0.0) {
-            norm2_b<T>(c, mg.bscratch, SB + irr, SS, r, N, nr);
+            norm2_b<T>(c, mg.bscratch, SB + irr, SS, b, N, nr);
             read_block(sv);
             for (int q = 0; q < nr; ++q) r0[q] = std::sqrt(sv[(size_t)q * SS + irr]);
         }
         // x += a p is deferred into the direction update, so each iteration
         // reads r, w (residual) and x, p, z (solution and direction) once
         for (int it = 0; it < iters; ++it) {
-            dnorm(w, p, false, iww);
+            dnorm(w, pin, false, iww);
             bool last = it + 1 == iters;
             if (!last) {
-                cg_r_b<T>(c, r, w, SB, SS, izz, iww, N, nr);
+                cg_r_b<T>(c, r, rin, w, SB, SS, izz, iww, N, nr);
+                rin = r;
                 if (rtol > 0.0 && (it + 1) % 8 == 0) {
                     norm2_b<T>(c, mg.bscratch, SB + irr, SS, r, N, nr);
                     read_block(sv);
@@ -690,11 +698,14 @@ template <typename R> class BatchRunner {
                 }
             }
             if (last) {
-                cg_px_b<T>(c, x, p, z, SB, SS, izz, iww, inew, N, nr, true);  // x += a p
+                cg_px_b<T>(c, x, p, pin, nullptr, SB, SS, izz, iww, inew, N, nr, true, xinit);  // x += a p
                 break;
             }
-            dnorm(z, r, true, inew);
-            cg_px_b<T>(c, x, p, z, SB, SS, izz, iww, inew, N, nr, false);
+            zi ^= 1;
+            dnorm(zbuf[zi], r, true, inew);
+            cg_px_b<T>(c, x, p, pin, zbuf[zi], SB, SS, izz, iww, inew, N, nr, false, xinit);
+            xinit = false;
+            pin = p;
             std::swap(izz, inew);
         }
     }
@@ -899,7 +910,7 @@ template <typename R> class BatchRunner {
     void vcycle_body(T *x, const T *b) {
         Level &L = mg.lev[0];
         const int64_t N = n(0), NT = N * nr, Nc = n(1);
-        T *res = wsb(0, 4), *sm = wsb(0, 5);
+        T *res = wsb(0, 4);
         T *b2 = wsb(1, 8), *x2 = wsb(1, 9);
         restrict_batch<R>(c, L, b2, b, one.Q(0), nr);
         coarse_solves(x2, b2, Nc);
@@ -907,8 +918,7 @@ template <typename R> class BatchRunner {
         if (mg.p.nu_post > 0) {
             dslash(c, res, x, false, nr);
             cxpay<T>(c, res, make_double2(-1.0, 0.0), b, NT);  // res = b - A x
-            cgnr_b(sm, res, mg.p.nu_post);
-            caxpy<T>(c, x, make_double2(1.0, 0.0), sm, NT);
+            cgnr_b(x, res, mg.p.nu_post, 0.0, true);            // x += S3(res)
         }
     }
 

@@ -35,7 +35,6 @@ struct Level {
     int npts = 9;
     DevBuf Y64, Y32, Y16;  // Y16 holds bf16 or fp16 pairs per coarse_prec
     DevBuf Ytc;            // BF16 stencil as per-site tensor-core operand images (coarse_gcr_tc.cu)
-    mutable int tc_ctas[17] = {0};  // grid of the tensor-core solver picked by timing, per batch width (0: not yet)
     dwf_prec yprec = DWF_F64;
     // block reductions scratch: [Vc][nv][nv] complex FP64
     DevBuf G, F, Rinv;
@@ -155,11 +154,13 @@ template <typename T> void multiaxpy_b(dwf_ctx *c, T *w, T *const *V, int k, int
 template <typename T>
 void cg_xr_b(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
 template <typename T> void cg_p_b(dwf_ctx *c, T *p, const T *z, int base, int stride, int inew, int iold, int64_t n, int nrhs);
+// r = rin - a w (rin may be r), a = |z|^2 / |w|^2 from the slots
 template <typename T>
-void cg_r_b(dwf_ctx *c, T *r, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
+void cg_r_b(dwf_ctx *c, T *r, const T *rin, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
+// x += a pin (x = a pin with xinit); unless last, pout = z + beta pin (pin may be pout)
 template <typename T>
-void cg_px_b(dwf_ctx *c, T *x, T *p, const T *z, int base, int stride, int izz, int iww, int inew, int64_t n, int nrhs,
-             bool last);
+void cg_px_b(dwf_ctx *c, T *x, T *pout, const T *pin, const T *z, int base, int stride, int izz, int iww, int inew,
+             int64_t n, int nrhs, bool last, bool xinit);
 template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs);
 template <typename T> void gcr_wr_b(dwf_ctx *c, T *w, T *res, const double *sc, const double2 *al, int64_t n, int nrhs);
 template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const double2 *g, int64_t n, int nrhs);
