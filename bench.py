@@ -52,7 +52,7 @@ FINE_BYTES_F32 = 204   # algorithmic bytes per 5D site of the FP32 Dslash
 # output norms (the instantiation of nearly all timed launches) per 2,097,152
 # 5D sites (one 16^3x32x16 field), from an ncu capture of a two-field launch on
 # 16^3x16x16; None until the kernel as it stands has been captured
-DSLASH_TRAFFIC_PER_FIELD = 424523776  # 252.34 MB read + 172.18 MB written
+DSLASH_TRAFFIC_PER_FIELD = 423999488  # 252.25 MB read + 171.75 MB written
 FINE_BYTES_F64 = 408
 # fine-operator applications per solve of this workload on the GPU path (FP32 and
 # FP64, the setup's amortised over 12 right-hand sides), from the timed bench steps;

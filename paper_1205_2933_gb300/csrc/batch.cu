@@ -37,8 +37,8 @@ dwf_status cuda_status(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? DWF_ENOMEM : DWF_ECUDA;
 }
 
-// one event per member plus one for the batch stream, kept in the batch's profiler pool
-cudaEvent_t batch_event(dwf_ctx *b, int i) { return b->prof_pool[i]; }
+// one event per member plus one for the batch stream
+cudaEvent_t batch_event(dwf_ctx *b, int i) { return b->batch_ev[i]; }
 
 }  // namespace
 
@@ -79,16 +79,16 @@ dwf_status create_batch(dwf_ctx **out, int nlat, const int (*dims)[4], int Ls, d
     for (int i = 0; i <= nlat && e == cudaSuccess; ++i) {
         cudaEvent_t ev = nullptr;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) b->prof_pool.push_back(ev);
+        if (e == cudaSuccess) b->batch_ev.push_back(ev);
     }
     st = cuda_status(e);
     // the members copy their links on their own streams: first wait for what the caller queued
-    if (st == DWF_OK) st = cuda_status(cudaEventRecord(b->prof_pool[nlat], b->stream));
+    if (st == DWF_OK) st = cuda_status(cudaEventRecord(b->batch_ev[nlat], b->stream));
     for (int i = 0; i < nlat && st == DWF_OK; ++i) {
         cudaStream_t s = nullptr;
         st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
         if (st != DWF_OK) break;
-        st = cuda_status(cudaStreamWaitEvent(s, b->prof_pool[nlat], 0));
+        st = cuda_status(cudaStreamWaitEvent(s, b->batch_ev[nlat], 0));
         dwf_ctx *m = nullptr;
         if (st == DWF_OK) st = create_one(&m, dims[i], Ls, M5, mf, links[i], antiperiodic_t, s);
         if (st != DWF_OK) {
@@ -111,8 +111,8 @@ dwf_status create_batch(dwf_ctx **out, int nlat, const int (*dims)[4], int Ls, d
 void destroy_batch(dwf_ctx *b) {
     for (dwf_ctx *m : b->members) dwf_destroy(m);
     b->members.clear();
-    for (cudaEvent_t ev : b->prof_pool) cudaEventDestroy(ev);
-    b->prof_pool.clear();
+    for (cudaEvent_t ev : b->batch_ev) cudaEventDestroy(ev);
+    b->batch_ev.clear();
     if (b->gate) {
         if (b->gate->last) cudaEventDestroy(b->gate->last);
         delete b->gate;

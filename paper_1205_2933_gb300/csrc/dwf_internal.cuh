@@ -188,6 +188,7 @@ struct dwf_ctx {
     // on one another.
     std::vector<dwf_ctx *> members;
     dwf::CoopGate *gate = nullptr;  // owned by the batch context, shared by its members
+    std::vector<cudaEvent_t> batch_ev;  // batch context: one join event per member, then the fork event
     bool own_stream = false;        // member streams are created and destroyed by the library
     long long applies64 = 0, applies32 = 0;
     // event profiler
