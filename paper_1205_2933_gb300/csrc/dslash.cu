@@ -217,13 +217,14 @@ void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nr
 
 namespace {
 // two slices per thread with packed FP32x2 arithmetic where Ls allows;
-// DWF_DSLASH_PAIR=0 selects the one-slice kernel
+// DWF_DSLASH_PAIR=0 selects the one-slice kernel, DWF_DSLASH_PAIR_MINB=4 the
+// 128-thread CTAs instead of the default 64-thread ones (8 per SM)
 int pair_minb() {
     static const int v = [] {
         const char *e = getenv("DWF_DSLASH_PAIR");
         if (e && atoi(e) == 0) return 0;
         const char *m = getenv("DWF_DSLASH_PAIR_MINB");
-        return (m && atoi(m) == 5) ? 5 : 4;
+        return (m && atoi(m) == 4) ? 4 : 8;
     }();
     return v;
 }
