@@ -52,8 +52,9 @@ FINE_BYTES_F32 = 204   # algorithmic bytes per 5D site of the FP32 Dslash
 # output norms (the instantiation of nearly all timed launches) per 2,097,152
 # 5D sites (one 16^3x32x16 field), from an ncu capture of a two-field launch on
 # 16^3x16x16; None until the kernel as it stands has been captured
-DSLASH_TRAFFIC_PER_FIELD = 423999488  # 252.25 MB read + 171.75 MB written
+DSLASH_TRAFFIC_PER_FIELD = 424006400  # 252.25 MB read + 171.76 MB written
 FINE_BYTES_F64 = 408
+FINE_BYTES_F32_Z = FINE_BYTES_F32 + 96  # the fused residual kernels also read b (or z) at every 5D site
 # fine-operator applications per solve of this workload on the GPU path (FP32 and
 # FP64, the setup's amortised over 12 right-hand sides), from the timed bench steps;
 # the reference arm scales its timed oracle applications by it
@@ -553,8 +554,8 @@ def main():
     launches = G.dwf_launch_count() - launches0
     ms_total = t0.elapsed_time(t1)
     clk = clocks.stop()
-    classes = (("dslash_f32", G.K_DSLASH_F32), ("dslash_f64", G.K_DSLASH_F64), ("restrict", G.K_RESTRICT),
-               ("prolong", G.K_PROLONG), ("coarse", G.K_COARSE))
+    classes = (("dslash_f32", G.K_DSLASH_F32), ("dslash_f32_z", G.K_DSLASH_F32_Z), ("dslash_f64", G.K_DSLASH_F64),
+               ("restrict", G.K_RESTRICT), ("prolong", G.K_PROLONG), ("coarse", G.K_COARSE))
     prof = {name: G.dwf_profile_read(ctx.h, k) for name, k in classes}
     units = {name: G.dwf_profile_units(ctx.h, k) for name, k in classes}
     G.dwf_profile(ctx.h, False)
@@ -579,7 +580,10 @@ def main():
 
     # fine-operator applications per solve in the timed region, setup included
     # (the paper's cost unit, Sec. 3): all fields the FP32 and FP64 Dslash processed
-    applies_per_solve = (units["dslash_f32"] + units["dslash_f64"]) / (nrhs * args.steps) or None
+    applies_per_solve = (units["dslash_f32"] + units["dslash_f32_z"] + units["dslash_f64"]) / (nrhs * args.steps) \
+        or None
+    nz, msz = prof["dslash_f32_z"]
+    dslash_z_gbs = FINE_BYTES_F32_Z * V5 * units["dslash_f32_z"] / (msz * 1e-3) / 1e9 if nz else None
 
     line = {"metric": METRIC,
             "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -588,7 +592,8 @@ def main():
             "config": workload_config(nrhs, args.coarsen), "gpu_launches": int(launches), "clocks": clk,
             "roofline": roof, "solve_stats": stats[-1] if stats else None,
             "applies_per_solve": applies_per_solve,
-            "kernel_time_ms": {k: {"launches": v[0], "fields": units[k], "ms": v[1]} for k, v in prof.items()}}
+            "kernel_time_ms": {k: {"launches": v[0], "fields": units[k], "ms": v[1]} for k, v in prof.items()},
+            "dslash_f32_z_gbs": dslash_z_gbs}
     # the chosen solutions of the last timed step stay on the device for the error check
     ctx.close()
     torch.cuda.synchronize()

@@ -308,12 +308,14 @@ dwf_status mg_vcycle_batch(dwf_ctx *ctx, void *x_dev, const void *b_dev, int nrh
  * records and starts recording, dwf_profile(ctx, 0) stops; dwf_profile_read
  * synchronises the stream and returns the number of launches and their
  * summed device time for one class.  Classes: 0 = fine D in FP64, 1 = fine
- * D in FP32, 2 = restriction, 3 = prolongation, 4 = coarse stencil. */
+ * D in FP32, 2 = restriction, 3 = prolongation, 4 = coarse stencil, 5 = fine
+ * D in FP32 that combines its result with a second field (the V-cycle's
+ * residual b - D x, the smoother's z - a D^+ w). */
 dwf_status dwf_profile(dwf_ctx *ctx, int enable);
 dwf_status dwf_profile_read(dwf_ctx *ctx, int kernel_class, long long *launches, double *total_ms);
 /* The number of fields (right-hand sides) the recorded launches of one class
- * processed: a batched launch over nrhs fields counts nrhs (classes 0, 1: fine
- * D applications; 2, 3: batched transfers count their right-hand sides). */
+ * processed: a batched launch over nrhs fields counts nrhs (classes 0, 1, 5:
+ * fine D applications; 2, 3: batched transfers count their right-hand sides). */
 dwf_status dwf_profile_units(dwf_ctx *ctx, int kernel_class, long long *units);
 
 /* Number of kernels this library has launched in the process so far. */

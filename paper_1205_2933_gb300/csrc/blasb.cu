@@ -226,6 +226,46 @@ __global__ void cg_px_b_kernel(T *__restrict__ x, T *pout, const T *pin, const T
     }
 }
 
+// CGNR direction update with the solution update deferred by one iteration
+// (two direction buffers).  a = zz/ww and b = z'z'/zz of the current
+// iteration as in cg_px_b; s[ia] holds the step of the deferred direction.
+//   mode 0 (defer): pout = z + b pin, s[ia] = a (x untouched)
+//   mode 1 (flush): x += s[ia] pprev + a pin, pout = z + b pin
+//   mode 2 (flush, last iteration): x += s[ia] pprev + a pin
+// pout may be pprev (each element is read before it is written).
+template <typename T>
+__global__ void cg_pxd_b_kernel(T *__restrict__ x, T *pout, const T *__restrict__ pin, const T *pprev,
+                                const T *__restrict__ z, double *s, int base, int stride, int izz, int iww, int inew,
+                                int ia, int64_t n, int mode) {
+    using R = typename RealB<T>::type;
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    double *sr = s + base + (size_t)r * stride;
+    const double ww = sr[iww], zz = sr[izz];
+    const R a = ww > 0.0 ? (R)(zz / ww) : R(0);
+    const R b = (mode != 2 && zz > 0.0) ? (R)(sr[inew] / zz) : R(0);
+    const R ap = mode != 0 ? (R)sr[ia] : R(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T pv = pin[off + i];
+        if (mode != 0) {
+            const T qv = pprev[off + i];
+            T xv = x[off + i];
+            xv.x += ap * qv.x + a * pv.x;
+            xv.y += ap * qv.y + a * pv.y;
+            x[off + i] = xv;
+        }
+        if (mode != 2) {
+            const T zv = z[off + i];
+            pv.x = zv.x + b * pv.x;
+            pv.y = zv.y + b * pv.y;
+            pout[off + i] = pv;
+        }
+    }
+    // every CTA has read sr[ia] before it is rewritten: only a defer launch writes it, and a
+    // defer launch does not read it
+    if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) sr[ia] = (double)a;
+}
+
 // y_r += coef[r] * x_r (complex coefficients in device memory)
 template <typename T>
 __global__ void axpy_b_kernel(T *__restrict__ y, const T *__restrict__ x, const double2 *__restrict__ coef, int64_t n) {
@@ -377,6 +417,16 @@ void cg_px_b(dwf_ctx *c, T *x, T *pout, const T *pin, const T *z, int base, int 
     DWF_CHECK_LAUNCH();
 }
 
+template <typename T>
+void cg_pxd_b(dwf_ctx *c, T *x, T *pout, const T *pin, const T *pprev, const T *z, int base, int stride, int izz,
+              int iww, int inew, int ia, int64_t n, int nrhs, int mode) {
+    DWF_REQUIRE(mode >= 0 && mode <= 2, DWF_EINVAL, "cg_pxd_b: mode");
+    dim3 g = grid_b(c, n, nrhs, 16);
+    cg_pxd_b_kernel<T><<<g, BT, 0, c->stream>>>(x, pout, pin, pprev, z, c->scal.as<double>(), base, stride, izz, iww,
+                                                inew, ia, n, mode);
+    DWF_CHECK_LAUNCH();
+}
+
 template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs) {
     dim3 g = grid_b(c, n, nrhs, 16);
     axpy_b_kernel<T><<<g, BT, 0, c->stream>>>(y, x, coef, n);
@@ -410,6 +460,8 @@ template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const d
     template void cg_r_b<T>(dwf_ctx *, T *, const T *, const T *, int, int, int, int, int64_t, int);          \
     template void cg_px_b<T>(dwf_ctx *, T *, T *, const T *, const T *, int, int, int, int, int, int64_t, int, bool, \
                              bool);                                                                            \
+    template void cg_pxd_b<T>(dwf_ctx *, T *, T *, const T *, const T *, const T *, int, int, int, int, int, int, \
+                              int64_t, int, int);                                                              \
     template void axpy_b<T>(dwf_ctx *, T *, const T *, const double2 *, int64_t, int);                        \
     template void gcr_wr_b<T>(dwf_ctx *, T *, T *, const double *, const double2 *, int64_t, int);            \
     template void combo_b<T>(dwf_ctx *, T *, T *const *, int, const double2 *, int64_t, int);

@@ -212,8 +212,10 @@ void dslash(dwf_ctx *c, double2 *out, const double2 *in, bool dag, int nrhs) {
 }
 
 bool dslash_pair_supported(int Ls);
+// zin with nslot: out = zin - a D^+ in, a = zz[r * nstride] / ww[r * nstride] per right-hand side r;
+// zin without nslot: out = zin - D in
 void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot,
-                     int nstride);
+                     int nstride, const float2 *zin = nullptr, const double *zz = nullptr, const double *ww = nullptr);
 
 namespace {
 // two slices per thread with packed FP32x2 arithmetic where Ls allows;
@@ -247,6 +249,24 @@ void dslash_norm(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, 
     DWF_REQUIRE(dslash_norm_fused(c), DWF_EINVAL, "fused Dslash norm needs the paired kernel");
     ProfScope ps(c, K_DSLASH_F32, nrhs);
     dslash_pair_f32(c, out, in, dag, nrhs, pair_minb(), c->scal.as<double>() + slot, stride);
+    c->applies32 += nrhs;
+}
+
+void dslash_residual(dwf_ctx *c, float2 *res, const float2 *x, const float2 *b, int nrhs) {
+    DWF_REQUIRE(dslash_norm_fused(c), DWF_EINVAL, "fused residual needs the paired kernel");
+    DWF_REQUIRE(res != x && res != b, DWF_EINVAL, "residual: output must not alias an input");
+    ProfScope ps(c, K_DSLASH_F32_Z, nrhs);
+    dslash_pair_f32(c, res, x, false, nrhs, pair_minb(), nullptr, 0, b);
+    c->applies32 += nrhs;
+}
+
+void dslash_zupdate(dwf_ctx *c, float2 *zout, const float2 *w, const float2 *zin, int nrhs, int slot, int stride,
+                    int izz, int iww) {
+    DWF_REQUIRE(dslash_norm_fused(c), DWF_EINVAL, "fused residual update needs the paired kernel");
+    DWF_REQUIRE(zout != zin && zout != w, DWF_EINVAL, "residual update: output must not alias an input");
+    ProfScope ps(c, K_DSLASH_F32_Z, nrhs);
+    double *s = c->scal.as<double>();
+    dslash_pair_f32(c, zout, w, true, nrhs, pair_minb(), s + slot, stride, zin, s + izz, s + iww);
     c->applies32 += nrhs;
 }
 

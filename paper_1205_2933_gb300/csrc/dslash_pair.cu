@@ -175,13 +175,25 @@ template <int LS> __device__ __forceinline__ void ldrow(float4 p[12], const floa
 // wavefront instead of one per site.
 constexpr int LSTRIDE = 73;
 
-// NORM: also |out_r|^2 of every right-hand side r = blockIdx.y: one FP64
-// partial per CTA (FP32 per thread) into npart; norm_finish_kernel adds them
-// in a fixed order into the scalar slots.
-template <bool DAG, int LS, int NT, int MINB, bool NORM>
+// The normal-equations residual update of CGNR, z <- z - a D^+ w, with
+// a = zz / ww of each right-hand side read from the scalar slots.
+struct ZUpdate {
+    const float2 *zin;  // z before the update (not the output buffer)
+    const double *zz;   // |z|^2 of right-hand side r at zz[r * stride]
+    const double *ww;   // |w|^2 = |D p|^2 of right-hand side r at ww[r * stride]
+    int stride;
+};
+
+// EPI 0: out = D in (or D^+ in).  EPI 1: also |out_r|^2 of every right-hand
+// side r = blockIdx.y: one FP64 partial per CTA (FP32 per thread) into npart;
+// norm_finish_kernel adds them in a fixed order into the scalar slots.
+// EPI 2: out = zu.zin - a D^+ in, and |out_r|^2 as with EPI 1.
+// EPI 3: out = zu.zin - D in (a residual b - D x), no norm.
+template <bool DAG, int LS, int NT, int MINB, int EPI>
 __global__ void __launch_bounds__(NT, MINB)
 dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, const float2 *__restrict__ U, Geom g,
-                   float diag, float mf, int spb, int64_t field, double *__restrict__ npart) {
+                   float diag, float mf, int spb, int64_t field, double *__restrict__ npart, ZUpdate zu) {
+    constexpr bool NORM = EPI == 1 || EPI == 2;
     constexpr int TPS = LS / 2;  // threads per site
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *sL = reinterpret_cast<float4 *>(smem_raw);                 // [spb][LSTRIDE]
@@ -191,6 +203,22 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
     const size_t rhs_off = (size_t)blockIdx.y * (size_t)field;
     in += rhs_off;
     out += rhs_off;
+    // EPI >= 2: the thread's 12 components of zin are requested first, by
+    // asynchronous copies into shared memory ([k][thread]), so that their
+    // latency hides behind the hops instead of following them.
+    float4 *sZ = reinterpret_cast<float4 *>(sN + spb * 8);
+    if (EPI >= 2) {
+        const int zs = site0 + (int)threadIdx.x / TPS;
+        if ((int)threadIdx.x < spb * TPS && zs < V) {
+            const float2 *zp = zu.zin + rhs_off + (size_t)zs * (12 * LS) + 2 * ((int)threadIdx.x % TPS);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(sZ + k * blockDim.x + threadIdx.x);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(zp + k * LS) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     for (int jj = threadIdx.x; jj < spb * 8; jj += blockDim.x) {
         const int ls = jj >> 3, k = jj & 7, mu = k & 3;
         const int site = site0 + ls;
@@ -278,9 +306,23 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
         hop2<3, false>(acc, pa, sLs + 3 * 9, fs);
         hop2<3, true>(acc, pb, sLs + 7 * 9, -fs);
         float2 *o = out + (size_t)site * row + s0;
+        float a = 1.f;
+        if (EPI >= 2) {
+            if (EPI == 2) {
+                const double ww = zu.ww[(size_t)blockIdx.y * zu.stride];
+                a = ww > 0.0 ? (float)(zu.zz[(size_t)blockIdx.y * zu.stride] / ww) : 0.f;
+            }
+            // each thread reads back only what its own copies wrote
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            const float2 re = unpk(acc[k].re), im = unpk(acc[k].im);
+            float2 re = unpk(acc[k].re), im = unpk(acc[k].im);
+            if (EPI >= 2) {
+                const float4 z = sZ[k * blockDim.x + threadIdx.x];
+                re = make_float2(fmaf(-a, re.x, z.x), fmaf(-a, re.y, z.z));
+                im = make_float2(fmaf(-a, im.x, z.y), fmaf(-a, im.y, z.w));
+            }
             *reinterpret_cast<float4 *>(o + k * LS) = make_float4(re.x, im.x, re.y, im.y);
             if (NORM) nrm += re.x * re.x + im.x * im.x + re.y * re.y + im.y * im.y;
         }
@@ -322,7 +364,8 @@ __global__ void __launch_bounds__(1024) norm_finish_kernel(const double *__restr
 // than 128 threads x 4, by locality of the smaller site tiles) or of 128
 // threads, 4 per SM (minb = 4); 128 registers either way.
 template <int LS>
-void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot, int nstride) {
+void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot, int nstride,
+               const ZUpdate *zu) {
     const Geom &g = c->g;
     constexpr int TPS = LS / 2;
     int spb = (minb == 4 ? 128 : 64) / TPS;
@@ -334,6 +377,7 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
     const int threads = spb * TPS;
     dim3 grid((unsigned)((g.V + spb - 1) / spb), (unsigned)nrhs);
     size_t smem = (size_t)spb * per_site;
+    if (zu) smem += (size_t)threads * 12 * sizeof(float4);  // the staged zin components
     int64_t field = g.V * g.Ls * 12;
     float diag = (float)(5.0 - c->M5), mf = (float)c->mf;
     const float2 *U = c->U32.as<float2>();
@@ -343,16 +387,23 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
         if (c->dn_part.bytes < pb) c->dn_part.alloc(pb);
         npart = c->dn_part.as<double>();
     }
-#define PL(D, NT, M, NRM) dslash_pair_kernel<D, LS, NT, M, NRM><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, \
-                                                                                                     spb, field, npart)
-    if (nslot) {
-        if (dag) { if (minb == 4) PL(true, 128, 4, true); else PL(true, 64, 8, true); }
-        else { if (minb == 4) PL(false, 128, 4, true); else PL(false, 64, 8, true); }
+    const ZUpdate z = zu ? *zu : ZUpdate{nullptr, nullptr, nullptr, 0};
+#define PL(D, NT, M, E) dslash_pair_kernel<D, LS, NT, M, E><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, \
+                                                                                                 spb, field, npart, z)
+    if (zu && !nslot) {
+        if (minb == 4) PL(false, 128, 4, 3); else PL(false, 64, 8, 3);
+    } else if (zu) {
+        if (minb == 4) PL(true, 128, 4, 2); else PL(true, 64, 8, 2);
+        DWF_CHECK_LAUNCH();
+        norm_finish_kernel<<<nrhs, 1024, 0, c->stream>>>(npart, nslot, nstride, (int)grid.x);
+    } else if (nslot) {
+        if (dag) { if (minb == 4) PL(true, 128, 4, 1); else PL(true, 64, 8, 1); }
+        else { if (minb == 4) PL(false, 128, 4, 1); else PL(false, 64, 8, 1); }
         DWF_CHECK_LAUNCH();
         norm_finish_kernel<<<nrhs, 1024, 0, c->stream>>>(npart, nslot, nstride, (int)grid.x);
     } else {
-        if (dag) { if (minb == 4) PL(true, 128, 4, false); else PL(true, 64, 8, false); }
-        else { if (minb == 4) PL(false, 128, 4, false); else PL(false, 64, 8, false); }
+        if (dag) { if (minb == 4) PL(true, 128, 4, 0); else PL(true, 64, 8, 0); }
+        else { if (minb == 4) PL(false, 128, 4, 0); else PL(false, 64, 8, 0); }
     }
 #undef PL
     DWF_CHECK_LAUNCH();
@@ -364,13 +415,15 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
 bool dslash_pair_supported(int Ls) { return Ls == 4 || Ls == 8 || Ls == 16 || Ls == 32 || Ls == 64; }
 
 void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot,
-                     int nstride) {
+                     int nstride, const float2 *zin, const double *zz, const double *ww) {
+    const ZUpdate zu{zin, zz, ww, nstride};
+    const ZUpdate *zp = zin ? &zu : nullptr;
     switch (c->g.Ls) {
-        case 4: launch_ls<4>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
-        case 8: launch_ls<8>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
-        case 16: launch_ls<16>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
-        case 32: launch_ls<32>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
-        case 64: launch_ls<64>(c, out, in, dag, nrhs, minb, nslot, nstride); break;
+        case 4: launch_ls<4>(c, out, in, dag, nrhs, minb, nslot, nstride, zp); break;
+        case 8: launch_ls<8>(c, out, in, dag, nrhs, minb, nslot, nstride, zp); break;
+        case 16: launch_ls<16>(c, out, in, dag, nrhs, minb, nslot, nstride, zp); break;
+        case 32: launch_ls<32>(c, out, in, dag, nrhs, minb, nslot, nstride, zp); break;
+        case 64: launch_ls<64>(c, out, in, dag, nrhs, minb, nslot, nstride, zp); break;
         default: throw Error{DWF_EINVAL, "paired Dslash needs Ls in {4, 8, 16, 32, 64}"};
     }
 }

@@ -145,7 +145,15 @@ struct CoopGate;
 cudaError_t coop_launch(dwf_ctx *c, const void *fn, dim3 grid, dim3 block, void **args, size_t smem);
 
 // Kernel classes timed by the optional event profiler (see dwf_profile).
-enum KernelClass { K_DSLASH_F64 = 0, K_DSLASH_F32 = 1, K_RESTRICT = 2, K_PROLONG = 3, K_COARSE = 4, K_NCLASS = 5 };
+enum KernelClass {
+    K_DSLASH_F64 = 0,
+    K_DSLASH_F32 = 1,
+    K_RESTRICT = 2,
+    K_PROLONG = 3,
+    K_COARSE = 4,
+    K_DSLASH_F32_Z = 5,  // FP32 D or D^+ that reads a second field in its epilogue: b - D x, z - a D^+ w
+    K_NCLASS = 6
+};
 
 struct ProfRecord {
     int cls;
@@ -224,6 +232,13 @@ void dslash(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs);
 // (available when dslash_norm_fused(c))
 bool dslash_norm_fused(dwf_ctx *c);
 void dslash_norm(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int slot, int stride);
+// res = b - D x on nrhs FP32 fields (res distinct from x and b; when dslash_norm_fused(c))
+void dslash_residual(dwf_ctx *c, float2 *res, const float2 *x, const float2 *b, int nrhs);
+// CGNR's normal-equations residual update z_out = z_in - a D^+ w for every
+// right-hand side r, a = scal[izz + r stride] / scal[iww + r stride], and
+// |z_out|^2 into scal[slot + r stride] (available when dslash_norm_fused(c))
+void dslash_zupdate(dwf_ctx *c, float2 *zout, const float2 *w, const float2 *zin, int nrhs, int slot, int stride,
+                    int izz, int iww);
 
 // ---- blas.cu ---- (n = number of complex elements; slots index ctx->scal)
 template <typename T> void bzero(dwf_ctx *c, T *x, int64_t n);

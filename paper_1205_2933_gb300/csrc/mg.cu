@@ -657,7 +657,7 @@ template <typename R> class BatchRunner {
             if (!accumulate) bzero<T>(c, x, NT);
             return;
         }
-        T *r = wsb(0, 0), *p = wsb(0, 2), *w = wsb(0, 3);
+        T *p = wsb(0, 2), *w = wsb(0, 3);
         T *zbuf[2] = {wsb(0, 1), wsb(0, 5)};
         int zi = 0;
         int izz = 0, inew = 1;
@@ -681,8 +681,60 @@ template <typename R> class BatchRunner {
             read_block(sv);
             for (int q = 0; q < nr; ++q) r0[q] = std::sqrt(sv[(size_t)q * SS + irr]);
         }
+        if constexpr (std::is_same<R, float>::value) {
+            if (fused && !(accumulate && rtol > 0.0)) {
+                // r itself is never needed: the normal-equations residual
+                // z = D^+ r follows its own recursion z <- z - a D^+ w (the
+                // same iterates in exact arithmetic), which the D^+ Dslash
+                // applies in its epilogue.  x += a p is further deferred by
+                // one iteration every other iteration (two direction buffers),
+                // so that two steps reach x in one pass.  Per iteration this
+                // streams w = D p, z (in, out), p (in, out) and, on average,
+                // half of x (in, out) and of the deferred direction.  A
+                // residual test (every 8 iterations) computes b - D x itself.
+                T *pb[2] = {p, wsb(0, 6)};
+                const int ia = 5;
+                bool pending = false;  // pb[0] holds a direction whose step is not in x yet (pin is pb[1])
+                for (int it = 0; it < iters; ++it) {
+                    dnorm(w, pin, false, iww);
+                    if (it + 1 == iters) {
+                        if (pending) cg_pxd_b<T>(c, x, nullptr, pin, pb[0], nullptr, SB, SS, izz, iww, inew, ia, N, nr, 2);
+                        else cg_px_b<T>(c, x, p, pin, nullptr, SB, SS, izz, iww, inew, N, nr, true, xinit);
+                        break;
+                    }
+                    zi ^= 1;
+                    dslash_zupdate(c, zbuf[zi], w, zbuf[zi ^ 1], nr, SB + inew, SS, SB + izz, SB + iww);
+                    const bool test = rtol > 0.0 && (it + 1) % 8 == 0;
+                    if (pending) {
+                        cg_pxd_b<T>(c, x, pb[0], pin, pb[0], zbuf[zi], SB, SS, izz, iww, inew, ia, N, nr, 1);
+                        pin = pb[0];
+                        pending = false;
+                    } else if (it > 0 && !test) {
+                        cg_pxd_b<T>(c, x, pb[1], pin, nullptr, zbuf[zi], SB, SS, izz, iww, inew, ia, N, nr, 0);
+                        pin = pb[1];
+                        pending = true;
+                    } else {
+                        cg_px_b<T>(c, x, pb[0], pin, zbuf[zi], SB, SS, izz, iww, inew, N, nr, false, xinit);
+                        pin = pb[0];
+                    }
+                    xinit = false;
+                    std::swap(izz, inew);
+                    if (test) {
+                        T *rt = wsb(0, 0);
+                        dslash_residual(c, rt, x, b, nr);
+                        norm2_b<T>(c, mg.bscratch, SB + irr, SS, rt, N, nr);
+                        read_block(sv);
+                        bool all = true;
+                        for (int q = 0; q < nr; ++q) all &= std::sqrt(sv[(size_t)q * SS + irr]) <= rtol * r0[q];
+                        if (all) break;
+                    }
+                }
+                return;
+            }
+        }
         // x += a p is deferred into the direction update, so each iteration
         // reads r, w (residual) and x, p, z (solution and direction) once
+        T *r = wsb(0, 0);
         for (int it = 0; it < iters; ++it) {
             dnorm(w, pin, false, iww);
             bool last = it + 1 == iters;
@@ -916,9 +968,16 @@ template <typename R> class BatchRunner {
         coarse_solves(x2, b2, Nc);
         prolong_batch<R>(c, L, x, x2, one.Q(0), nr, false);
         if (mg.p.nu_post > 0) {
-            dslash(c, res, x, false, nr);
-            cxpay<T>(c, res, make_double2(-1.0, 0.0), b, NT);  // res = b - A x
-            cgnr_b(x, res, mg.p.nu_post, 0.0, true);            // x += S3(res)
+            bool fused = false;
+            if constexpr (std::is_same<R, float>::value) {
+                fused = dslash_norm_fused(c);
+                if (fused) dslash_residual(c, res, x, b, nr);  // res = b - A x in the Dslash epilogue
+            }
+            if (!fused) {
+                dslash(c, res, x, false, nr);
+                cxpay<T>(c, res, make_double2(-1.0, 0.0), b, NT);  // res = b - A x
+            }
+            cgnr_b(x, res, mg.p.nu_post, 0.0, true);  // x += S3(res)
         }
     }
 
@@ -1165,7 +1224,7 @@ template <typename R> bool batch_eligible(const MGState &mg, int nrhs) {
 template <typename R> int batch_width(const MGState &mg, int nrhs, bool solve) {
     const int64_t N = mg.lev[0].lg.nelem;
     const int restart = std::min(mg.p.outer_restart, 32);
-    std::vector<int> used = {0, 1, 2, 3, 4, 5, 8, 9, 10};
+    std::vector<int> used = {0, 1, 2, 3, 4, 5, 6, 8, 9, 10};
     if (solve)
         for (int i = 0; i < 2 * restart; ++i) used.push_back(16 + i);
     auto held = [&](const std::vector<DevBuf> &v, int i) { return i < (int)v.size() ? (double)v[i].bytes : 0.0; };

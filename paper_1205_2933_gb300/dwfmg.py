@@ -301,7 +301,7 @@ def mg_vcycle_batch(ctx, x, b, nrhs):
     return _check(_lib.mg_vcycle_batch(ctx, _ptr(x), _ptr(b), int(nrhs)), "mg_vcycle_batch")
 
 
-K_DSLASH_F64, K_DSLASH_F32, K_RESTRICT, K_PROLONG, K_COARSE = 0, 1, 2, 3, 4
+K_DSLASH_F64, K_DSLASH_F32, K_RESTRICT, K_PROLONG, K_COARSE, K_DSLASH_F32_Z = 0, 1, 2, 3, 4, 5
 
 
 def dwf_profile(ctx, enable):

@@ -190,14 +190,18 @@ def test_vcycle_parity(G):
     c.close()
 
 
-@pytest.mark.parametrize("cfg", [SMALL, RAGGED], ids=["4^4xLs8", "ragged"])
-def test_vcycle_batch_parity(G, cfg):
+@pytest.mark.parametrize("cfg,nu", [(SMALL, 4), (RAGGED, 4), (SMALL, 5), (SMALL, 1)],
+                         ids=["4^4xLs8", "ragged", "4^4xLs8-nu5", "4^4xLs8-nu1"])
+def test_vcycle_batch_parity(G, cfg, nu):
     """The batched FP32 V-cycle (three right-hand sides together) against the
     oracle's V-cycle of each and against the one-at-a-time GPU V-cycle.  A
     fixed number of coarsest GCR iterations (tolerance 0) keeps both sides on
-    the same Krylov step count, so the comparison is one of rounding only."""
+    the same Krylov step count, so the comparison is one of rounding only.
+    The batched smoother defers every other solution update by one
+    iteration: nu = 4 ends without a deferred step, nu = 5 with one, nu = 1
+    has none."""
     c = Case(G, **cfg, setup_iters0=10, setup_sweeps=0, smoother_prec=G.DWF_F32,
-             coarse_prec=[G.DWF_F32], coarsest_tol=0.0, coarsest_maxiter=8, nu_post=4)
+             coarse_prec=[G.DWF_F32], coarsest_tol=0.0, coarsest_maxiter=8, nu_post=nu)
     from gpu_util import to_internal, to_canonical, rel_norm
     nr = 3
     bs = [I.gaussian_source(c.dims, c.Ls, 40 + r) for r in range(nr)]
@@ -214,6 +218,26 @@ def test_vcycle_batch_parity(G, cfg):
         ref = c.mg.vcycle(0, bs[r].reshape(c.op.shape)).reshape(bs[r].shape)
         eo = rel_norm(got, ref)
         assert eo < 1e-4, (r, eo)
+    c.close()
+
+
+def test_fp32_batched_relaxation_stops_with_the_oracle(G):
+    """The FP32 setup relaxes the start vectors in one batched CGNR whose
+    residual test (every 8 iterations) forms |D x| explicitly.  On this lattice
+    the oracle's relaxation of each vector passes |D x| <= 4e-3 |D x0| first at
+    iteration 24 (about 7e-3 at 16, 2.1e-3 to 2.4e-3 at 24), so both sides stop
+    there and the bases agree to FP32 rounding; had the GPU run on to the
+    100-iteration cap, or stopped at 16, they would differ by order one (0.85 and 1.4
+    in this measure, oracle against oracle)."""
+    c = Case(G, **SMALL, setup_iters0=100, setup_tol0=4e-3, setup_sweeps=0, smoother_prec=G.DWF_F32,
+             coarse_prec=[G.DWF_F32])
+    from gpu_util import to_canonical, rel_max
+    nv = SMALL["nvec"][0]
+    q = torch.empty(c.ctx.field_elems * nv, dtype=torch.complex128, device="cuda")
+    G.mg_get_vectors(c.ctx.h, 0, q)
+    got = to_canonical(c.ctx, q, (nv,) + c.op.shape, nrhs=nv)
+    ref = np.stack([c.mg.levels[0].transfer.vector(k) for k in range(nv)])
+    assert rel_max(got, ref) < 1e-4
     c.close()
 
 
@@ -526,7 +550,8 @@ def test_batched_vcycle_graphs_and_profiler(G):
     """The batched V-cycle replayed as CUDA graphs gives the solution of the
     kernel-by-kernel path, and the event profiler and application counters
     see the replayed launches: with the profiler on, both paths report the
-    same fine applications, and the profiler's FP32 Dslash units match them."""
+    same fine applications, and the profiler's FP32 Dslash units (plain and
+    fused-residual launches) match them."""
     from gpu_util import to_internal, to_canonical, rel_norm
     res = {}
     for graph in (0, 1):
@@ -539,9 +564,11 @@ def test_batched_vcycle_graphs_and_profiler(G):
         st = G.mg_solve(c.ctx.h, bt, xt, 1e-10, nrhs=3)
         n32, ms32 = G.dwf_profile_read(c.ctx.h, G.K_DSLASH_F32)
         u32 = G.dwf_profile_units(c.ctx.h, G.K_DSLASH_F32)
+        nz, msz = G.dwf_profile_read(c.ctx.h, G.K_DSLASH_F32_Z)
+        uz = G.dwf_profile_units(c.ctx.h, G.K_DSLASH_F32_Z)
         G.dwf_profile(c.ctx.h, False)
-        assert st.true_res <= 1e-10 and n32 > 0 and ms32 > 0
-        assert u32 == st.fine_applies_f32
+        assert st.true_res <= 1e-10 and n32 > 0 and ms32 > 0 and nz > 0 and msz > 0
+        assert u32 + uz == st.fine_applies_f32
         res[graph] = (to_canonical(c.ctx, xt, bs.shape, nrhs=3), st.iters, st.fine_applies_f32)
         c.close()
     assert rel_norm(res[1][0], res[0][0]) < 1e-8
