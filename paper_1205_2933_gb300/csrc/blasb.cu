@@ -226,15 +226,19 @@ __global__ void cg_px_b_kernel(T *__restrict__ x, T *pout, const T *pin, const T
     }
 }
 
-// CGNR direction update with the solution update deferred by one iteration
-// (two direction buffers).  a = zz/ww and b = z'z'/zz of the current
-// iteration as in cg_px_b; s[ia] holds the step of the deferred direction.
-//   mode 0 (defer): pout = z + b pin, s[ia] = a (x untouched)
-//   mode 1 (flush): x += s[ia] pprev + a pin, pout = z + b pin
-//   mode 2 (flush, last iteration): x += s[ia] pprev + a pin
-// pout may be pprev (each element is read before it is written).
-template <typename T>
-__global__ void cg_pxd_b_kernel(T *__restrict__ x, T *pout, const T *__restrict__ pin, const T *pprev,
+// CGNR direction update with the solution update x += a p deferred: up to
+// CG_MAXDEFER directions whose steps are not in x yet wait in buffers of
+// their own, their steps in the scalar slots ia, ia+1, ...  a = zz/ww and
+// b = z'z'/zz of the current iteration as in cg_px_b.
+//   mode 0 (defer): pout = z + b pin; s[ia + NP] = a (pin joins the pending)
+//   mode 1 (flush): x += sum_j s[ia + j] pend[j] + a pin; pout = z + b pin
+//   mode 2 (flush, last iteration): x += sum_j s[ia + j] pend[j] + a pin
+// pout may be one of the pending buffers (each element is read before it is written).
+template <typename T> struct Pending {
+    const T *p[CG_MAXDEFER];
+};
+template <typename T, int NP>
+__global__ void cg_pxd_b_kernel(T *__restrict__ x, T *pout, const T *__restrict__ pin, Pending<T> pend,
                                 const T *__restrict__ z, double *s, int base, int stride, int izz, int iww, int inew,
                                 int ia, int64_t n, int mode) {
     using R = typename RealB<T>::type;
@@ -244,14 +248,21 @@ __global__ void cg_pxd_b_kernel(T *__restrict__ x, T *pout, const T *__restrict_
     const double ww = sr[iww], zz = sr[izz];
     const R a = ww > 0.0 ? (R)(zz / ww) : R(0);
     const R b = (mode != 2 && zz > 0.0) ? (R)(sr[inew] / zz) : R(0);
-    const R ap = mode != 0 ? (R)sr[ia] : R(0);
+    R ap[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) ap[j] = mode != 0 ? (R)sr[ia + j] : R(0);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         T pv = pin[off + i];
         if (mode != 0) {
-            const T qv = pprev[off + i];
             T xv = x[off + i];
-            xv.x += ap * qv.x + a * pv.x;
-            xv.y += ap * qv.y + a * pv.y;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const T qv = pend.p[j][off + i];
+                xv.x += ap[j] * qv.x;
+                xv.y += ap[j] * qv.y;
+            }
+            xv.x += a * pv.x;
+            xv.y += a * pv.y;
             x[off + i] = xv;
         }
         if (mode != 2) {
@@ -261,9 +272,8 @@ __global__ void cg_pxd_b_kernel(T *__restrict__ x, T *pout, const T *__restrict_
             pout[off + i] = pv;
         }
     }
-    // every CTA has read sr[ia] before it is rewritten: only a defer launch writes it, and a
-    // defer launch does not read it
-    if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) sr[ia] = (double)a;
+    // a defer launch reads no pending step, so no CTA can see this slot change
+    if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) sr[ia + NP] = (double)a;
 }
 
 // y_r += coef[r] * x_r (complex coefficients in device memory)
@@ -418,12 +428,23 @@ void cg_px_b(dwf_ctx *c, T *x, T *pout, const T *pin, const T *z, int base, int 
 }
 
 template <typename T>
-void cg_pxd_b(dwf_ctx *c, T *x, T *pout, const T *pin, const T *pprev, const T *z, int base, int stride, int izz,
-              int iww, int inew, int ia, int64_t n, int nrhs, int mode) {
-    DWF_REQUIRE(mode >= 0 && mode <= 2, DWF_EINVAL, "cg_pxd_b: mode");
+void cg_pxd_b(dwf_ctx *c, T *x, T *pout, const T *pin, T *const *pend, int np, const T *z, int base, int stride,
+              int izz, int iww, int inew, int ia, int64_t n, int nrhs, int mode) {
+    DWF_REQUIRE(mode >= 0 && mode <= 2 && np >= 0 && np <= CG_MAXDEFER && !(mode == 0 && np == CG_MAXDEFER),
+                DWF_EINVAL, "cg_pxd_b: mode or pending count");
     dim3 g = grid_b(c, n, nrhs, 16);
-    cg_pxd_b_kernel<T><<<g, BT, 0, c->stream>>>(x, pout, pin, pprev, z, c->scal.as<double>(), base, stride, izz, iww,
-                                                inew, ia, n, mode);
+    Pending<T> pd{};
+    for (int j = 0; j < np; ++j) pd.p[j] = pend[j];
+    double *s = c->scal.as<double>();
+#define PX(NP) cg_pxd_b_kernel<T, NP><<<g, BT, 0, c->stream>>>(x, pout, pin, pd, z, s, base, stride, izz, iww, inew, ia, \
+                                                                n, mode)
+    switch (np) {
+        case 0: PX(0); break;
+        case 1: PX(1); break;
+        case 2: PX(2); break;
+        default: PX(3); break;
+    }
+#undef PX
     DWF_CHECK_LAUNCH();
 }
 
@@ -460,8 +481,8 @@ template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const d
     template void cg_r_b<T>(dwf_ctx *, T *, const T *, const T *, int, int, int, int, int64_t, int);          \
     template void cg_px_b<T>(dwf_ctx *, T *, T *, const T *, const T *, int, int, int, int, int, int64_t, int, bool, \
                              bool);                                                                            \
-    template void cg_pxd_b<T>(dwf_ctx *, T *, T *, const T *, const T *, const T *, int, int, int, int, int, int, \
-                              int64_t, int, int);                                                              \
+    template void cg_pxd_b<T>(dwf_ctx *, T *, T *, const T *, T *const *, int, const T *, int, int, int, int, int, \
+                              int, int64_t, int, int);                                                         \
     template void axpy_b<T>(dwf_ctx *, T *, const T *, const double2 *, int64_t, int);                        \
     template void gcr_wr_b<T>(dwf_ctx *, T *, T *, const double *, const double2 *, int64_t, int);            \
     template void combo_b<T>(dwf_ctx *, T *, T *const *, int, const double2 *, int64_t, int);

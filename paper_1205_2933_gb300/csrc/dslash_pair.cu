@@ -370,7 +370,10 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
     constexpr int TPS = LS / 2;
     int spb = (minb == 4 ? 128 : 64) / TPS;
     const size_t per_site = LSTRIDE * sizeof(float4) + 8 * sizeof(int);
-    const int max_spb = (int)((46 * 1024) / per_site);
+    // shared memory per site: staged links and neighbour table, and with zu
+    // the TPS threads' staged components of zin (12 float4 each)
+    const size_t per_site_all = per_site + (zu ? (size_t)TPS * 12 * sizeof(float4) : 0);
+    const int max_spb = (int)((46 * 1024) / per_site_all);
     if (spb > max_spb) spb = max_spb;
     // whole warps: the s-neighbour shuffles and the norm reduction use full masks
     if (TPS < 32) spb = std::max(32 / TPS, spb / (32 / TPS) * (32 / TPS));
@@ -378,6 +381,7 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
     dim3 grid((unsigned)((g.V + spb - 1) / spb), (unsigned)nrhs);
     size_t smem = (size_t)spb * per_site;
     if (zu) smem += (size_t)threads * 12 * sizeof(float4);  // the staged zin components
+    DWF_REQUIRE(smem <= 48 * 1024, DWF_EINVAL, "paired Dslash: shared memory above the default 48 KB");
     int64_t field = g.V * g.Ls * 12;
     float diag = (float)(5.0 - c->M5), mf = (float)c->mf;
     const float2 *U = c->U32.as<float2>();

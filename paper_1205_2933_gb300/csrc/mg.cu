@@ -651,6 +651,21 @@ template <typename R> class BatchRunner {
     // is copied: the first residual is b itself, the first direction is the
     // first z (kept in the other of two z buffers), and x is first written,
     // not read, unless it accumulates.
+    // how many solution updates the smoother may defer: CG_MAXDEFER when two
+    // more direction buffers per right-hand side fit (decided once per runner)
+    int defer_ = 0;
+    int max_defer() {
+        if (!defer_) {
+            const size_t need = 2 * sizeof(T) * (size_t)n(0) * nr;
+            size_t fr = 0, tot = 0;
+            DWF_CUDA(cudaMemGetInfo(&fr, &tot));
+            const auto &v = mg.wsb[0];
+            const bool held = v.size() > 11 && v[7].bytes >= need / 2 && v[11].bytes >= need / 2;
+            defer_ = (held || (double)need < 0.5 * (double)fr) ? CG_MAXDEFER : 1;
+        }
+        return defer_;
+    }
+
     void cgnr_b(T *x, const T *b, int iters, double rtol = 0.0, bool accumulate = false) {
         const int64_t N = n(0), NT = N * nr;
         if (iters <= 0) {
@@ -686,36 +701,54 @@ template <typename R> class BatchRunner {
                 // r itself is never needed: the normal-equations residual
                 // z = D^+ r follows its own recursion z <- z - a D^+ w (the
                 // same iterates in exact arithmetic), which the D^+ Dslash
-                // applies in its epilogue.  x += a p is further deferred by
-                // one iteration every other iteration (two direction buffers),
-                // so that two steps reach x in one pass.  Per iteration this
-                // streams w = D p, z (in, out), p (in, out) and, on average,
-                // half of x (in, out) and of the deferred direction.  A
-                // residual test (every 8 iterations) computes b - D x itself.
-                T *pb[2] = {p, wsb(0, 6)};
-                const int ia = 5;
-                bool pending = false;  // pb[0] holds a direction whose step is not in x yet (pin is pb[1])
+                // applies in its epilogue.  x += a p is deferred for up to
+                // CG_MAXDEFER iterations (their directions kept in buffers of
+                // their own), so that up to four steps reach x in one pass.
+                // Per iteration this streams w = D p, z (in, out), p (in, out)
+                // and, on average, a quarter of x (in, out) and of the
+                // deferred directions.  A residual test (every 8 iterations)
+                // computes b - D x itself.
+                // direction buffers: p and, where memory allows, CG_MAXDEFER more
+                const int md = max_defer();
+                std::vector<T *> pool = {p, wsb(0, 6)};
+                if (md > 1) {
+                    pool.push_back(wsb(0, 7));
+                    pool.push_back(wsb(0, 11));
+                }
+                const int ia = 5;                // steps of the pending directions: slots ia, ia+1, ...
+                std::vector<T *> pend;           // directions whose steps are not in x yet
+                auto take = [&](const T *avoid) {  // a pool buffer that is neither pin nor pending
+                    for (T *q : pool)
+                        if (q != avoid && std::find(pend.begin(), pend.end(), q) == pend.end()) return q;
+                    throw Error{DWF_ESTATE, "smoother: no free direction buffer"};
+                };
                 for (int it = 0; it < iters; ++it) {
                     dnorm(w, pin, false, iww);
+                    const int np = (int)pend.size();
                     if (it + 1 == iters) {
-                        if (pending) cg_pxd_b<T>(c, x, nullptr, pin, pb[0], nullptr, SB, SS, izz, iww, inew, ia, N, nr, 2);
+                        if (np) cg_pxd_b<T>(c, x, nullptr, pin, pend.data(), np, nullptr, SB, SS, izz, iww, inew, ia, N,
+                                            nr, 2);
                         else cg_px_b<T>(c, x, p, pin, nullptr, SB, SS, izz, iww, inew, N, nr, true, xinit);
                         break;
                     }
                     zi ^= 1;
                     dslash_zupdate(c, zbuf[zi], w, zbuf[zi ^ 1], nr, SB + inew, SS, SB + izz, SB + iww);
                     const bool test = rtol > 0.0 && (it + 1) % 8 == 0;
-                    if (pending) {
-                        cg_pxd_b<T>(c, x, pb[0], pin, pb[0], zbuf[zi], SB, SS, izz, iww, inew, ia, N, nr, 1);
-                        pin = pb[0];
-                        pending = false;
+                    if (np && (np == md || test)) {
+                        T *out = pend[0];
+                        cg_pxd_b<T>(c, x, out, pin, pend.data(), np, zbuf[zi], SB, SS, izz, iww, inew, ia, N, nr, 1);
+                        pend.clear();
+                        pin = out;
                     } else if (it > 0 && !test) {
-                        cg_pxd_b<T>(c, x, pb[1], pin, nullptr, zbuf[zi], SB, SS, izz, iww, inew, ia, N, nr, 0);
-                        pin = pb[1];
-                        pending = true;
+                        // pin (a pool buffer from it = 1 on) joins the pending
+                        T *out = take(pin);
+                        cg_pxd_b<T>(c, x, out, pin, pend.data(), np, zbuf[zi], SB, SS, izz, iww, inew, ia, N, nr, 0);
+                        pend.push_back(const_cast<T *>(pin));
+                        pin = out;
                     } else {
-                        cg_px_b<T>(c, x, pb[0], pin, zbuf[zi], SB, SS, izz, iww, inew, N, nr, false, xinit);
-                        pin = pb[0];
+                        T *out = (it == 0) ? p : const_cast<T *>(pin);
+                        cg_px_b<T>(c, x, out, pin, zbuf[zi], SB, SS, izz, iww, inew, N, nr, false, xinit);
+                        pin = out;
                     }
                     xinit = false;
                     std::swap(izz, inew);
@@ -1224,7 +1257,7 @@ template <typename R> bool batch_eligible(const MGState &mg, int nrhs) {
 template <typename R> int batch_width(const MGState &mg, int nrhs, bool solve) {
     const int64_t N = mg.lev[0].lg.nelem;
     const int restart = std::min(mg.p.outer_restart, 32);
-    std::vector<int> used = {0, 1, 2, 3, 4, 5, 6, 8, 9, 10};
+    std::vector<int> used = {0, 1, 2, 3, 4, 5, 6, 8, 9, 10};  // 7 and 11 only where they fit (max_defer)
     if (solve)
         for (int i = 0; i < 2 * restart; ++i) used.push_back(16 + i);
     auto held = [&](const std::vector<DevBuf> &v, int i) { return i < (int)v.size() ? (double)v[i].bytes : 0.0; };

@@ -161,12 +161,14 @@ void cg_r_b(dwf_ctx *c, T *r, const T *rin, const T *w, int base, int stride, in
 template <typename T>
 void cg_px_b(dwf_ctx *c, T *x, T *pout, const T *pin, const T *z, int base, int stride, int izz, int iww, int inew,
              int64_t n, int nrhs, bool last, bool xinit);
-// CGNR direction update with x += a p deferred by one iteration (two direction
-// buffers, the deferred step in scalar slot ia): mode 0 defers, mode 1 adds both
-// pending steps to x and updates the direction, mode 2 only adds them (last iteration)
+// CGNR direction update with x += a p deferred: np (<= CG_MAXDEFER) pending
+// directions pend[] with their steps in scalar slots ia, ia+1, ...; mode 0
+// defers pin as well (its step into slot ia + np), mode 1 adds every pending
+// step and a pin to x and updates the direction, mode 2 only adds them (last iteration)
+constexpr int CG_MAXDEFER = 3;
 template <typename T>
-void cg_pxd_b(dwf_ctx *c, T *x, T *pout, const T *pin, const T *pprev, const T *z, int base, int stride, int izz,
-              int iww, int inew, int ia, int64_t n, int nrhs, int mode);
+void cg_pxd_b(dwf_ctx *c, T *x, T *pout, const T *pin, T *const *pend, int np, const T *z, int base, int stride,
+              int izz, int iww, int inew, int ia, int64_t n, int nrhs, int mode);
 template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs);
 template <typename T> void gcr_wr_b(dwf_ctx *c, T *w, T *res, const double *sc, const double2 *al, int64_t n, int nrhs);
 template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const double2 *g, int64_t n, int nrhs);

@@ -190,16 +190,17 @@ def test_vcycle_parity(G):
     c.close()
 
 
-@pytest.mark.parametrize("cfg,nu", [(SMALL, 4), (RAGGED, 4), (SMALL, 5), (SMALL, 1)],
-                         ids=["4^4xLs8", "ragged", "4^4xLs8-nu5", "4^4xLs8-nu1"])
+@pytest.mark.parametrize("cfg,nu", [(SMALL, 4), (RAGGED, 4), (SMALL, 5), (SMALL, 1), (SMALL, 8)],
+                         ids=["4^4xLs8", "ragged", "4^4xLs8-nu5", "4^4xLs8-nu1", "4^4xLs8-nu8"])
 def test_vcycle_batch_parity(G, cfg, nu):
     """The batched FP32 V-cycle (three right-hand sides together) against the
     oracle's V-cycle of each and against the one-at-a-time GPU V-cycle.  A
     fixed number of coarsest GCR iterations (tolerance 0) keeps both sides on
     the same Krylov step count, so the comparison is one of rounding only.
-    The batched smoother defers every other solution update by one
-    iteration: nu = 4 ends without a deferred step, nu = 5 with one, nu = 1
-    has none."""
+    The batched smoother defers the solution updates of up to three
+    iterations and adds them in one pass: nu = 1 defers none, nu = 4 and 5
+    end with two and three deferred steps, nu = 8 also flushes three in its
+    middle."""
     c = Case(G, **cfg, setup_iters0=10, setup_sweeps=0, smoother_prec=G.DWF_F32,
              coarse_prec=[G.DWF_F32], coarsest_tol=0.0, coarsest_maxiter=8, nu_post=nu)
     from gpu_util import to_internal, to_canonical, rel_norm
