@@ -30,6 +30,7 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <atomic>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -79,6 +80,7 @@ struct TcArgs {
     double tol;
     int maxiter, restart, nb, nbp;  // nbp: nb rounded up to a multiple of 4
     int bbuf;                   // bytes of one B' stage
+    int force_wait;             // test hook: thread 0 of every CTA first waits on a barrier nothing completes
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
     __shared__ double2 tot[TMAXV];
     __shared__ double rn2[TMAXB], stop[TMAXB], wwv[TMAXB];
     __shared__ int act[TMAXB], its[TMAXB];
-    __shared__ __align__(8) uint64_t bars[4];
+    __shared__ __align__(8) uint64_t bars[5];  // copy and MMA barriers of the two stages; [4]: the test hook's
     __shared__ uint32_t tbase;
     __shared__ int bad, quit;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
         reinterpret_cast<float *>(pp.sA[1] + Gm::AIMG)[i] = 0.f;
     }
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[i])));
+        for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[i])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         bad = 0;
         quit = 0;
@@ -346,6 +348,10 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
     __syncthreads();
     tc_fence_after();
     pp.tmem = tbase;
+    // A wait that runs out takes the same exit as an expired copy or MMA
+    // wait: the flag reaches every CTA through the next reduction, all stop
+    // together with x as it stands, and the host reports DWF_ETIMEOUT.
+    if (a.force_wait && tid == 0 && !mbar_wait(smem_addr(&bars[4]), 0u)) bad = 1;
 
     auto zero_red = [&](int nv) {
         for (int q = tid; q < NWARP * 2 * nv; q += TCT) red[q / (2 * nv)][q % (2 * nv)] = 0.f;
@@ -646,7 +652,7 @@ template <int NV> void *tc_kernel_fn() { return (void *)coarse_gcr_tc_kernel<NV>
 
 size_t tc_static_smem() {
     return sizeof(float) * NWARP * 2 * TMAXV + sizeof(double2) * TMAXV + 2 * sizeof(double) * TMAXB +
-           2 * sizeof(int) * TMAXB + 4 * sizeof(uint64_t) + 3 * sizeof(int) + 64;
+           2 * sizeof(int) * TMAXB + 5 * sizeof(uint64_t) + 3 * sizeof(int) + 64;
 }
 
 template <int NV> bool tc_fits(dwf_ctx *c, int nb) {
@@ -667,6 +673,21 @@ bool tc_shape_ok(dwf_ctx *c, const Level &L, int nb) {
         case 32: return tc_fits<32>(c, nb);
         default: return false;
     }
+}
+
+// Test hook for the bounded waits: DWF_TC_FORCE_WAIT=n in the environment
+// makes the first n solver launches outside stream capture start with a wait
+// that nothing completes, so that it runs out (after about one second).
+bool forced_wait(dwf_ctx *c) {
+    static std::atomic<int> left{[] {
+        const char *e = getenv("DWF_TC_FORCE_WAIT");
+        return e ? std::max(0, atoi(e)) : 0;
+    }()};
+    if (left.load() <= 0) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DWF_CUDA(cudaStreamIsCapturing(c->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return false;
+    return left.fetch_sub(1) > 0;
 }
 
 template <int NV>
@@ -696,6 +717,7 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
     a.nb = nb;
     a.nbp = (nb + 3) / 4 * 4;
     a.bbuf = TcGeom<NV>::bbuf(4 * a.nbp);
+    a.force_wait = 0;
     c->tc_used = true;
     void *kargs[] = {&a};
     void *fn = tc_kernel_fn<NV>();
@@ -759,6 +781,7 @@ void launch_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, f
         }
         c->tc_grid.push_back({V, (int64_t)NV, (int64_t)nb, (int64_t)nblk});
     }
+    a.force_wait = forced_wait(c) ? 1 : 0;
     DWF_CUDA(coop_launch(c, fn, dim3((unsigned)nblk), dim3(TCT), kargs, smem));
     DWF_CHECK_LAUNCH();
 }

@@ -184,15 +184,18 @@ struct ZUpdate {
     int stride;
 };
 
+// A CTA stages its sites' links once and applies the operator to rb
+// right-hand sides in turn (r = blockIdx.y * rb + 0 .. rb-1, below nrhs).
 // EPI 0: out = D in (or D^+ in).  EPI 1: also |out_r|^2 of every right-hand
-// side r = blockIdx.y: one FP64 partial per CTA (FP32 per thread) into npart;
+// side r: one FP64 partial per CTA (FP32 per thread) into npart;
 // norm_finish_kernel adds them in a fixed order into the scalar slots.
 // EPI 2: out = zu.zin - a D^+ in, and |out_r|^2 as with EPI 1.
 // EPI 3: out = zu.zin - D in (a residual b - D x), no norm.
 template <bool DAG, int LS, int NT, int MINB, int EPI>
 __global__ void __launch_bounds__(NT, MINB)
-dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, const float2 *__restrict__ U, Geom g,
-                   float diag, float mf, int spb, int64_t field, double *__restrict__ npart, ZUpdate zu) {
+dslash_pair_kernel(float2 *__restrict__ out0, const float2 *__restrict__ in0, const float2 *__restrict__ U, Geom g,
+                   float diag, float mf, int spb, int64_t field, double *__restrict__ npart, ZUpdate zu, int nrhs,
+                   int rb) {
     constexpr bool NORM = EPI == 1 || EPI == 2;
     constexpr int TPS = LS / 2;  // threads per site
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -200,17 +203,17 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
     int *sN = reinterpret_cast<int *>(sL + (size_t)spb * LSTRIDE);      // [spb][8]
     const int V = (int)g.V;
     const int site0 = blockIdx.x * spb;
-    const size_t rhs_off = (size_t)blockIdx.y * (size_t)field;
-    in += rhs_off;
-    out += rhs_off;
-    // EPI >= 2: the thread's 12 components of zin are requested first, by
+    const int r0 = blockIdx.y * rb, r1 = min(r0 + rb, nrhs);
+    // EPI >= 2: the thread's 12 components of zin are requested ahead, by
     // asynchronous copies into shared memory ([k][thread]), so that their
-    // latency hides behind the hops instead of following them.
+    // latency hides behind the hops instead of following them: those of the
+    // first right-hand side before the links are staged, each next one once
+    // the previous epilogue has read its own.
     float4 *sZ = reinterpret_cast<float4 *>(sN + spb * 8);
-    if (EPI >= 2) {
+    auto request_z = [&](int r) {
         const int zs = site0 + (int)threadIdx.x / TPS;
         if ((int)threadIdx.x < spb * TPS && zs < V) {
-            const float2 *zp = zu.zin + rhs_off + (size_t)zs * (12 * LS) + 2 * ((int)threadIdx.x % TPS);
+            const float2 *zp = zu.zin + (size_t)r * (size_t)field + (size_t)zs * (12 * LS) + 2 * ((int)threadIdx.x % TPS);
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
                 const unsigned sa = (unsigned)__cvta_generic_to_shared(sZ + k * blockDim.x + threadIdx.x);
@@ -218,7 +221,8 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
             }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
+    };
+    if (EPI >= 2 && r0 < r1) request_z(r0);
     for (int jj = threadIdx.x; jj < spb * 8; jj += blockDim.x) {
         const int ls = jj >> 3, k = jj & 7, mu = k & 3;
         const int site = site0 + ls;
@@ -258,6 +262,9 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
     const bool active = (ls < spb) && (site < V);
     const int row = 12 * LS;
     const int *sNs = sN + ls * 8;
+    for (int rhs = r0; rhs < r1; ++rhs) {
+    const float2 *__restrict__ in = in0 + (size_t)rhs * (size_t)field;
+    float2 *__restrict__ out = out0 + (size_t)rhs * (size_t)field;
     // the first two hops' rows are requested together with the thread's own
     // row; each later row is requested while the hop before it computes
     float4 pa[12], pb[12], self[12];
@@ -292,7 +299,7 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
         acc[dn_lo + q].re = add2(acc[dn_lo + q].re, pk(c_dn0 * pz, -sd.x));
         acc[dn_lo + q].im = add2(acc[dn_lo + q].im, pk(c_dn0 * pw, -sd.y));
     }
-    if (!NORM && !active) return;
+    if (!NORM && !active) continue;
     float nrm = 0.f;
     if (!NORM || active) {
         const float4 *sLs = sL + ls * LSTRIDE;
@@ -309,8 +316,8 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
         float a = 1.f;
         if (EPI >= 2) {
             if (EPI == 2) {
-                const double ww = zu.ww[(size_t)blockIdx.y * zu.stride];
-                a = ww > 0.0 ? (float)(zu.zz[(size_t)blockIdx.y * zu.stride] / ww) : 0.f;
+                const double ww = zu.ww[(size_t)rhs * zu.stride];
+                a = ww > 0.0 ? (float)(zu.zz[(size_t)rhs * zu.stride] / ww) : 0.f;
             }
             // each thread reads back only what its own copies wrote
             asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -327,6 +334,8 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
             if (NORM) nrm += re.x * re.x + im.x * im.x + re.y * re.y + im.y * im.y;
         }
     }
+    // the epilogue has read this thread's staged components: request the next ones
+    if (EPI >= 2 && rhs + 1 < r1) request_z(rhs + 1);
     if (NORM) {
         __shared__ double wsum[4];
 #pragma unroll
@@ -337,8 +346,10 @@ dslash_pair_kernel(float2 *__restrict__ out, const float2 *__restrict__ in, cons
         if (threadIdx.x == 0) {
             double t = 0;
             for (int w = 0; w < ((int)blockDim.x + 31) >> 5; ++w) t += wsum[w];
-            npart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+            npart[(size_t)rhs * gridDim.x + blockIdx.x] = t;
         }
+        __syncthreads();  // wsum is rewritten for the next right-hand side
+    }
     }
 }
 
@@ -378,7 +389,11 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
     // whole warps: the s-neighbour shuffles and the norm reduction use full masks
     if (TPS < 32) spb = std::max(32 / TPS, spb / (32 / TPS) * (32 / TPS));
     const int threads = spb * TPS;
-    dim3 grid((unsigned)((g.V + spb - 1) / spb), (unsigned)nrhs);
+    // right-hand sides per CTA: the links staged once serve up to 4 of them
+    // (measured 3-4 % faster for the plain and norm kernels; the kernels that
+    // stage a second field run one right-hand side per CTA, 5 % faster so)
+    const int rb = zu ? 1 : std::min(nrhs, 4);
+    dim3 grid((unsigned)((g.V + spb - 1) / spb), (unsigned)((nrhs + rb - 1) / rb));
     size_t smem = (size_t)spb * per_site;
     if (zu) smem += (size_t)threads * 12 * sizeof(float4);  // the staged zin components
     DWF_REQUIRE(smem <= 48 * 1024, DWF_EINVAL, "paired Dslash: shared memory above the default 48 KB");
@@ -393,7 +408,8 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
     }
     const ZUpdate z = zu ? *zu : ZUpdate{nullptr, nullptr, nullptr, 0};
 #define PL(D, NT, M, E) dslash_pair_kernel<D, LS, NT, M, E><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, \
-                                                                                                 spb, field, npart, z)
+                                                                                                 spb, field, npart, z, \
+                                                                                                 nrhs, rb)
     if (zu && !nslot) {
         if (minb == 4) PL(false, 128, 4, 3); else PL(false, 64, 8, 3);
     } else if (zu) {
