@@ -52,8 +52,8 @@ FINE_BYTES_F32 = 204   # algorithmic bytes per 5D site of the FP32 Dslash
 # output norms (the instantiation of nearly all timed launches) per 2,097,152
 # 5D sites (one 16^3x32x16 field), from an ncu capture of a two-field launch on
 # 16^3x16x16; None until the kernel as it stands has been captured
-DSLASH_TRAFFIC_PER_FIELD = 424006400  # 252.25 MB read + 171.76 MB written
-DSLASH_Z_TRAFFIC_PER_FIELD = 630882048  # 453.73 MB read + 177.16 MB written
+DSLASH_TRAFFIC_PER_FIELD = 425732864  # 251.68 MB read + 174.05 MB written
+DSLASH_Z_TRAFFIC_PER_FIELD = 630616832  # 453.86 MB read + 176.76 MB written
 FINE_BYTES_F64 = 408
 FINE_BYTES_F32_Z = FINE_BYTES_F32 + 96  # the fused residual kernels also read b (or z) at every 5D site
 # fine-operator applications per solve of this workload on the GPU path (FP32 and
@@ -589,7 +589,8 @@ def main():
                     "2 x 16^3x16x16 = one 16^3x32x16 field of sites)"),
         dslash_roof("dslash_f32_z", FINE_BYTES_F32_Z, DSLASH_Z_TRAFFIC_PER_FIELD,
                     "ncu dram bytes per field application of the residual-update kernel z - a D^+ w (same launch "
-                    "shape); the class also holds the V-cycle's b - D x launches (same bytes)")) if r]
+                    "shape); the class also holds the w updates D z + b w and the V-cycle's b - D x (same bytes)"))
+             if r]
     roofs.sort(key=lambda r: -r["ms"])
     roof = roofs[0] if roofs else None
     if roof and len(roofs) > 1:

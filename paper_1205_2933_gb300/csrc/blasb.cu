@@ -332,6 +332,42 @@ __global__ void combo_b_kernel(T *__restrict__ x, MArgs<T> a, const double2 *__r
     }
 }
 
+// x_r += sum_j g_j Z_j,r for the k (<= 32) stored normal-equations residuals
+// z_0 .. z_{k-1} of k CGNR iterations, with g the solution's coefficients in
+// that basis: x = sum_k a_k p_k and p_k = z_k + b_{k-1} p_{k-1} give
+// g_{k-1} = a_{k-1}, g_j = a_j + b_j g_{j+1}, where a_j = |z_j|^2 / |w_j|^2
+// and b_j = |z_{j+1}|^2 / |z_j|^2 come from the scalar slots zb + j and wb + j.
+template <typename T>
+__global__ void cg_combine_b_kernel(T *__restrict__ x, MArgs<T> a, const double *__restrict__ s, int base, int stride,
+                                    int zb, int wb, int64_t n) {
+    using R = typename RealB<T>::type;
+    __shared__ R gam[32];
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    if (threadIdx.x == 0) {
+        const double *sr = s + base + (size_t)r * stride;
+        double g = 0.0;
+        for (int j = a.k - 1; j >= 0; --j) {
+            const double zz = sr[zb + j], ww = sr[wb + j];
+            const double al = ww > 0.0 ? zz / ww : 0.0;
+            const double be = (j + 1 < a.k && zz > 0.0) ? sr[zb + j + 1] / zz : 0.0;
+            g = al + be * g;
+            gam[j] = (R)g;
+        }
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T v = x[off + i];
+#pragma unroll 8
+        for (int j = 0; j < a.k; ++j) {
+            const T u = a.v[j][off + i];
+            v.x += gam[j] * u.x;
+            v.y += gam[j] * u.y;
+        }
+        x[off + i] = v;
+    }
+}
+
 dim3 grid_b(dwf_ctx *c, int64_t n, int nrhs, int cap_per_sm) {
     int64_t b = (n + BT - 1) / BT;
     int64_t cap = std::max<int64_t>(1, (int64_t)c->sm_count * cap_per_sm / std::max(1, nrhs));
@@ -472,6 +508,17 @@ template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const d
     DWF_CHECK_LAUNCH();
 }
 
+template <typename T>
+void cg_combine_b(dwf_ctx *c, T *x, T *const *Z, int k, int base, int stride, int zb, int wb, int64_t n, int nrhs) {
+    DWF_REQUIRE(k >= 1 && k <= 32, DWF_EINVAL, "cg_combine_b: 1 to 32 stored residuals");
+    dim3 gr = grid_b(c, n, nrhs, 16);
+    MArgs<T> a;
+    a.k = k;
+    for (int j = 0; j < k; ++j) a.v[j] = Z[j];
+    cg_combine_b_kernel<T><<<gr, BT, 0, c->stream>>>(x, a, c->scal.as<double>(), base, stride, zb, wb, n);
+    DWF_CHECK_LAUNCH();
+}
+
 #define INSTB(T)                                                                                            \
     template void norm2_b<T>(dwf_ctx *, BatchScratch &, int, int, const T *, int64_t, int);                  \
     template void multidot_b<T>(dwf_ctx *, BatchScratch &, int, int, T *const *, int, const T *, int64_t, int); \
@@ -483,6 +530,7 @@ template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const d
                              bool);                                                                            \
     template void cg_pxd_b<T>(dwf_ctx *, T *, T *, const T *, T *const *, int, const T *, int, int, int, int, int, \
                               int, int64_t, int, int);                                                         \
+    template void cg_combine_b<T>(dwf_ctx *, T *, T *const *, int, int, int, int, int, int64_t, int);        \
     template void axpy_b<T>(dwf_ctx *, T *, const T *, const double2 *, int64_t, int);                        \
     template void gcr_wr_b<T>(dwf_ctx *, T *, T *, const double *, const double2 *, int64_t, int);            \
     template void combo_b<T>(dwf_ctx *, T *, T *const *, int, const double2 *, int64_t, int);

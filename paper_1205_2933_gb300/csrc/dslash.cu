@@ -212,10 +212,11 @@ void dslash(dwf_ctx *c, double2 *out, const double2 *in, bool dag, int nrhs) {
 }
 
 bool dslash_pair_supported(int Ls);
-// zin with nslot: out = zin - a D^+ in, a = zz[r * nstride] / ww[r * nstride] per right-hand side r;
-// zin without nslot: out = zin - D in
+// zin with nslot: out = zin - a D^+ in (add: out = D in + a zin), a = zz[r * nstride] / ww[r * nstride]
+// per right-hand side r; zin without nslot: out = zin - D in
 void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot,
-                     int nstride, const float2 *zin = nullptr, const double *zz = nullptr, const double *ww = nullptr);
+                     int nstride, const float2 *zin = nullptr, const double *zz = nullptr, const double *ww = nullptr,
+                     bool add = false);
 
 namespace {
 // two slices per thread with packed FP32x2 arithmetic where Ls allows;
@@ -257,6 +258,16 @@ void dslash_residual(dwf_ctx *c, float2 *res, const float2 *x, const float2 *b, 
     DWF_REQUIRE(res != x && res != b, DWF_EINVAL, "residual: output must not alias an input");
     ProfScope ps(c, K_DSLASH_F32_Z, nrhs);
     dslash_pair_f32(c, res, x, false, nrhs, pair_minb(), nullptr, 0, b);
+    c->applies32 += nrhs;
+}
+
+void dslash_wupdate(dwf_ctx *c, float2 *wout, const float2 *z, const float2 *win, int nrhs, int slot, int stride,
+                    int inum, int iden) {
+    DWF_REQUIRE(dslash_norm_fused(c), DWF_EINVAL, "fused direction update needs the paired kernel");
+    DWF_REQUIRE(wout != win && wout != z, DWF_EINVAL, "direction update: output must not alias an input");
+    ProfScope ps(c, K_DSLASH_F32_Z, nrhs);
+    double *s = c->scal.as<double>();
+    dslash_pair_f32(c, wout, z, false, nrhs, pair_minb(), s + slot, stride, win, s + inum, s + iden, true);
     c->applies32 += nrhs;
 }
 

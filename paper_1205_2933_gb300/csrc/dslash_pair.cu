@@ -178,10 +178,11 @@ constexpr int LSTRIDE = 73;
 // The normal-equations residual update of CGNR, z <- z - a D^+ w, with
 // a = zz / ww of each right-hand side read from the scalar slots.
 struct ZUpdate {
-    const float2 *zin;  // z before the update (not the output buffer)
-    const double *zz;   // |z|^2 of right-hand side r at zz[r * stride]
-    const double *ww;   // |w|^2 = |D p|^2 of right-hand side r at ww[r * stride]
+    const float2 *zin;  // the second field (not the output buffer)
+    const double *zz;   // numerator of a for right-hand side r at zz[r * stride]
+    const double *ww;   // denominator of a at ww[r * stride]
     int stride;
+    int add;            // 1: out = D in + a zin (EPI 4); 0: out = zin - a D^+ in (EPI 2)
 };
 
 // A CTA stages its sites' links once and applies the operator to rb
@@ -191,12 +192,14 @@ struct ZUpdate {
 // norm_finish_kernel adds them in a fixed order into the scalar slots.
 // EPI 2: out = zu.zin - a D^+ in, and |out_r|^2 as with EPI 1.
 // EPI 3: out = zu.zin - D in (a residual b - D x), no norm.
+// EPI 4: out = D in + a zu.zin (CGNR's w = D p carried as D z + b w), and |out_r|^2.
+// a = zz[r * stride] / ww[r * stride] (0 where the denominator is not positive).
 template <bool DAG, int LS, int NT, int MINB, int EPI>
 __global__ void __launch_bounds__(NT, MINB)
 dslash_pair_kernel(float2 *__restrict__ out0, const float2 *__restrict__ in0, const float2 *__restrict__ U, Geom g,
                    float diag, float mf, int spb, int64_t field, double *__restrict__ npart, ZUpdate zu, int nrhs,
                    int rb) {
-    constexpr bool NORM = EPI == 1 || EPI == 2;
+    constexpr bool NORM = EPI == 1 || EPI == 2 || EPI == 4;
     constexpr int TPS = LS / 2;  // threads per site
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *sL = reinterpret_cast<float4 *>(smem_raw);                 // [spb][LSTRIDE]
@@ -315,7 +318,7 @@ dslash_pair_kernel(float2 *__restrict__ out0, const float2 *__restrict__ in0, co
         float2 *o = out + (size_t)site * row + s0;
         float a = 1.f;
         if (EPI >= 2) {
-            if (EPI == 2) {
+            if (EPI == 2 || EPI == 4) {
                 const double ww = zu.ww[(size_t)rhs * zu.stride];
                 a = ww > 0.0 ? (float)(zu.zz[(size_t)rhs * zu.stride] / ww) : 0.f;
             }
@@ -325,10 +328,14 @@ dslash_pair_kernel(float2 *__restrict__ out0, const float2 *__restrict__ in0, co
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             float2 re = unpk(acc[k].re), im = unpk(acc[k].im);
-            if (EPI >= 2) {
+            if (EPI == 2 || EPI == 3) {
                 const float4 z = sZ[k * blockDim.x + threadIdx.x];
                 re = make_float2(fmaf(-a, re.x, z.x), fmaf(-a, re.y, z.z));
                 im = make_float2(fmaf(-a, im.x, z.y), fmaf(-a, im.y, z.w));
+            } else if (EPI == 4) {
+                const float4 z = sZ[k * blockDim.x + threadIdx.x];
+                re = make_float2(fmaf(a, z.x, re.x), fmaf(a, z.z, re.y));
+                im = make_float2(fmaf(a, z.y, im.x), fmaf(a, z.w, im.y));
             }
             *reinterpret_cast<float4 *>(o + k * LS) = make_float4(re.x, im.x, re.y, im.y);
             if (NORM) nrm += re.x * re.x + im.x * im.x + re.y * re.y + im.y * im.y;
@@ -406,12 +413,16 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
         if (c->dn_part.bytes < pb) c->dn_part.alloc(pb);
         npart = c->dn_part.as<double>();
     }
-    const ZUpdate z = zu ? *zu : ZUpdate{nullptr, nullptr, nullptr, 0};
+    const ZUpdate z = zu ? *zu : ZUpdate{nullptr, nullptr, nullptr, 0, 0};
 #define PL(D, NT, M, E) dslash_pair_kernel<D, LS, NT, M, E><<<grid, threads, smem, c->stream>>>(out, in, U, g, diag, mf, \
                                                                                                  spb, field, npart, z, \
                                                                                                  nrhs, rb)
     if (zu && !nslot) {
         if (minb == 4) PL(false, 128, 4, 3); else PL(false, 64, 8, 3);
+    } else if (zu && zu->add) {
+        if (minb == 4) PL(false, 128, 4, 4); else PL(false, 64, 8, 4);
+        DWF_CHECK_LAUNCH();
+        norm_finish_kernel<<<nrhs, 1024, 0, c->stream>>>(npart, nslot, nstride, (int)grid.x);
     } else if (zu) {
         if (minb == 4) PL(true, 128, 4, 2); else PL(true, 64, 8, 2);
         DWF_CHECK_LAUNCH();
@@ -435,8 +446,8 @@ void launch_ls(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, in
 bool dslash_pair_supported(int Ls) { return Ls == 4 || Ls == 8 || Ls == 16 || Ls == 32 || Ls == 64; }
 
 void dslash_pair_f32(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int minb, double *nslot,
-                     int nstride, const float2 *zin, const double *zz, const double *ww) {
-    const ZUpdate zu{zin, zz, ww, nstride};
+                     int nstride, const float2 *zin, const double *zz, const double *ww, bool add) {
+    const ZUpdate zu{zin, zz, ww, nstride, add ? 1 : 0};
     const ZUpdate *zp = zin ? &zu : nullptr;
     switch (c->g.Ls) {
         case 4: launch_ls<4>(c, out, in, dag, nrhs, minb, nslot, nstride, zp); break;

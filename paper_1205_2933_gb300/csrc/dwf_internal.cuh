@@ -234,6 +234,11 @@ bool dslash_norm_fused(dwf_ctx *c);
 void dslash_norm(dwf_ctx *c, float2 *out, const float2 *in, bool dag, int nrhs, int slot, int stride);
 // res = b - D x on nrhs FP32 fields (res distinct from x and b; when dslash_norm_fused(c))
 void dslash_residual(dwf_ctx *c, float2 *res, const float2 *x, const float2 *b, int nrhs);
+// CGNR's w = D p carried without p: w_out = D z + b w_in for every right-hand
+// side r, b = scal[inum + r stride] / scal[iden + r stride], and |w_out|^2 into
+// scal[slot + r stride] (when dslash_norm_fused(c))
+void dslash_wupdate(dwf_ctx *c, float2 *wout, const float2 *z, const float2 *win, int nrhs, int slot, int stride,
+                    int inum, int iden);
 // CGNR's normal-equations residual update z_out = z_in - a D^+ w for every
 // right-hand side r, a = scal[izz + r stride] / scal[iww + r stride], and
 // |z_out|^2 into scal[slot + r stride] (available when dslash_norm_fused(c))

@@ -666,20 +666,71 @@ template <typename R> class BatchRunner {
         return defer_;
     }
 
+    // whether the smoother may keep its nu residuals (nu fields per right-hand
+    // side at workspace indices 100 ..): decided once per runner and nu;
+    // DWF_SMOOTHER_HISTORY=0 in the environment selects the other form
+    int hist_nu_ = -1;
+    bool hist_ok_ = false;
+    bool keep_history(int nu) {
+        if (nu != hist_nu_) {
+            if (const char *e = getenv("DWF_SMOOTHER_HISTORY"); e && atoi(e) == 0) {
+                hist_nu_ = nu;
+                hist_ok_ = false;
+                return false;
+            }
+            const size_t need = sizeof(T) * (size_t)n(0) * nr * (size_t)(nu + 1);
+            size_t fr = 0, tot = 0;
+            DWF_CUDA(cudaMemGetInfo(&fr, &tot));
+            const auto &v = mg.wsb[0];
+            bool held = (int)v.size() >= 100 + nu;
+            for (int j = 0; held && j < nu; ++j) held = v[100 + j].bytes >= need / (nu + 1);
+            hist_ok_ = held || (double)need < 0.5 * (double)fr;
+            hist_nu_ = nu;
+        }
+        return hist_ok_;
+    }
+
     void cgnr_b(T *x, const T *b, int iters, double rtol = 0.0, bool accumulate = false) {
         const int64_t N = n(0), NT = N * nr;
         if (iters <= 0) {
             if (!accumulate) bzero<T>(c, x, NT);
             return;
         }
-        T *p = wsb(0, 2), *w = wsb(0, 3);
+        // the FP32 Dslash can produce the norms of its outputs in its epilogue
+        bool fused = false;
+        if constexpr (std::is_same<R, float>::value) fused = dslash_norm_fused(c);
+        T *w = wsb(0, 3);
+        if constexpr (std::is_same<R, float>::value) {
+            if (fused && accumulate && rtol <= 0.0 && iters <= 32 && keep_history(iters)) {
+                // The smoother's form when its residuals z_0 .. z_{nu-1} fit in
+                // memory: no direction p and no per-iteration solution update.
+                // w = D p follows w_{k+1} = D z_{k+1} + b_k w_k (p_{k+1} = z_{k+1}
+                // + b_k p_k), applied in the D Dslash's epilogue as z's update is
+                // in the D^+ one, and x gains sum_k a_k p_k = sum_j g_j z_j once
+                // at the end (cg_combine_b).  |z_k|^2 and |w_k|^2 stay in slots
+                // ZB + k and WB + k, from which that kernel forms the g_j.
+                constexpr int ZB = 8, WB = 72;
+                std::vector<T *> Zh(iters);
+                for (int j = 0; j < iters; ++j) Zh[j] = wsb(0, 100 + j);
+                T *wb[2] = {w, wsb(0, 13)};
+                dslash_norm(c, Zh[0], b, true, nr, SB + ZB, SS);         // z_0 = D^+ r_0, r_0 = b
+                dslash_norm(c, wb[0], Zh[0], false, nr, SB + WB, SS);    // w_0 = D p_0, p_0 = z_0
+                for (int k = 0; k + 1 < iters; ++k) {
+                    // z_{k+1} = z_k - a_k D^+ w_k, a_k = |z_k|^2 / |w_k|^2
+                    dslash_zupdate(c, Zh[k + 1], wb[k & 1], Zh[k], nr, SB + ZB + k + 1, SS, SB + ZB + k, SB + WB + k);
+                    // w_{k+1} = D z_{k+1} + b_k w_k, b_k = |z_{k+1}|^2 / |z_k|^2
+                    dslash_wupdate(c, wb[(k + 1) & 1], Zh[k + 1], wb[k & 1], nr, SB + WB + k + 1, SS, SB + ZB + k + 1,
+                                   SB + ZB + k);
+                }
+                cg_combine_b<T>(c, x, Zh.data(), iters, SB, SS, ZB, WB, N, nr);
+                return;
+            }
+        }
+        T *p = wsb(0, 2);
         T *zbuf[2] = {wsb(0, 1), wsb(0, 5)};
         int zi = 0;
         int izz = 0, inew = 1;
         const int iww = 2;
-        // the FP32 Dslash can produce the norms of its outputs in its epilogue
-        bool fused = false;
-        if constexpr (std::is_same<R, float>::value) fused = dslash_norm_fused(c);
         auto dnorm = [&](T *out, const T *in, bool dag, int slot) {
             if constexpr (std::is_same<R, float>::value)
                 if (fused) return dslash_norm(c, out, in, dag, nr, SB + slot, SS);

@@ -169,6 +169,11 @@ constexpr int CG_MAXDEFER = 3;
 template <typename T>
 void cg_pxd_b(dwf_ctx *c, T *x, T *pout, const T *pin, T *const *pend, int np, const T *z, int base, int stride,
               int izz, int iww, int inew, int ia, int64_t n, int nrhs, int mode);
+// x += the solution of k CGNR iterations expressed in their stored
+// normal-equations residuals Z[0..k-1] (k <= 32); |z_j|^2 in slot zb + j and
+// |w_j|^2 = |D p_j|^2 in slot wb + j of each right-hand side's block
+template <typename T>
+void cg_combine_b(dwf_ctx *c, T *x, T *const *Z, int k, int base, int stride, int zb, int wb, int64_t n, int nrhs);
 template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs);
 template <typename T> void gcr_wr_b(dwf_ctx *c, T *w, T *res, const double *sc, const double2 *al, int64_t n, int nrhs);
 template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const double2 *g, int64_t n, int nrhs);

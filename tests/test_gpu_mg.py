@@ -190,17 +190,23 @@ def test_vcycle_parity(G):
     c.close()
 
 
-@pytest.mark.parametrize("cfg,nu", [(SMALL, 4), (RAGGED, 4), (SMALL, 5), (SMALL, 1), (SMALL, 8)],
-                         ids=["4^4xLs8", "ragged", "4^4xLs8-nu5", "4^4xLs8-nu1", "4^4xLs8-nu8"])
-def test_vcycle_batch_parity(G, cfg, nu):
+@pytest.mark.parametrize("cfg,nu,hist", [(SMALL, 4, 1), (RAGGED, 4, 1), (SMALL, 5, 1), (SMALL, 1, 1), (SMALL, 8, 1),
+                                         (SMALL, 1, 0), (SMALL, 5, 0), (SMALL, 8, 0), (RAGGED, 4, 0)],
+                         ids=["4^4xLs8", "ragged", "4^4xLs8-nu5", "4^4xLs8-nu1", "4^4xLs8-nu8",
+                              "4^4xLs8-nu1-p", "4^4xLs8-nu5-p", "4^4xLs8-nu8-p", "ragged-p"])
+def test_vcycle_batch_parity(G, cfg, nu, hist, monkeypatch):
     """The batched FP32 V-cycle (three right-hand sides together) against the
     oracle's V-cycle of each and against the one-at-a-time GPU V-cycle.  A
     fixed number of coarsest GCR iterations (tolerance 0) keeps both sides on
     the same Krylov step count, so the comparison is one of rounding only.
-    The batched smoother defers the solution updates of up to three
-    iterations and adds them in one pass: nu = 1 defers none, nu = 4 and 5
-    end with two and three deferred steps, nu = 8 also flushes three in its
-    middle."""
+    The batched smoother has two forms.  With its residuals kept (hist = 1)
+    it carries w = D p by recursion and forms x once from the stored z.  With
+    a direction p (hist = 0, DWF_SMOOTHER_HISTORY=0) it defers the solution
+    updates of up to three iterations and adds them in one pass: nu = 1
+    defers none, nu = 5 ends with three deferred steps, and nu = 8 also
+    flushes three in its middle."""
+    if not hist:
+        monkeypatch.setenv("DWF_SMOOTHER_HISTORY", "0")
     c = Case(G, **cfg, setup_iters0=10, setup_sweeps=0, smoother_prec=G.DWF_F32,
              coarse_prec=[G.DWF_F32], coarsest_tol=0.0, coarsest_maxiter=8, nu_post=nu)
     from gpu_util import to_internal, to_canonical, rel_norm
