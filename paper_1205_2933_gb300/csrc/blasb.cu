@@ -368,6 +368,68 @@ __global__ void cg_combine_b_kernel(T *__restrict__ x, MArgs<T> a, const double 
     }
 }
 
+// End of a chunk of m CGNR iterations k0 .. k0+m-1 that kept the residuals
+// z_{k0+1} .. z_{k0+m-1} (and z_{k0+m} when the chunk is not the last) and
+// carried w = D p by recursion.  With p_0 the chunk's first direction,
+// p_t = z_t + b_{t-1} p_{t-1}:
+//   x (+)= sum_t a_t p_t = G_0 p_0 + sum_{t=1}^{m-1} G_t z_t,
+//          G_{m-1} = a_{m-1}, G_t = a_t + b_t G_{t+1};
+//   p_0 <- p_m = P_0 p_0 + sum_{t=1}^{m} P_t z_t, P_m = 1, P_t = b_t P_{t+1}
+// (the latter only with next).  a_t = |z_t|^2 / |w_t|^2 and
+// b_t = |z_{t+1}|^2 / |z_t|^2 from the ring of scalar slots
+// zb + (k0 + t) % rs and wb + (k0 + t) % rs.
+template <typename T>
+__global__ void cg_chunk_b_kernel(T *__restrict__ x, T *__restrict__ p, MArgs<T> z, const double *__restrict__ s,
+                                  int base, int stride, int zb, int wb, int k0, int rs, int m, int next, int xinit,
+                                  int64_t n) {
+    using R = typename RealB<T>::type;
+    __shared__ R G[33], P[33];
+    const int r = blockIdx.y;
+    const size_t off = (size_t)r * n;
+    if (threadIdx.x == 0) {
+        const double *sr = s + base + (size_t)r * stride;
+        auto zz = [&](int t) { return sr[zb + (k0 + t) % rs]; };
+        auto ww = [&](int t) { return sr[wb + (k0 + t) % rs]; };
+        double g = 0.0, q = 1.0;
+        if (next) P[m] = (R)1;
+        for (int t = m - 1; t >= 0; --t) {
+            const double zt = zz(t), wt = ww(t);
+            const double al = wt > 0.0 ? zt / wt : 0.0;
+            const bool have_b = t + 1 < m || next;
+            const double be = (have_b && zt > 0.0) ? zz(t + 1) / zt : 0.0;
+            g = al + (t + 1 < m ? be * g : 0.0);
+            G[t] = (R)g;
+            if (next) {
+                q *= be;
+                P[t] = (R)q;
+            }
+        }
+    }
+    __syncthreads();
+    const int nz = next ? m : m - 1;  // z pointers: z_1 .. z_nz
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T pv = p[off + i];
+        T xv = xinit ? T{0, 0} : x[off + i];
+        T pn = next ? T{P[0] * pv.x, P[0] * pv.y} : T{0, 0};
+        xv.x += G[0] * pv.x;
+        xv.y += G[0] * pv.y;
+#pragma unroll 8
+        for (int t = 1; t <= nz; ++t) {
+            const T u = z.v[t - 1][off + i];
+            if (t < m) {
+                xv.x += G[t] * u.x;
+                xv.y += G[t] * u.y;
+            }
+            if (next) {
+                pn.x += P[t] * u.x;
+                pn.y += P[t] * u.y;
+            }
+        }
+        x[off + i] = xv;
+        if (next) p[off + i] = pn;
+    }
+}
+
 dim3 grid_b(dwf_ctx *c, int64_t n, int nrhs, int cap_per_sm) {
     int64_t b = (n + BT - 1) / BT;
     int64_t cap = std::max<int64_t>(1, (int64_t)c->sm_count * cap_per_sm / std::max(1, nrhs));
@@ -519,6 +581,19 @@ void cg_combine_b(dwf_ctx *c, T *x, T *const *Z, int k, int base, int stride, in
     DWF_CHECK_LAUNCH();
 }
 
+template <typename T>
+void cg_chunk_b(dwf_ctx *c, T *x, T *p, T *const *Z, int m, bool next, bool xinit, int base, int stride, int zb, int wb,
+                int k0, int rs, int64_t n, int nrhs) {
+    DWF_REQUIRE(m >= 1 && m <= 32 && rs > m, DWF_EINVAL, "cg_chunk_b: 1 to 32 iterations, slot ring longer than that");
+    dim3 gr = grid_b(c, n, nrhs, 16);
+    MArgs<T> a;
+    a.k = next ? m : m - 1;
+    for (int j = 0; j < a.k; ++j) a.v[j] = Z[j];
+    cg_chunk_b_kernel<T><<<gr, BT, 0, c->stream>>>(x, p, a, c->scal.as<double>(), base, stride, zb, wb, k0, rs, m,
+                                                   next ? 1 : 0, xinit ? 1 : 0, n);
+    DWF_CHECK_LAUNCH();
+}
+
 #define INSTB(T)                                                                                            \
     template void norm2_b<T>(dwf_ctx *, BatchScratch &, int, int, const T *, int64_t, int);                  \
     template void multidot_b<T>(dwf_ctx *, BatchScratch &, int, int, T *const *, int, const T *, int64_t, int); \
@@ -531,6 +606,8 @@ void cg_combine_b(dwf_ctx *c, T *x, T *const *Z, int k, int base, int stride, in
     template void cg_pxd_b<T>(dwf_ctx *, T *, T *, const T *, T *const *, int, const T *, int, int, int, int, int, \
                               int, int64_t, int, int);                                                         \
     template void cg_combine_b<T>(dwf_ctx *, T *, T *const *, int, int, int, int, int, int64_t, int);        \
+    template void cg_chunk_b<T>(dwf_ctx *, T *, T *, T *const *, int, bool, bool, int, int, int, int, int, int,   \
+                                int64_t, int);                                                                 \
     template void axpy_b<T>(dwf_ctx *, T *, const T *, const double2 *, int64_t, int);                        \
     template void gcr_wr_b<T>(dwf_ctx *, T *, T *, const double *, const double2 *, int64_t, int);            \
     template void combo_b<T>(dwf_ctx *, T *, T *const *, int, const double2 *, int64_t, int);

@@ -666,6 +666,8 @@ template <typename R> class BatchRunner {
         return defer_;
     }
 
+    static constexpr int CHUNK = 8;  // iterations per chunk of a long CGNR run in the residual-keeping form
+
     // whether the smoother may keep its nu residuals (nu fields per right-hand
     // side at workspace indices 100 ..): decided once per runner and nu;
     // DWF_SMOOTHER_HISTORY=0 in the environment selects the other form
@@ -723,6 +725,54 @@ template <typename R> class BatchRunner {
                                    SB + ZB + k);
                 }
                 cg_combine_b<T>(c, x, Zh.data(), iters, SB, SS, ZB, WB, N, nr);
+                return;
+            }
+            if (fused && !accumulate && keep_history(CHUNK + 1)) {
+                // A long run (the setup's relaxation) in the same form, in
+                // chunks of CHUNK iterations: each keeps its residuals in a ring
+                // of CHUNK + 1 buffers, and its end adds sum a_k p_k to x and
+                // forms the next chunk's first direction from the chunk's first
+                // one and those residuals (cg_chunk_b).  A residual test (every
+                // chunk) computes b - D x itself.  Norms in slot rings of RS.
+                constexpr int RS = 2 * CHUNK, ZB = 8, WB = 8 + RS;
+                T *pp = wsb(0, 2);
+                T *wb[2] = {w, wsb(0, 13)};
+                std::vector<T *> ring(CHUNK + 1);
+                for (int j = 0; j <= CHUNK; ++j) ring[j] = wsb(0, 100 + j);
+                auto zptr = [&](int k) { return k == 0 ? pp : ring[k % (CHUNK + 1)]; };  // z_0 is p_0
+                const int irr = 3;
+                std::vector<double> r0(nr, 0.0), sv;
+                if (rtol > 0.0) {
+                    norm2_b<T>(c, mg.bscratch, SB + irr, SS, b, N, nr);
+                    read_block(sv);
+                    for (int q = 0; q < nr; ++q) r0[q] = std::sqrt(sv[(size_t)q * SS + irr]);
+                }
+                dslash_norm(c, pp, b, true, nr, SB + ZB, SS);       // p_0 = z_0 = D^+ b
+                dslash_norm(c, wb[0], pp, false, nr, SB + WB, SS);  // w_0 = D p_0
+                std::vector<T *> zc(CHUNK);
+                for (int k0 = 0; k0 < iters;) {
+                    const int k1 = std::min(k0 + CHUNK, iters), m = k1 - k0;
+                    const bool last = k1 == iters;
+                    for (int k = k0; k < (last ? k1 - 1 : k1); ++k) {
+                        dslash_zupdate(c, zptr(k + 1), wb[k & 1], zptr(k), nr, SB + ZB + (k + 1) % RS, SS,
+                                       SB + ZB + k % RS, SB + WB + k % RS);
+                        dslash_wupdate(c, wb[(k + 1) & 1], zptr(k + 1), wb[k & 1], nr, SB + WB + (k + 1) % RS, SS,
+                                       SB + ZB + (k + 1) % RS, SB + ZB + k % RS);
+                    }
+                    const int nz = last ? m - 1 : m;
+                    for (int t = 1; t <= nz; ++t) zc[t - 1] = zptr(k0 + t);
+                    cg_chunk_b<T>(c, x, pp, zc.data(), m, !last, k0 == 0, SB, SS, ZB, WB, k0, RS, N, nr);
+                    k0 = k1;
+                    if (rtol > 0.0 && !last) {
+                        T *rt = wsb(0, 0);
+                        dslash_residual(c, rt, x, b, nr);
+                        norm2_b<T>(c, mg.bscratch, SB + irr, SS, rt, N, nr);
+                        read_block(sv);
+                        bool all = true;
+                        for (int q = 0; q < nr; ++q) all &= std::sqrt(sv[(size_t)q * SS + irr]) <= rtol * r0[q];
+                        if (all) break;
+                    }
+                }
                 return;
             }
         }

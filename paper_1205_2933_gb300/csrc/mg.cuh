@@ -174,6 +174,13 @@ void cg_pxd_b(dwf_ctx *c, T *x, T *pout, const T *pin, T *const *pend, int np, c
 // |w_j|^2 = |D p_j|^2 in slot wb + j of each right-hand side's block
 template <typename T>
 void cg_combine_b(dwf_ctx *c, T *x, T *const *Z, int k, int base, int stride, int zb, int wb, int64_t n, int nrhs);
+// End of a chunk of m CGNR iterations from k0 that kept their residuals
+// Z[t-1] = z_{k0+t} (t = 1 .. m-1, and m with next): x (+)= sum_t a_t p_t with
+// p the chunk's first direction, and with next p <- the next chunk's first
+// direction; norms in the slot rings zb + (k0 + t) % rs and wb + (k0 + t) % rs
+template <typename T>
+void cg_chunk_b(dwf_ctx *c, T *x, T *p, T *const *Z, int m, bool next, bool xinit, int base, int stride, int zb, int wb,
+                int k0, int rs, int64_t n, int nrhs);
 template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs);
 template <typename T> void gcr_wr_b(dwf_ctx *c, T *w, T *res, const double *sc, const double2 *al, int64_t n, int nrhs);
 template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const double2 *g, int64_t n, int nrhs);

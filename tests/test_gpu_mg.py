@@ -228,14 +228,19 @@ def test_vcycle_batch_parity(G, cfg, nu, hist, monkeypatch):
     c.close()
 
 
-def test_fp32_batched_relaxation_stops_with_the_oracle(G):
+@pytest.mark.parametrize("hist", [1, 0], ids=["chunks", "direction"])
+def test_fp32_batched_relaxation_stops_with_the_oracle(G, hist, monkeypatch):
     """The FP32 setup relaxes the start vectors in one batched CGNR whose
     residual test (every 8 iterations) forms |D x| explicitly.  On this lattice
     the oracle's relaxation of each vector passes |D x| <= 4e-3 |D x0| first at
     iteration 24 (about 7e-3 at 16, 2.1e-3 to 2.4e-3 at 24), so both sides stop
     there and the bases agree to FP32 rounding; had the GPU run on to the
     100-iteration cap, or stopped at 16, they would differ by order one (0.85 and 1.4
-    in this measure, oracle against oracle)."""
+    in this measure, oracle against oracle).  Both forms of the batched CGNR run:
+    chunks of 8 iterations that keep their residuals (hist = 1) and the form with
+    a direction vector (hist = 0, DWF_SMOOTHER_HISTORY=0)."""
+    if not hist:
+        monkeypatch.setenv("DWF_SMOOTHER_HISTORY", "0")
     c = Case(G, **SMALL, setup_iters0=100, setup_tol0=4e-3, setup_sweeps=0, smoother_prec=G.DWF_F32,
              coarse_prec=[G.DWF_F32])
     from gpu_util import to_canonical, rel_max
