@@ -17,12 +17,13 @@
 // flight: the copy and the B' build of one overlap the MMAs of the other and
 // the read-back of the one before.
 //
-// The GCR around it is the same algorithm as the SIMT batched solver
-// (coarse_gcr_batch.cu): classical Gram-Schmidt twice, |w| normalisation,
+// The GCR around it is that of the SIMT batched solver (coarse_gcr_batch.cu)
+// with one change, the second classical Gram-Schmidt pass runs only where
+// the first removed 3/4 or more of |w|^2: |w| normalisation,
 // x += <w,r> z, r -= <w,r> w, true residual at each restart, right-hand
-// sides leaving the lockstep as they converge.  Element arithmetic and the
-// in-warp sums are FP32; per-CTA partials and the fixed-order cross-CTA sums
-// are FP64, so all CTAs take identical decisions.  Waits on the copy and the
+// sides leaving the lockstep as they converge.  Element arithmetic, the
+// in-warp sums and the per-CTA partials are FP32; every CTA adds all CTAs'
+// partials in the same fixed order, so all take identical decisions.  Waits on the copy and the
 // MMA completion are bounded (about one second); on expiry the kernel sets
 // an error word, every CTA leaves the iteration at the next reduction, and
 // the caller reports DWF_ETIMEOUT.
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
     __shared__ int act[TMAXB], its[TMAXB];
     __shared__ __align__(8) uint64_t bars[5];  // copy and MMA barriers of the two stages; [4]: the test hook's
     __shared__ uint32_t tbase;
-    __shared__ int bad, quit;
+    __shared__ int bad, quit, second;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nb = a.nb, nblk = gridDim.x;
     const int V = a.V, Nf = V * NV;
@@ -506,32 +507,49 @@ __global__ void __launch_bounds__(TCT, 1) coarse_gcr_tc_kernel(TcArgs a) {
         __threadfence();
         grid.sync();
         tc_apply<NV>(a, pp, Wk, Zk, s0, s1, act, Nf, &bad);
-        // first classical Gram-Schmidt pass
-        if (k > 0) {
-            zero_red(k * nb);
-            dots(k, false);
-            finish(k * nb);
-            if (quit) break;
-            for (int base = warp * 32; base < nitems; base += TCT) {
-                const int rr = base / Epad;
-                const int eo = base - rr * Epad + lane;
-                if (!act[rr] || eo >= E) continue;
-                const int ie = rr * Nf + e0 + eo;
-                float2 w = Wk[ie], z = Zk[ie];
-                project_out(k, w, z, rr, ie);
-                Wk[ie] = w;
-                Zk[ie] = z;
-            }
-            __syncthreads();
-        }
-        // second pass, reduced together with |W_k|^2 and <W_k, r> of the first
-        // pass's W_k: after the second projection |W_k|^2 loses sum |beta_i|^2
-        // (the W_i are orthonormal) and <W_k, r> is unchanged (r is orthogonal
-        // to the W_i in GCR)
+        // Classical Gram-Schmidt against the stored W_i, reduced together with
+        // |W_k|^2 and <W_k, r>: after the projection |W_k|^2 loses
+        // sum |beta_i|^2 (the W_i are orthonormal) and <W_k, r> is unchanged
+        // (r is orthogonal to the W_i in GCR).  Where the projection removes
+        // 3/4 or more of |W_k|^2 for some right-hand side, that difference
+        // has lost too many digits: the projection is applied and a second
+        // pass reduced the same way instead.  Every CTA holds the same totals
+        // and so takes the same branch.
         zero_red((k + 2) * nb);
         dots(k, true);
         finish((k + 2) * nb);
         if (quit) break;
+        if (k > 0) {
+            if (tid == 0) {
+                bool again = false;
+                for (int rr = 0; rr < nb; ++rr) {
+                    if (!act[rr]) continue;
+                    double removed = 0.0;
+                    for (int i = 0; i < k; ++i)
+                        removed += tot[i * nb + rr].x * tot[i * nb + rr].x + tot[i * nb + rr].y * tot[i * nb + rr].y;
+                    again |= !(removed < 0.75 * tot[k * nb + rr].x);
+                }
+                second = again;
+            }
+            __syncthreads();
+            if (second) {
+                for (int base = warp * 32; base < nitems; base += TCT) {
+                    const int rr = base / Epad;
+                    const int eo = base - rr * Epad + lane;
+                    if (!act[rr] || eo >= E) continue;
+                    const int ie = rr * Nf + e0 + eo;
+                    float2 w = Wk[ie], z = Zk[ie];
+                    project_out(k, w, z, rr, ie);
+                    Wk[ie] = w;
+                    Zk[ie] = z;
+                }
+                __syncthreads();
+                zero_red((k + 2) * nb);
+                dots(k, true);
+                finish((k + 2) * nb);
+                if (quit) break;
+            }
+        }
         if (tid < nb) {
             double ww = tot[k * nb + tid].x;
             for (int i = 0; i < k; ++i) ww -= tot[i * nb + tid].x * tot[i * nb + tid].x + tot[i * nb + tid].y * tot[i * nb + tid].y;
@@ -652,7 +670,7 @@ template <int NV> void *tc_kernel_fn() { return (void *)coarse_gcr_tc_kernel<NV>
 
 size_t tc_static_smem() {
     return sizeof(float) * NWARP * 2 * TMAXV + sizeof(double2) * TMAXV + 2 * sizeof(double) * TMAXB +
-           2 * sizeof(int) * TMAXB + 5 * sizeof(uint64_t) + 3 * sizeof(int) + 64;
+           2 * sizeof(int) * TMAXB + 5 * sizeof(uint64_t) + 4 * sizeof(int) + 64;
 }
 
 template <int NV> bool tc_fits(dwf_ctx *c, int nb) {
