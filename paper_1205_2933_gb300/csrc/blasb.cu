@@ -138,40 +138,6 @@ __global__ void multiaxpy_b_kernel(T *__restrict__ w, MArgs<T> a, const double *
     }
 }
 
-// multiaxpy_b that also reduces the updated w: |w_r|^2 into slot nbase and
-// <w_r, q_r> into slots nbase + 2, nbase + 3 (nbase + 1 is written 0)
-template <typename T>
-__global__ void __launch_bounds__(BT) multiaxpy_nrm_b_kernel(T *__restrict__ w, MArgs<T> a, const T *__restrict__ q,
-                                                             double2 *part, unsigned *count, double *s, int base,
-                                                             int stride, double sgn, int nbase, int64_t n) {
-    using R = typename RealB<T>::type;
-    const int r = blockIdx.y;
-    const size_t off = (size_t)r * n;
-    R cr[32], ci[32];
-    for (int j = 0; j < a.k; ++j) {
-        cr[j] = (R)(sgn * s[base + r * stride + 2 * j]);
-        ci[j] = (R)(sgn * s[base + r * stride + 2 * j + 1]);
-    }
-    R nn = 0, dr = 0, di = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T v = w[off + i];
-#pragma unroll 4
-        for (int j = 0; j < a.k; ++j) {
-            T u = a.v[j][off + i];
-            v.x += cr[j] * u.x - ci[j] * u.y;
-            v.y += cr[j] * u.y + ci[j] * u.x;
-        }
-        w[off + i] = v;
-        const T y = q[off + i];
-        nn += v.x * v.x + v.y * v.y;
-        dr += v.x * y.x + v.y * y.y;
-        di += v.x * y.y - v.y * y.x;
-    }
-    // every CTA has read its coefficients before the last one writes the results
-    double2 m[2] = {make_double2((double)nn, 0.0), make_double2((double)dr, (double)di)};
-    finish_b<2>(m, part, count, s, nbase, stride);
-}
-
 // CGNR steps with per-RHS scalars at slot blocks base + r*stride:
 //   xr:  a = s[izz] / s[iww]; x += a p; r -= a w
 //   p :  b = s[inew] / s[iold]; p = z + b p
@@ -530,20 +496,6 @@ void multiaxpy_b(dwf_ctx *c, T *w, T *const *V, int k, int base, int stride, dou
 }
 
 template <typename T>
-void multiaxpy_nrm_b(dwf_ctx *c, BatchScratch &bs, T *w, T *const *V, int k, const T *q, int base, int stride,
-                     double sgn, int nbase, int64_t n, int nrhs) {
-    DWF_REQUIRE(k >= 1 && k <= 32, DWF_EINVAL, "multiaxpy_nrm_b: 1 to 32 vectors");
-    DWF_REQUIRE(nbase + 3 < base || nbase >= base + 2 * k, DWF_EINVAL, "multiaxpy_nrm_b: result slots overlap the coefficients");
-    dim3 g = grid_b(c, n, nrhs, 8);
-    MArgs<T> a;
-    a.k = k;
-    for (int j = 0; j < k; ++j) a.v[j] = V[j];
-    multiaxpy_nrm_b_kernel<T><<<g, BT, 0, c->stream>>>(w, a, q, bs.part.as<double2>(), bs.count.as<unsigned>(),
-                                                       c->scal.as<double>(), base, stride, sgn, nbase, n);
-    DWF_CHECK_LAUNCH();
-}
-
-template <typename T>
 void cg_xr_b(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs) {
     dim3 g = grid_b(c, n, nrhs, 16);
     cg_xr_b_kernel<T><<<g, BT, 0, c->stream>>>(x, r, p, w, c->scal.as<double>(), base, stride, izz, iww, n);
@@ -646,8 +598,6 @@ void cg_chunk_b(dwf_ctx *c, T *x, T *p, T *const *Z, int m, bool next, bool xini
     template void norm2_b<T>(dwf_ctx *, BatchScratch &, int, int, const T *, int64_t, int);                  \
     template void multidot_b<T>(dwf_ctx *, BatchScratch &, int, int, T *const *, int, const T *, int64_t, int); \
     template void multiaxpy_b<T>(dwf_ctx *, T *, T *const *, int, int, int, double, int64_t, int);            \
-    template void multiaxpy_nrm_b<T>(dwf_ctx *, BatchScratch &, T *, T *const *, int, const T *, int, int, double, \
-                                     int, int64_t, int);                                                       \
     template void cg_xr_b<T>(dwf_ctx *, T *, T *, const T *, const T *, int, int, int, int, int64_t, int);    \
     template void cg_p_b<T>(dwf_ctx *, T *, const T *, int, int, int, int, int64_t, int);                     \
     template void cg_r_b<T>(dwf_ctx *, T *, const T *, const T *, int, int, int, int, int64_t, int);          \

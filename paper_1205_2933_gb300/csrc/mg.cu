@@ -1152,13 +1152,11 @@ template <typename R> class BatchRunner {
             dslash(c, W[k], Z[k], false, nr);
             for (int r = 0; r < nr; ++r)
                 for (int i = 0; i <= k; ++i) Tm[(size_t)r * restart * restart + i * restart + k] = make_double2(0, 0);
-            // Classical Gram-Schmidt of W_k against W_0 .. W_{k-1} (a second pass
-            // where the first removed 3/4 or more of |W_k|^2); the update pass
-            // also reduces |W_k|^2 and <W_k, r> of the result into slots NRM ..
-            constexpr int NRM = 120;
+            // classical Gram-Schmidt of W_k against W_0 .. W_{k-1} (a second pass
+            // where the first removed 3/4 or more of |W_k|^2)
             for (int pass = 0; pass < 2; ++pass) {
                 multidot_b<T>(c, mg.bscratch, SB, SS, W.data(), k + 1, W[k], N, nr);
-                if (k > 0) multiaxpy_nrm_b<T>(c, mg.bscratch, W[k], W.data(), k, rr, SB, SS, -1.0, SB + NRM, N, nr);
+                if (k > 0) multiaxpy_b<T>(c, W[k], W.data(), k, SB, SS, -1.0, N, nr);
                 read_block(sv);
                 bool again = false;
                 for (int r = 0; r < nr; ++r) {
@@ -1174,17 +1172,13 @@ template <typename R> class BatchRunner {
                 }
                 if (!again) break;
             }
-            // |W_k|^2 and <W_k, r> per right-hand side (k = 0: computed here)
-            int iw = NRM;
-            if (k == 0) {
-                norm2_b<T>(c, mg.bscratch, SB + 2, SS, W[k], N, nr);
-                T *wk = W[k];
-                multidot_b<T>(c, mg.bscratch, SB + 4, SS, &wk, 1, rr, N, nr);
-                read_block(sv);
-                iw = 2;
-            }
+            // |W_k|^2 and <W_k, r> per right-hand side
+            norm2_b<T>(c, mg.bscratch, SB + 2, SS, W[k], N, nr);
+            T *wk = W[k];
+            multidot_b<T>(c, mg.bscratch, SB + 4, SS, &wk, 1, rr, N, nr);
+            read_block(sv);
             for (int r = 0; r < nr; ++r) {
-                const double *v = sv.data() + (size_t)r * SS + iw - 2;
+                const double *v = sv.data() + (size_t)r * SS;
                 const double ww = v[2];
                 double2 &Td = Tm[(size_t)r * restart * restart + k * restart + k];
                 const bool ok = ww > 0.0 && std::isfinite(ww);

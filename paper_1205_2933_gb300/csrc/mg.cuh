@@ -151,11 +151,6 @@ template <typename T> void norm2_b(dwf_ctx *c, BatchScratch &bs, int base, int s
 template <typename T>
 void multidot_b(dwf_ctx *c, BatchScratch &bs, int base, int stride, T *const *V, int k, const T *w, int64_t n, int nrhs);
 template <typename T> void multiaxpy_b(dwf_ctx *c, T *w, T *const *V, int k, int base, int stride, double sgn, int64_t n, int nrhs);
-// multiaxpy_b, and |w_r|^2 into slot nbase, <w_r, q_r> into nbase + 2, + 3 of
-// each right-hand side's block (the slots must not overlap the coefficients)
-template <typename T>
-void multiaxpy_nrm_b(dwf_ctx *c, BatchScratch &bs, T *w, T *const *V, int k, const T *q, int base, int stride,
-                     double sgn, int nbase, int64_t n, int nrhs);
 template <typename T>
 void cg_xr_b(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
 template <typename T> void cg_p_b(dwf_ctx *c, T *p, const T *z, int base, int stride, int inew, int iold, int64_t n, int nrhs);
