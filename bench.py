@@ -352,7 +352,7 @@ def _timed(torch, f):
 
 
 def run_workload(args):
-    """The survey's other measured configurations (one JSON line each):
+    """The other measured configurations (one JSON line each):
     config3: 24^3 x 48, Ls = 16, m_f = 0.001, heatbath beta = 6.0 (seed 200),
       12 spin-colour point sources at the origin (plus args.nrhs - 12 Z2 noise
       sources, seeds 201...), all solved as one batch with the chosen mixed
