@@ -80,8 +80,8 @@ def parse():
                          "reference of the per-solve errors)")
     ap.add_argument("--e2e-steps", type=int, default=2, help="timed end-to-end steps (after one warm-up)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-setup comparison")
-    ap.add_argument("--workload", choices=["headline", "config3", "config4"], default="headline",
-                    help="config3: 24^3x48 Ls=16 batched point (+Z2) sources; config4: the uneven batch "
+    ap.add_argument("--workload", choices=["headline", "point-sources-24x48", "uneven-batch"], default="headline",
+                    help="point-sources-24x48: 24^3x48 Ls=16 batched point (+Z2) sources; uneven-batch: the uneven batch "
                          "8^4 + 12^3x24 + 16^3x32 in one context and a 3-level solve (one JSON line each; "
                          "the default is the headline workload)")
     ap.add_argument("--profile-solve", action="store_true",
@@ -353,11 +353,11 @@ def _timed(torch, f):
 
 def run_workload(args):
     """The other measured configurations (one JSON line each):
-    config3: 24^3 x 48, Ls = 16, m_f = 0.001, heatbath beta = 6.0 (seed 200),
+    point-sources-24x48: 24^3 x 48, Ls = 16, m_f = 0.001, heatbath beta = 6.0 (seed 200),
       12 spin-colour point sources at the origin (plus args.nrhs - 12 Z2 noise
       sources, seeds 201...), all solved as one batch with the chosen mixed
       precision; per-RHS time, Dslash GB/s and the coarse solver's share.
-    config4: 8^4, 12^3 x 24 and 16^3 x 32 at Ls = 16, m_f = 0.002, heatbath
+    uneven-batch: 8^4, 12^3 x 24 and 16^3 x 32 at Ls = 16, m_f = 0.002, heatbath
       beta = 5.9 (seeds 300-302) in one batch context (one setup call, one
       solve call over all three lattices) against the three lattices one after
       another in contexts of their own; then a 3-level solve of the 16^3 x 32
@@ -367,7 +367,7 @@ def run_workload(args):
     p = mixed_params(G)
     line = {"metric": f"{args.workload}: solve time per right-hand side (setup amortised)", "unit": "s/rhs",
             "higher_is_better": False, "dtype": "f32+bf16 (fp64 outer)", "data": "synthetic"}
-    if args.workload == "config3":
+    if args.workload == "point-sources-24x48":
         dims, mf = (24, 24, 24, 48), 0.001
         nr = max(12, args.nrhs)
         U = I.heatbath_links(dims, BETA, HB_SWEEPS, 200)
