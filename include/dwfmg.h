@@ -341,6 +341,28 @@ const char *dwf_strerror(dwf_status s);
  * context and stream).  Safe on NULL. */
 void dwf_destroy(dwf_ctx *ctx);
 
+/* ---- Environment switches ----------------------------------------------
+ * Unset, every switch selects the production path.  They exist for
+ * measurements and tests; each is read once per process except where noted.
+ *   DWF_DSLASH_PAIR=0        FP32 Dslash with one fifth-dimension slice per
+ *                            thread instead of the paired kernel (which also
+ *                            disables the fused norm and residual epilogues)
+ *   DWF_DSLASH_PAIR_MINB=4   paired FP32 Dslash in 128-thread CTAs, 4 per SM
+ *                            (default: 64 threads, 8 per SM)
+ *   DWF_DSLASH_MINB=6        one-slice Dslash at 80 registers, 6 CTAs per SM
+ *   DWF_BATCH=0              several right-hand sides solved one at a time
+ *   DWF_COARSE_BATCH=0       the batched V-cycle's coarsest solves one
+ *                            right-hand side per cooperative launch
+ *   DWF_SMOOTHER_HISTORY=0   the batched CGNR with a direction vector instead
+ *                            of the form that keeps its residuals (read at
+ *                            every solve call)
+ *   DWF_TC_FORCE_WAIT=n      test hook: the first n launches of the
+ *                            tensor-core coarsest solver begin with a wait
+ *                            that runs out after about one second (the call
+ *                            returns DWF_ETIMEOUT)
+ *   DWF_VERBOSE=1            the coarsest solver's grid tuning is printed
+ */
+
 #ifdef __cplusplus
 }
 #endif
