@@ -450,8 +450,8 @@ def run_workload(args):
                                "status": st_b.status},
                      "one_after_another": seq, "one_after_another_s": tseq, "batch_s": ts_b + tv_b,
                      "three_level_16x16x16x32": three,
-                     "note": "32^3x64 with three levels is not run: its FP64 and FP32 Nvec=24 bases alone "
-                             "hold 231 GB of the 288 GB"})
+                     "note": "32^3x64 with three levels is not run: at Nvec 24 its FP32 basis, the FP64 "
+                             "adaptive vectors and the coarse construction's D q_k take 231 GB of the 288 GB"})
     print(json.dumps(line), flush=True)
 
 
