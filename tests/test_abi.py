@@ -93,3 +93,16 @@ def test_struct_layouts_match_the_header(tmp_path):
         cls = structs[name]
         expect = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
         assert int(value) == expect, (name, field, value, expect)
+
+
+def test_environment_switches_are_documented():
+    """Every environment variable the library reads is listed in the header."""
+    csrc = os.path.join(ROOT, "paper_1205_2933_gb300", "csrc")
+    used = set()
+    for f in os.listdir(csrc):
+        if f.endswith((".cu", ".cuh", ".h")):
+            used |= set(re.findall(r'getenv\("([A-Z0-9_]+)"\)', open(os.path.join(csrc, f)).read()))
+    header = open(os.path.join(ROOT, "include", "dwfmg.h")).read()
+    assert used, "no switches found"
+    missing = sorted(v for v in used if v not in header)
+    assert not missing, missing
