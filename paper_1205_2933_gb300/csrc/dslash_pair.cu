@@ -5,7 +5,7 @@
 // 4D site.  Every complex quantity is held as two register pairs: the real
 // parts (s0, s1) and the imaginary parts (s0, s1).  The link is the same
 // for both slices, so each complex multiply-add of the 3x3 link products is
-// four packed FP32x2 FMAs for two sites (fma.rn.f32x2) instead of eight
+// four packed FP32x2 FMAs for the two slices (fma.rn.f32x2) instead of eight
 // scalar FMAs, and multiplications by +-i are a choice of operands, not
 // arithmetic.  Component loads are 16 bytes (the two slices of one
 // component are adjacent in the s-fastest layout).  Links are staged once
