@@ -157,6 +157,41 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def dslash_roofline(prof, units, V5, peak, peak_kind):
+    """Roofline object of the dominant FP32 Dslash class by summed device time:
+    the plain kernels (204 B per 5D site) or those with a fused second field
+    (300 B per 5D site); the other class goes in `other_dslash`.  prof maps a
+    class name to (launches, ms), units to the fields its launches covered
+    (a batched launch over nrhs fields counts nrhs); achieved = algorithmic
+    bytes of all those fields over their summed device time."""
+    def one(name, bytes_site, traffic, note):
+        n, ms = prof[name]
+        if not n or not ms:
+            return None
+        u = units[name]
+        achieved = bytes_site * V5 * u / (ms * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "avg_launch_us": ms / n * 1e3, "launches": n, "fields": u, "ms": ms,
+                "bytes_per_launch": bytes_site * V5 * u / n, "bytes_per_site": bytes_site, "traffic_note": note}
+
+    roofs = [r for r in (
+        one("dslash_f32", FINE_BYTES_F32, DSLASH_TRAFFIC_PER_FIELD,
+            "ncu dram bytes per field application of the norm-epilogue kernel (two-field launch of "
+            "2 x 16^3x16x16 = one 16^3x32x16 field of sites)"),
+        one("dslash_f32_z", FINE_BYTES_F32_Z, DSLASH_Z_TRAFFIC_PER_FIELD,
+            "ncu dram bytes per field application of the residual-update kernel z - a D^+ w (same launch "
+            "shape); the class also holds the w updates D z + b w and the V-cycle's b - D x (same bytes)"))
+             if r]
+    roofs.sort(key=lambda r: -r["ms"])
+    roof = roofs[0] if roofs else None
+    if roof and len(roofs) > 1:
+        o = roofs[1]
+        roof["other_dslash"] = {k: o[k] for k in ("kernel", "achieved", "frac", "ms", "fields", "bytes_per_site",
+                                                  "traffic")}
+    return roof
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -568,35 +603,7 @@ def main():
     V5 = ctx.V * LS
     peak, peak_kind = measured_peaks()
 
-    # roofline of the dominant kernel class (by summed device time in the timed
-    # region): the plain FP32 Dslash or the one with a fused residual update;
-    # launches cover 1 (setup, single solves) or nrhs (batched solve) fields:
-    # algorithmic bytes of all of them over their summed device time
-    def dslash_roof(name, bytes_site, traffic, note):
-        n, ms = prof[name]
-        if not n:
-            return None
-        u = units[name]
-        achieved = bytes_site * V5 * u / (ms * 1e-3) / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "avg_launch_us": ms / n * 1e3, "launches": n, "fields": u, "ms": ms,
-                "bytes_per_launch": bytes_site * V5 * u / n, "bytes_per_site": bytes_site, "traffic_note": note}
-
-    roofs = [r for r in (
-        dslash_roof("dslash_f32", FINE_BYTES_F32, DSLASH_TRAFFIC_PER_FIELD,
-                    "ncu dram bytes per field application of the norm-epilogue kernel (two-field launch of "
-                    "2 x 16^3x16x16 = one 16^3x32x16 field of sites)"),
-        dslash_roof("dslash_f32_z", FINE_BYTES_F32_Z, DSLASH_Z_TRAFFIC_PER_FIELD,
-                    "ncu dram bytes per field application of the residual-update kernel z - a D^+ w (same launch "
-                    "shape); the class also holds the w updates D z + b w and the V-cycle's b - D x (same bytes)"))
-             if r]
-    roofs.sort(key=lambda r: -r["ms"])
-    roof = roofs[0] if roofs else None
-    if roof and len(roofs) > 1:
-        o = roofs[1]
-        roof["other_dslash"] = {k: o[k] for k in ("kernel", "achieved", "frac", "ms", "fields", "bytes_per_site",
-                                                  "traffic")}
+    roof = dslash_roofline(prof, units, V5, peak, peak_kind)
 
     # fine-operator applications per solve in the timed region, setup included
     # (the paper's cost unit, Sec. 3): all fields the FP32 and FP64 Dslash processed
