@@ -138,43 +138,6 @@ __global__ void multiaxpy_b_kernel(T *__restrict__ w, MArgs<T> a, const double *
     }
 }
 
-// CGNR steps with per-RHS scalars at slot blocks base + r*stride:
-//   xr:  a = s[izz] / s[iww]; x += a p; r -= a w
-//   p :  b = s[inew] / s[iold]; p = z + b p
-template <typename T>
-__global__ void cg_xr_b_kernel(T *__restrict__ x, T *__restrict__ rr, const T *__restrict__ p, const T *__restrict__ w,
-                               const double *__restrict__ s, int base, int stride, int izz, int iww, int64_t n) {
-    using R = typename RealB<T>::type;
-    const int r = blockIdx.y;
-    const size_t off = (size_t)r * n;
-    const double ww = s[base + r * stride + iww];
-    const R a = ww > 0.0 ? (R)(s[base + r * stride + izz] / ww) : R(0);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T pv = p[off + i], wv = w[off + i], xv = x[off + i], rv = rr[off + i];
-        xv.x += a * pv.x;
-        xv.y += a * pv.y;
-        rv.x -= a * wv.x;
-        rv.y -= a * wv.y;
-        x[off + i] = xv;
-        rr[off + i] = rv;
-    }
-}
-template <typename T>
-__global__ void cg_p_b_kernel(T *__restrict__ p, const T *__restrict__ z, const double *__restrict__ s, int base,
-                              int stride, int inew, int iold, int64_t n) {
-    using R = typename RealB<T>::type;
-    const int r = blockIdx.y;
-    const size_t off = (size_t)r * n;
-    const double old = s[base + r * stride + iold];
-    const R b = old > 0.0 ? (R)(s[base + r * stride + inew] / old) : R(0);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T pv = p[off + i], zv = z[off + i];
-        pv.x = zv.x + b * pv.x;
-        pv.y = zv.y + b * pv.y;
-        p[off + i] = pv;
-    }
-}
-
 // The CGNR step split so that every field is read once per iteration:
 //   r:  a = s[izz] / s[iww]; r -= a w
 //   px: a as above, b = s[inew] / s[izz]; x += a p; p = z + b p
@@ -274,21 +237,6 @@ __global__ void cg_pxd_b_kernel(T *__restrict__ x, T *pout, const T *__restrict_
     }
     // a defer launch reads no pending step, so no CTA can see this slot change
     if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) sr[ia + NP] = (double)a;
-}
-
-// y_r += coef[r] * x_r (complex coefficients in device memory)
-template <typename T>
-__global__ void axpy_b_kernel(T *__restrict__ y, const T *__restrict__ x, const double2 *__restrict__ coef, int64_t n) {
-    using R = typename RealB<T>::type;
-    const int r = blockIdx.y;
-    const size_t off = (size_t)r * n;
-    const R ar = (R)coef[r].x, ai = (R)coef[r].y;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T xv = x[off + i], yv = y[off + i];
-        yv.x += ar * xv.x - ai * xv.y;
-        yv.y += ar * xv.y + ai * xv.x;
-        y[off + i] = yv;
-    }
 }
 
 // w_r *= sc[r];  res_r -= al[r] * w_r   (GCR direction normalisation and residual update)
@@ -496,20 +444,6 @@ void multiaxpy_b(dwf_ctx *c, T *w, T *const *V, int k, int base, int stride, dou
 }
 
 template <typename T>
-void cg_xr_b(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs) {
-    dim3 g = grid_b(c, n, nrhs, 16);
-    cg_xr_b_kernel<T><<<g, BT, 0, c->stream>>>(x, r, p, w, c->scal.as<double>(), base, stride, izz, iww, n);
-    DWF_CHECK_LAUNCH();
-}
-
-template <typename T>
-void cg_p_b(dwf_ctx *c, T *p, const T *z, int base, int stride, int inew, int iold, int64_t n, int nrhs) {
-    dim3 g = grid_b(c, n, nrhs, 16);
-    cg_p_b_kernel<T><<<g, BT, 0, c->stream>>>(p, z, c->scal.as<double>(), base, stride, inew, iold, n);
-    DWF_CHECK_LAUNCH();
-}
-
-template <typename T>
 void cg_r_b(dwf_ctx *c, T *r, const T *rin, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs) {
     dim3 g = grid_b(c, n, nrhs, 16);
     cg_r_b_kernel<T><<<g, BT, 0, c->stream>>>(r, rin, w, c->scal.as<double>(), base, stride, izz, iww, n);
@@ -543,12 +477,6 @@ void cg_pxd_b(dwf_ctx *c, T *x, T *pout, const T *pin, T *const *pend, int np, c
         default: PX(3); break;
     }
 #undef PX
-    DWF_CHECK_LAUNCH();
-}
-
-template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs) {
-    dim3 g = grid_b(c, n, nrhs, 16);
-    axpy_b_kernel<T><<<g, BT, 0, c->stream>>>(y, x, coef, n);
     DWF_CHECK_LAUNCH();
 }
 
@@ -598,8 +526,6 @@ void cg_chunk_b(dwf_ctx *c, T *x, T *p, T *const *Z, int m, bool next, bool xini
     template void norm2_b<T>(dwf_ctx *, BatchScratch &, int, int, const T *, int64_t, int);                  \
     template void multidot_b<T>(dwf_ctx *, BatchScratch &, int, int, T *const *, int, const T *, int64_t, int); \
     template void multiaxpy_b<T>(dwf_ctx *, T *, T *const *, int, int, int, double, int64_t, int);            \
-    template void cg_xr_b<T>(dwf_ctx *, T *, T *, const T *, const T *, int, int, int, int, int64_t, int);    \
-    template void cg_p_b<T>(dwf_ctx *, T *, const T *, int, int, int, int, int64_t, int);                     \
     template void cg_r_b<T>(dwf_ctx *, T *, const T *, const T *, int, int, int, int, int64_t, int);          \
     template void cg_px_b<T>(dwf_ctx *, T *, T *, const T *, const T *, int, int, int, int, int, int64_t, int, bool, \
                              bool);                                                                            \
@@ -608,7 +534,6 @@ void cg_chunk_b(dwf_ctx *c, T *x, T *p, T *const *Z, int m, bool next, bool xini
     template void cg_combine_b<T>(dwf_ctx *, T *, T *const *, int, int, int, int, int, int64_t, int);        \
     template void cg_chunk_b<T>(dwf_ctx *, T *, T *, T *const *, int, bool, bool, int, int, int, int, int, int,   \
                                 int64_t, int);                                                                 \
-    template void axpy_b<T>(dwf_ctx *, T *, const T *, const double2 *, int64_t, int);                        \
     template void gcr_wr_b<T>(dwf_ctx *, T *, T *, const double *, const double2 *, int64_t, int);            \
     template void combo_b<T>(dwf_ctx *, T *, T *const *, int, const double2 *, int64_t, int);
 INSTB(float2)

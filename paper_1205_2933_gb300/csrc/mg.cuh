@@ -151,9 +151,6 @@ template <typename T> void norm2_b(dwf_ctx *c, BatchScratch &bs, int base, int s
 template <typename T>
 void multidot_b(dwf_ctx *c, BatchScratch &bs, int base, int stride, T *const *V, int k, const T *w, int64_t n, int nrhs);
 template <typename T> void multiaxpy_b(dwf_ctx *c, T *w, T *const *V, int k, int base, int stride, double sgn, int64_t n, int nrhs);
-template <typename T>
-void cg_xr_b(dwf_ctx *c, T *x, T *r, const T *p, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
-template <typename T> void cg_p_b(dwf_ctx *c, T *p, const T *z, int base, int stride, int inew, int iold, int64_t n, int nrhs);
 // r = rin - a w (rin may be r), a = |z|^2 / |w|^2 from the slots
 template <typename T>
 void cg_r_b(dwf_ctx *c, T *r, const T *rin, const T *w, int base, int stride, int izz, int iww, int64_t n, int nrhs);
@@ -181,7 +178,6 @@ void cg_combine_b(dwf_ctx *c, T *x, T *const *Z, int k, int base, int stride, in
 template <typename T>
 void cg_chunk_b(dwf_ctx *c, T *x, T *p, T *const *Z, int m, bool next, bool xinit, int base, int stride, int zb, int wb,
                 int k0, int rs, int64_t n, int nrhs);
-template <typename T> void axpy_b(dwf_ctx *c, T *y, const T *x, const double2 *coef, int64_t n, int nrhs);
 template <typename T> void gcr_wr_b(dwf_ctx *c, T *w, T *res, const double *sc, const double2 *al, int64_t n, int nrhs);
 template <typename T> void combo_b(dwf_ctx *c, T *x, T *const *V, int k, const double2 *g, int64_t n, int nrhs);
 
