@@ -411,7 +411,9 @@ bool coarse_gcr_batch_ok(const Level &L, int restart, int nb) {
     return restart >= 1 && restart <= BMAXR && nb >= 1 && nb <= BMAXB;
 }
 
-// partial sums, totals and (tensor-core solver) an error word
+// partial sums and totals; the tensor-core solver's two alternating buffers
+// of FP32 partials (2 x (16 + 2) x 16 complex values per CTA, at most
+// sm_count CTAs) take no more
 size_t coarse_gcr_batch_part_bytes(dwf_ctx *c) { return sizeof(double2) * (size_t)MAXV * (c->sm_count + 1) + 256; }
 
 template <typename R>

@@ -810,8 +810,6 @@ bool coarse_gcr_tc_ok(dwf_ctx *c, const Level &L, int restart, int nb) {
     return restart >= 1 && restart <= TMAXR && L.Ytc.p && tc_shape_ok(c, L, nb);
 }
 
-size_t coarse_gcr_tc_part_bytes(dwf_ctx *c) { return sizeof(double2) * (size_t)TMAXV * (c->sm_count + 1) + 256; }
-
 void coarse_gcr_tc(dwf_ctx *c, const Level &L, float2 *x, const float2 *b, int nb, float2 *r, float2 *Z, float2 *W,
                    double2 *part, int *iters, double tol, int maxiter, int restart) {
     DWF_REQUIRE(coarse_gcr_tc_ok(c, L, restart, nb), DWF_EINVAL, "tensor-core coarse solve: unsupported shape");
